@@ -1,0 +1,192 @@
+/*
+ * libsscf: sparse SCF hot path (Scemama, Renon & Rapacioli 2014, "A Sparse
+ * SCF algorithm and its parallel implementation: Application to DFTB") on one
+ * GB300 GPU (sm_103a).
+ *
+ * One context holds one water-like cluster: molecules of three consecutive
+ * atoms (O, H, H), 6 atomic orbitals each (O s, px, py, pz, H s, H s), 4
+ * doubly occupied and 2 virtual MOs per molecule. All device memory is owned
+ * by the context; every host pointer passed in is read (or written) during
+ * the call only and stays owned by the caller. Calls on one context run in
+ * order on the context's CUDA stream and are not thread-safe.
+ *
+ * Status codes: every function returns SSCF_OK (0) or a negative error; no
+ * exception or abort crosses this interface. Units: bohr, hartree, electrons.
+ */
+#ifndef SSCF_H
+#define SSCF_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    SSCF_OK = 0,
+    SSCF_ERR_INVALID_ARG = -1,   /* bad pointer, size or value                      */
+    SSCF_ERR_OOM = -2,           /* device allocation failed                         */
+    SSCF_ERR_CUDA = -3,          /* a CUDA runtime call or a kernel launch failed    */
+    SSCF_ERR_NONFINITE = -4,     /* NaN or Inf in an input or a result               */
+    SSCF_ERR_CAPACITY = -5,      /* a sparse row outgrew its capacity; state kept    */
+    SSCF_ERR_NOT_CONVERGED = -6, /* sscf_run reached max_scc; state kept             */
+    SSCF_ERR_TIMEOUT = -7,       /* a bounded device wait gave up                    */
+    SSCF_ERR_STATE = -8          /* call made out of order (e.g. step before guess)  */
+};
+
+enum { SSCF_FP64 = 0, SSCF_MIXED = 1 };
+enum { SSCF_ORTHO_ALL = 0, SSCF_ORTHO_OCC = 1 };
+
+typedef struct sscf_ctx sscf_ctx;
+
+/* Geometry and partition (host arrays, copied at sscf_create). */
+typedef struct {
+    int n_atoms;              /* 3 * n_mol                                              */
+    const int* species;       /* n_atoms: 0 = O, 1 = H; molecule-major O, H, H          */
+    const double* xyz;        /* 3 * n_atoms, bohr                                       */
+    const int* group_of_mol;  /* n_atoms / 3: MO-group index of every molecule          */
+} sscf_system;
+
+/* Model and SCF parameters (Section "Specific implementation for DFTB",
+ * Section "Sparsity and numerical accuracy"). */
+typedef struct {
+    double onsite[3];        /* O s, O p, H s on-site energies of H0                    */
+    double V0[4];            /* H0 two-centre prefactors: ss-sigma, sp-sigma, pp-sigma, pp-pi */
+    double S0[4];            /* overlap prefactors, same order                           */
+    double r_decay;          /* V(r) = V0 exp(-r / r_decay)                              */
+    double r_cut;            /* pairs with r <= r_cut interact                           */
+    double U[2];             /* Hubbard parameters O, H: gamma = 1/sqrt(r^2 + a^2)       */
+    double q0[2];            /* reference populations O, H                               */
+    double eps;              /* sparse threshold epsilon of the current stage            */
+    double dq_tol;           /* delta q_max convergence criterion                        */
+    double e_tol;            /* |E_n - E_{n-1}| convergence criterion                    */
+    double group_cut;        /* MO groups closer than this are neighbours (20 bohr)      */
+    double rot_cap_factor;   /* at most factor * N_occ rotations per sweep (10)          */
+    double mix_beta;         /* linear charge mixing                                     */
+    int max_scc;             /* iteration limit of sscf_run (per stage)                  */
+    int precision;           /* SSCF_FP64 or SSCF_MIXED                                   */
+    int ortho_every;         /* 1: one occupied orthonormalisation pass per SCC step     */
+    int cap_tiles;           /* per-row tile capacity of C; 0 picks the dense size       */
+} sscf_params;
+
+typedef struct {
+    double energy;           /* E = sum P*H0 + 1/2 dq^T gamma dq (Ha)                    */
+    double dq_max;           /* max_a |q_a^(n) - q_a^(n-1)|                               */
+    double dE;               /* E^(n) - E^(n-1)                                          */
+    double max_fov;          /* largest |F_ij| over kept occupied-virtual blocks          */
+    double eta;              /* largest normalised off-diagonal overlap of the ortho pass */
+    int64_t n_rot;           /* rotations applied in the sweep                           */
+    int64_t n_combo;         /* orthonormalisation combinations applied                  */
+    int64_t nnz_c;           /* stored tiles of C times 96 (6 AO rows x 16 MOs)          */
+    int iteration;
+} sscf_step_info;
+
+/* Context ---------------------------------------------------------------- */
+
+/* Builds the structure of step I (atom and molecule neighbour lists within
+ * r_cut, the MO-group neighbour map at group_cut, the greedy colouring of the
+ * group graph; Section "Defining neighbouring lists"), uploads the geometry,
+ * evaluates H0 and S on the molecule-pair blocks and allocates C.
+ * `cuda_stream` is a cudaStream_t or NULL for the legacy default stream.
+ * Errors: INVALID_ARG (non-water layout, bad sizes), OOM, CUDA, NONFINITE. */
+int sscf_create(const sscf_system* sys, const sscf_params* prm, void* cuda_stream,
+                sscf_ctx** out);
+void sscf_destroy(sscf_ctx* ctx);
+const char* sscf_strerror(int status);
+
+/* Device allocator used by the next sscf_create (NULL restores cudaMalloc /
+ * cudaFree). alloc returns NULL on failure, which sscf_create reports as
+ * SSCF_ERR_OOM. */
+typedef void* (*sscf_alloc_fn)(size_t bytes, void* user);
+typedef void (*sscf_free_fn)(void* ptr, void* user);
+int sscf_set_allocator(sscf_alloc_fn alloc, sscf_free_fn free_, void* user);
+
+/* Thresholds of the current SCF stage (Section "Sparsity and numerical
+ * accuracy": loose eps 1e-3 / dq 1e-1, then the user values). */
+int sscf_set_thresholds(sscf_ctx* ctx, double eps, double dq_tol, double e_tol);
+
+/* Sizes: n_ao, n_mo, n_occ, n_groups, n_tiles, n_colours (any may be NULL). */
+int sscf_get_dims(const sscf_ctx* ctx, int* n_ao, int* n_mo, int* n_occ, int* n_groups,
+                  int* n_tiles, int* n_colours);
+
+/* Steps ---------------------------------------------------------------- */
+
+/* Step II (Section "Initial guess"): one non-SCC generalised eigensolve per
+ * molecule; occupied MOs group-major, then virtual MOs; in a molecule the
+ * MOs follow ascending eigenvalue, the largest-magnitude coefficient made
+ * positive (first index within 1e-9 of the largest magnitude). */
+int sscf_guess(sscf_ctx* ctx);
+
+/* Step III (Section "Orthonormalization", steps a-e): passes of
+ * sigma = C^T S C on neighbouring-group blocks, normalisation by diag(sigma),
+ * first-order combinations C'_i = C_i - sigma_ij C_j / 2,
+ * C'_j = C_j - sigma_ij C_i / 2 on pairs |sigma_ij| >= 1e-3 eta, truncation
+ * at 1e-3 eps, until eta < eps / 100 or max_pass passes. `which` is
+ * SSCF_ORTHO_ALL or SSCF_ORTHO_OCC. passes_out, eta_out may be NULL. */
+int sscf_orthonormalise(sscf_ctx* ctx, int which, int max_pass, int* passes_out,
+                        double* eta_out);
+
+/* Step IV, Eq. (H_dftb2): Q = gamma dq_in (all atom pairs, unscreened) is
+ * kept from the last charge update; H = H0 + 1/2 S (Q_a + Q_b) on the
+ * molecule-pair blocks, off-diagonal |H_mn| < eps set to zero. */
+int sscf_build_fock(sscf_ctx* ctx);
+
+/* Step V (Section "Partial diagonalization"): F = C^T H C on the occupied-
+ * virtual blocks of neighbouring groups plus diag(F); pairs with
+ * |F_ij| >= eps, at most rot_cap_factor * N_occ of the largest (ties kept);
+ * Jacobi angles p, t, c, s in FP64 from the F of the sweep start; rotations
+ * C'_i = c C_i + s C_j, C'_j = -s C_i + c C_j applied block colour by block
+ * colour, then by in-block colour (i_loc + j_loc) mod n, truncating
+ * |C| < eps after each. Outputs may be NULL. */
+int sscf_rotate_sweep(sscf_ctx* ctx, int64_t* n_rot_out, double* max_fov_out);
+
+/* Eq. (pop) with P = 2 C_occ C_occ^T on the molecule-pair pattern: Mulliken
+ * charges q (host, n_atoms, or NULL), E = sum P*H0 + 1/2 dq^T gamma dq with
+ * gamma dq recomputed from these charges, and max |q - q_previous|. The new
+ * charges become q_previous and the SCC input is mixed:
+ * dq_in += beta (dq - dq_in), Q_in += beta (gamma dq - Q_in). */
+int sscf_density(sscf_ctx* ctx, double* q_out, double* E_out, double* dq_max_out);
+
+/* Charges of the current C without mixing: they become q_previous, and the
+ * SCC input is set to them (dq_in = dq, Q_in = gamma dq). This is how an SCF
+ * stage starts after the guess and the orthonormalisation. E_out may be NULL. */
+int sscf_reset_charges(sscf_ctx* ctx, double* E_out);
+
+/* One SCC iteration: build_fock, rotate_sweep, one occupied ortho pass
+ * (ortho_every = 1), density and mixing. */
+int sscf_step(sscf_ctx* ctx, sscf_step_info* info);
+
+/* Loose stage (eps 1e-3, dq 1e-1), full orthonormalisation, user stage until
+ * dq_max <= dq_tol and |dE| <= e_tol, final occupied orthonormalisation to
+ * eps / 100 and final charges and energy. Returns NOT_CONVERGED with the
+ * state kept if max_scc is reached. */
+int sscf_run(sscf_ctx* ctx, sscf_step_info* info);
+
+/* State access (checkpoint / restart and tests) -------------------------- */
+
+/* Dense copies for small systems: C is n_ao x n_mo, row-major (C[mu*n_mo+i]). */
+int sscf_get_C_dense(sscf_ctx* ctx, double* C);
+int sscf_set_C_dense(sscf_ctx* ctx, const double* C);
+/* Dense n_ao x n_ao copies of the current H, of H0 and of S. */
+int sscf_get_H_dense(sscf_ctx* ctx, double* H, double* H0, double* S);
+/* Dense F_ov (n_occ x (n_mo - n_occ), zero off the kept blocks) and diag(F)
+ * (n_mo) of the last transform. */
+int sscf_get_F_dense(sscf_ctx* ctx, double* F_ov, double* F_diag);
+/* Charges: q_prev (last output charges), dq_in and Q_in (SCC input). */
+int sscf_get_charges(sscf_ctx* ctx, double* q_prev, double* dq_in, double* Q_in);
+int sscf_set_charges(sscf_ctx* ctx, const double* q_prev, const double* dq_in,
+                     const double* Q_in);
+/* Group colouring (n_groups x n_groups, -1 off the graph) for structure tests. */
+int sscf_get_colouring(sscf_ctx* ctx, int* colour);
+/* Last pair list (rotations after sscf_rotate_sweep or sscf_step's sweep;
+ * combinations after an orthonormalisation pass): for every pair its block
+ * colour, in-block colour, and MO indices (i, j), grouped by colour, then
+ * in-block colour. Any output array may be NULL; capacity is in pairs and
+ * n_out receives the full count. */
+int sscf_get_pairs(sscf_ctx* ctx, int64_t capacity, int32_t* colour_out, int32_t* sub_out, int32_t* i_out,
+                   int32_t* j_out, int64_t* n_out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

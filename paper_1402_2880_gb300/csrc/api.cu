@@ -1,0 +1,814 @@
+// C-ABI of libsscf: context creation (step I structure on the host), device
+// allocation, and the order of kernel launches of every step.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <numeric>
+#include <new>
+
+#include "sscf_internal.h"
+
+using namespace sscf;
+
+namespace {
+
+sscf_alloc_fn g_alloc = nullptr;
+sscf_free_fn g_free = nullptr;
+void* g_alloc_user = nullptr;
+
+#define CK(call)                                                          \
+    do {                                                                  \
+        cudaError_t e_ = (call);                                          \
+        if (e_ != cudaSuccess) {                                          \
+            fprintf(stderr, "libsscf: %s failed: %s (%s:%d)\n", #call,     \
+                    cudaGetErrorString(e_), __FILE__, __LINE__);          \
+            return SSCF_ERR_CUDA;                                         \
+        }                                                                 \
+    } while (0)
+
+#define CKS(call)                              \
+    do {                                       \
+        int s_ = (call);                       \
+        if (s_ != SSCF_OK) return s_;          \
+    } while (0)
+
+// Squared distance evaluated as (dx*dx + dy*dy) + dz*dz. The library is
+// compiled with -ffp-contract=off so that no product is fused into the sums:
+// neighbour decisions are then bit-identical to any other IEEE evaluation of
+// the same expression.
+inline double dist2(const double* a, const double* b) {
+    double dx = b[0] - a[0], dy = b[1] - a[1], dz = b[2] - a[2];
+    double xx = dx * dx, yy = dy * dy, zz = dz * dz;
+    double s = xx + yy;
+    return s + zz;
+}
+
+struct CellGrid {
+    double lo[3], h;
+    int n[3];
+    std::vector<int> head, next;
+    void build(const std::vector<double>& pts, int npts, double cell) {
+        for (int d = 0; d < 3; ++d) lo[d] = 1e300;
+        double hi[3] = {-1e300, -1e300, -1e300};
+        for (int i = 0; i < npts; ++i)
+            for (int d = 0; d < 3; ++d) {
+                lo[d] = std::min(lo[d], pts[3 * i + d]);
+                hi[d] = std::max(hi[d], pts[3 * i + d]);
+            }
+        h = cell;
+        for (int d = 0; d < 3; ++d) n[d] = std::max(1, (int)std::floor((hi[d] - lo[d]) / h) + 1);
+        head.assign((size_t)n[0] * n[1] * n[2], -1);
+        next.assign(npts, -1);
+        for (int i = 0; i < npts; ++i) {
+            int c = cell_of(&pts[3 * i]);
+            next[i] = head[c];
+            head[c] = i;
+        }
+    }
+    int coord(const double* p, int d) const {
+        int k = (int)std::floor((p[d] - lo[d]) / h);
+        return std::min(std::max(k, 0), n[d] - 1);
+    }
+    int cell_of(const double* p) const {
+        return coord(p, 0) + n[0] * (coord(p, 1) + n[1] * coord(p, 2));
+    }
+};
+
+int build_structure(Ctx& c, const sscf_system* sys) {
+    const int nA = c.n_atoms, nM = c.n_mol;
+    const double* X = c.h_xyz.data();
+    // ---- molecule pairs with an atom pair within r_cut (plus (m, m)) ----
+    std::vector<double> ox(3 * nM);
+    std::vector<double> rad(nM, 0.0);
+    double rmax = 0.0;
+    for (int m = 0; m < nM; ++m) {
+        for (int d = 0; d < 3; ++d) ox[3 * m + d] = X[3 * (3 * m) + d];
+        for (int k = 1; k < 3; ++k) rad[m] = std::max(rad[m], std::sqrt(dist2(&X[9 * m], &X[9 * m + 3 * k])));
+        rmax = std::max(rmax, rad[m]);
+    }
+    const double rc2 = c.prm.r_cut * c.prm.r_cut;
+    CellGrid grid;
+    grid.build(ox, nM, c.prm.r_cut + 2.0 * rmax + 1e-9);
+    std::vector<std::vector<int>> nbm(nM);
+    for (int m = 0; m < nM; ++m) {
+        int cx = grid.coord(&ox[3 * m], 0), cy = grid.coord(&ox[3 * m], 1), cz = grid.coord(&ox[3 * m], 2);
+        for (int dz = -1; dz <= 1; ++dz)
+            for (int dy = -1; dy <= 1; ++dy)
+                for (int dx = -1; dx <= 1; ++dx) {
+                    int x = cx + dx, y = cy + dy, z = cz + dz;
+                    if (x < 0 || y < 0 || z < 0 || x >= grid.n[0] || y >= grid.n[1] || z >= grid.n[2]) continue;
+                    for (int n = grid.head[x + grid.n[0] * (y + grid.n[1] * z)]; n >= 0; n = grid.next[n]) {
+                        bool hit = (n == m);
+                        for (int a = 0; a < 3 && !hit; ++a)
+                            for (int b = 0; b < 3 && !hit; ++b)
+                                if (dist2(&X[3 * (3 * m + a)], &X[3 * (3 * n + b)]) <= rc2) hit = true;
+                        if (hit) nbm[m].push_back(n);
+                    }
+                }
+        std::sort(nbm[m].begin(), nbm[m].end());
+    }
+    c.h_mp_ptr.assign(nM + 1, 0);
+    for (int m = 0; m < nM; ++m) c.h_mp_ptr[m + 1] = c.h_mp_ptr[m] + (int)nbm[m].size();
+    c.n_mp = c.h_mp_ptr[nM];
+    c.h_mp_col.resize(c.n_mp);
+    for (int m = 0; m < nM; ++m) std::copy(nbm[m].begin(), nbm[m].end(), c.h_mp_col.begin() + c.h_mp_ptr[m]);
+
+    // ---- groups ----
+    const int G = c.n_groups;
+    std::vector<std::vector<int>> mols(G);
+    for (int m = 0; m < nM; ++m) mols[c.h_mol_group[m]].push_back(m);
+    c.h_mol_local.assign(nM, 0);
+    c.h_group_nmol.assign(G, 0);
+    c.h_group_occ0.assign(G, 0);
+    c.h_group_virt0.assign(G, 0);
+    c.h_group_ot0.assign(G, 0);
+    c.h_group_not.assign(G, 0);
+    c.h_group_vt0.assign(G, 0);
+    c.h_group_nvt.assign(G, 0);
+    int o = 0, v = c.n_occ, ot = 0;
+    for (int g = 0; g < G; ++g) {
+        if (mols[g].empty() || mols[g].size() > 8) return SSCF_ERR_INVALID_ARG;
+        for (size_t k = 0; k < mols[g].size(); ++k) c.h_mol_local[mols[g][k]] = (int)k;
+        int nm = (int)mols[g].size();
+        c.h_group_nmol[g] = nm;
+        c.h_group_occ0[g] = o;
+        c.h_group_virt0[g] = v;
+        o += 4 * nm;
+        v += 2 * nm;
+        c.h_group_ot0[g] = ot;
+        c.h_group_not[g] = (4 * nm + kTileW - 1) / kTileW;
+        ot += c.h_group_not[g];
+    }
+    c.n_occ_tiles = ot;
+    int vt = ot;
+    for (int g = 0; g < G; ++g) {
+        c.h_group_vt0[g] = vt;
+        c.h_group_nvt[g] = (2 * c.h_group_nmol[g] + kTileW - 1) / kTileW;
+        vt += c.h_group_nvt[g];
+    }
+    c.n_tiles = vt;
+    c.h_tile_group.assign(c.n_tiles, 0);
+    c.h_tile_kind.assign(c.n_tiles, 0);
+    c.h_tile_loc0.assign(c.n_tiles, 0);
+    c.h_tile_nmo.assign(c.n_tiles, 0);
+    c.h_tile_mo0.assign(c.n_tiles, 0);
+    for (int g = 0; g < G; ++g) {
+        int no = 4 * c.h_group_nmol[g], nv = 2 * c.h_group_nmol[g];
+        for (int t = 0; t < c.h_group_not[g]; ++t) {
+            int id = c.h_group_ot0[g] + t;
+            c.h_tile_group[id] = g;
+            c.h_tile_kind[id] = 0;
+            c.h_tile_loc0[id] = t * kTileW;
+            c.h_tile_nmo[id] = std::min(kTileW, no - t * kTileW);
+            c.h_tile_mo0[id] = c.h_group_occ0[g] + t * kTileW;
+        }
+        for (int t = 0; t < c.h_group_nvt[g]; ++t) {
+            int id = c.h_group_vt0[g] + t;
+            c.h_tile_group[id] = g;
+            c.h_tile_kind[id] = 1;
+            c.h_tile_loc0[id] = t * kTileW;
+            c.h_tile_nmo[id] = std::min(kTileW, nv - t * kTileW);
+            c.h_tile_mo0[id] = c.h_group_virt0[g] + t * kTileW;
+        }
+    }
+
+    // ---- group neighbour map: some atom pair closer than group_cut ----
+    std::vector<double> gc(3 * G, 0.0), grad(G, 0.0);
+    std::vector<std::vector<int>> gatoms(G);
+    for (int g = 0; g < G; ++g) {
+        for (int m : mols[g])
+            for (int a = 0; a < 3; ++a) gatoms[g].push_back(3 * m + a);
+        for (int a : gatoms[g])
+            for (int d = 0; d < 3; ++d) gc[3 * g + d] += X[3 * a + d];
+        for (int d = 0; d < 3; ++d) gc[3 * g + d] /= (double)gatoms[g].size();
+        for (int a : gatoms[g]) grad[g] = std::max(grad[g], std::sqrt(dist2(&gc[3 * g], &X[3 * a])));
+    }
+    double gmax = *std::max_element(grad.begin(), grad.end());
+    const double gc2 = c.prm.group_cut * c.prm.group_cut;
+    CellGrid gg;
+    gg.build(gc, G, c.prm.group_cut + 2.0 * gmax + 1e-9);
+    std::vector<std::vector<int>> gnb(G);
+    for (int A = 0; A < G; ++A) {
+        int cx = gg.coord(&gc[3 * A], 0), cy = gg.coord(&gc[3 * A], 1), cz = gg.coord(&gc[3 * A], 2);
+        for (int dz = -1; dz <= 1; ++dz)
+            for (int dy = -1; dy <= 1; ++dy)
+                for (int dx = -1; dx <= 1; ++dx) {
+                    int x = cx + dx, y = cy + dy, z = cz + dz;
+                    if (x < 0 || y < 0 || z < 0 || x >= gg.n[0] || y >= gg.n[1] || z >= gg.n[2]) continue;
+                    for (int B = gg.head[x + gg.n[0] * (y + gg.n[1] * z)]; B >= 0; B = gg.next[B]) {
+                        bool hit = (A == B);
+                        for (size_t i = 0; i < gatoms[A].size() && !hit; ++i)
+                            for (size_t j = 0; j < gatoms[B].size() && !hit; ++j)
+                                if (dist2(&X[3 * gatoms[A][i]], &X[3 * gatoms[B][j]]) < gc2) hit = true;
+                        if (hit) gnb[A].push_back(B);
+                    }
+                }
+        std::sort(gnb[A].begin(), gnb[A].end());
+    }
+    // ---- greedy first-fit edge colouring, edges {A < B} in lexicographic order ----
+    std::vector<std::vector<char>> used(G);
+    std::vector<std::vector<int>> ecol(G);
+    int n_col = 1;
+    for (int A = 0; A < G; ++A) ecol[A].assign(gnb[A].size(), -1);
+    for (int A = 0; A < G; ++A) {
+        for (size_t k = 0; k < gnb[A].size(); ++k) {
+            int B = gnb[A][k];
+            if (B == A) {
+                ecol[A][k] = 0;
+                continue;
+            }
+            if (B < A) continue;
+            int col = 1;
+            while ((col < (int)used[A].size() && used[A][col]) || (col < (int)used[B].size() && used[B][col])) ++col;
+            ecol[A][k] = col;
+            if ((int)used[A].size() <= col) used[A].resize(col + 1, 0);
+            if ((int)used[B].size() <= col) used[B].resize(col + 1, 0);
+            used[A][col] = used[B][col] = 1;
+            n_col = std::max(n_col, col + 1);
+        }
+    }
+    for (int A = 0; A < G; ++A)
+        for (size_t k = 0; k < gnb[A].size(); ++k) {
+            int B = gnb[A][k];
+            if (B < A) {
+                auto it = std::lower_bound(gnb[B].begin(), gnb[B].end(), A);
+                ecol[A][k] = ecol[B][it - gnb[B].begin()];
+            }
+        }
+    c.n_colours = n_col;
+    c.h_gnb_ptr.assign(G + 1, 0);
+    for (int A = 0; A < G; ++A) c.h_gnb_ptr[A + 1] = c.h_gnb_ptr[A] + (int)gnb[A].size();
+    c.n_gnb = c.h_gnb_ptr[G];
+    c.h_gnb_col.resize(c.n_gnb);
+    c.h_gnb_row.resize(c.n_gnb);
+    c.h_gnb_colour.resize(c.n_gnb);
+    for (int A = 0; A < G; ++A)
+        for (size_t k = 0; k < gnb[A].size(); ++k) {
+            int e = c.h_gnb_ptr[A] + (int)k;
+            c.h_gnb_col[e] = gnb[A][k];
+            c.h_gnb_row[e] = A;
+            c.h_gnb_colour[e] = ecol[A][k];
+        }
+    // blocks by colour: all directed blocks, and blocks with A <= B
+    c.h_colour_ptr.assign(n_col + 1, 0);
+    c.h_ocolour_ptr.assign(n_col + 1, 0);
+    for (int e = 0; e < c.n_gnb; ++e) {
+        c.h_colour_ptr[c.h_gnb_colour[e] + 1]++;
+        if (c.h_gnb_row[e] <= c.h_gnb_col[e]) c.h_ocolour_ptr[c.h_gnb_colour[e] + 1]++;
+    }
+    for (int k = 0; k < n_col; ++k) {
+        c.h_colour_ptr[k + 1] += c.h_colour_ptr[k];
+        c.h_ocolour_ptr[k + 1] += c.h_ocolour_ptr[k];
+    }
+    c.h_colour_blk.assign(c.n_gnb, 0);
+    c.h_ocolour_blk.assign(c.h_ocolour_ptr[n_col], 0);
+    {
+        std::vector<int> f1(c.h_colour_ptr.begin(), c.h_colour_ptr.end() - 1);
+        std::vector<int> f2(c.h_ocolour_ptr.begin(), c.h_ocolour_ptr.end() - 1);
+        for (int e = 0; e < c.n_gnb; ++e) {
+            int col = c.h_gnb_colour[e];
+            c.h_colour_blk[f1[col]++] = e;
+            if (c.h_gnb_row[e] <= c.h_gnb_col[e]) c.h_ocolour_blk[f2[col]++] = e;
+        }
+    }
+
+    // ---- tile pairs of the occupied-virtual transform ----
+    // block e = (A, B): a in occ tiles of A, b in virt tiles of B
+    std::vector<std::vector<std::pair<int, int>>> by_a(c.n_tiles);
+    c.h_rot_blk_tp0.assign(c.n_gnb, 0);
+    int out = 0;
+    for (int e = 0; e < c.n_gnb; ++e) {
+        int A = c.h_gnb_row[e], B = c.h_gnb_col[e];
+        c.h_rot_blk_tp0[e] = out;
+        for (int ia = 0; ia < c.h_group_not[A]; ++ia)
+            for (int ib = 0; ib < c.h_group_nvt[B]; ++ib)
+                by_a[c.h_group_ot0[A] + ia].push_back({c.h_group_vt0[B] + ib, out++});
+    }
+    c.n_rot_tp = out;
+    c.h_rot_tp_ptr.assign(c.n_tiles + 1, 0);
+    for (int t = 0; t < c.n_tiles; ++t) c.h_rot_tp_ptr[t + 1] = c.h_rot_tp_ptr[t] + (int)by_a[t].size();
+    c.h_rot_tp_b.resize(out);
+    c.h_rot_tp_out.resize(out);
+    for (int t = 0; t < c.n_tiles; ++t)
+        for (size_t k = 0; k < by_a[t].size(); ++k) {
+            c.h_rot_tp_b[c.h_rot_tp_ptr[t] + k] = by_a[t][k].first;
+            c.h_rot_tp_out[c.h_rot_tp_ptr[t] + k] = by_a[t][k].second;
+        }
+    (void)sys;
+    (void)nA;
+    return SSCF_OK;
+}
+
+// Tile pairs of the overlap transform for a pass over all MOs (w = 0) or the
+// occupied MOs only (w = 1): blocks (A, B) with A <= B; the side of a group
+// lists its occupied tiles, then (w = 0) its virtual tiles.
+void ortho_lists(const Ctx& c, int w, std::vector<int>& ptr, std::vector<int>& bl, std::vector<int>& outl,
+                 std::vector<int>& blk_tp, int& n_tp) {
+    std::vector<std::vector<std::pair<int, int>>> by_a(c.n_tiles);
+    blk_tp.assign((size_t)c.n_gnb * 9, -1);
+    int out = 0;
+    auto side = [&](int g, int* t) {
+        int n = 0;
+        for (int i = 0; i < c.h_group_not[g]; ++i) t[n++] = c.h_group_ot0[g] + i;
+        if (w == 0)
+            for (int i = 0; i < c.h_group_nvt[g]; ++i) t[n++] = c.h_group_vt0[g] + i;
+        return n;
+    };
+    for (int e = 0; e < c.n_gnb; ++e) {
+        int A = c.h_gnb_row[e], B = c.h_gnb_col[e];
+        if (A > B) continue;
+        int ta[3], tb[3];
+        int na = side(A, ta), nb = side(B, tb);
+        for (int i = 0; i < na; ++i)
+            for (int j = 0; j < nb; ++j) {
+                if (A == B && j < i) continue;
+                blk_tp[(size_t)e * 9 + i * 3 + j] = out;
+                by_a[ta[i]].push_back({tb[j], out++});
+            }
+    }
+    n_tp = out;
+    ptr.assign(c.n_tiles + 1, 0);
+    for (int t = 0; t < c.n_tiles; ++t) ptr[t + 1] = ptr[t] + (int)by_a[t].size();
+    bl.resize(out);
+    outl.resize(out);
+    for (int t = 0; t < c.n_tiles; ++t)
+        for (size_t k = 0; k < by_a[t].size(); ++k) {
+            bl[ptr[t] + k] = by_a[t][k].first;
+            outl[ptr[t] + k] = by_a[t][k].second;
+        }
+}
+
+template <typename V>
+int upload(Ctx& c, V** d, const std::vector<V>& h) {
+    size_t n = std::max<size_t>(h.size(), 1);
+    CKS(dalloc(&c, d, n));
+    if (!h.empty()) CK(cudaMemcpy(*d, h.data(), h.size() * sizeof(V), cudaMemcpyHostToDevice));
+    return SSCF_OK;
+}
+
+int sync_scalars(Ctx& c) {
+    CK(cudaMemcpyAsync(c.h_sc, c.d_sc, sizeof(DeviceScalars), cudaMemcpyDeviceToHost, c.stream));
+    CK(cudaStreamSynchronize(c.stream));
+    if (c.h_sc->err & kErrCapacity) return SSCF_ERR_CAPACITY;
+    if (c.h_sc->err & kErrSortSize) return SSCF_ERR_CAPACITY;
+    if (c.h_sc->err & kErrNonFinite) return SSCF_ERR_NONFINITE;
+    if (c.h_sc->err & kErrGuess) return SSCF_ERR_NONFINITE;
+    return SSCF_OK;
+}
+
+}  // namespace
+
+namespace sscf {
+
+int dev_alloc(Ctx* c, void** p, size_t bytes) {
+    bytes = std::max<size_t>(bytes, 16);
+    void* q = nullptr;
+    if (g_alloc) {
+        q = g_alloc(bytes, g_alloc_user);
+        if (!q) return SSCF_ERR_OOM;
+    } else {
+        if (cudaMalloc(&q, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            return SSCF_ERR_OOM;
+        }
+    }
+    c->allocations.push_back(q);
+    *p = q;
+    return SSCF_OK;
+}
+
+void dev_free_all(Ctx* c) {
+    for (void* q : c->allocations) {
+        if (g_free)
+            g_free(q, g_alloc_user);
+        else
+            cudaFree(q);
+    }
+    c->allocations.clear();
+}
+
+}  // namespace sscf
+
+// ============================================================================
+// C-ABI
+// ============================================================================
+
+extern "C" {
+
+const char* sscf_strerror(int s) {
+    switch (s) {
+        case SSCF_OK: return "ok";
+        case SSCF_ERR_INVALID_ARG: return "invalid argument";
+        case SSCF_ERR_OOM: return "device allocation failed";
+        case SSCF_ERR_CUDA: return "CUDA error";
+        case SSCF_ERR_NONFINITE: return "non-finite value";
+        case SSCF_ERR_CAPACITY: return "sparse capacity exceeded";
+        case SSCF_ERR_NOT_CONVERGED: return "SCF not converged";
+        case SSCF_ERR_TIMEOUT: return "device wait timed out";
+        case SSCF_ERR_STATE: return "call out of order";
+        default: return "unknown status";
+    }
+}
+
+int sscf_set_allocator(sscf_alloc_fn alloc, sscf_free_fn free_, void* user) {
+    if ((alloc == nullptr) != (free_ == nullptr)) return SSCF_ERR_INVALID_ARG;
+    g_alloc = alloc;
+    g_free = free_;
+    g_alloc_user = user;
+    return SSCF_OK;
+}
+
+int sscf_create(const sscf_system* sys, const sscf_params* prm, void* cuda_stream, sscf_ctx** out) {
+    if (!sys || !prm || !out || !sys->species || !sys->xyz || !sys->group_of_mol) return SSCF_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (sys->n_atoms <= 0 || sys->n_atoms % 3 != 0) return SSCF_ERR_INVALID_ARG;
+    if (prm->precision != SSCF_FP64 && prm->precision != SSCF_MIXED) return SSCF_ERR_INVALID_ARG;
+    if (!(prm->r_cut > 0) || !(prm->r_decay > 0) || !(prm->group_cut > 0) || !(prm->eps >= 0) ||
+        !(prm->U[0] > 0) || !(prm->U[1] > 0) || !(prm->rot_cap_factor > 0))
+        return SSCF_ERR_INVALID_ARG;
+    for (int a = 0; a < sys->n_atoms; ++a) {
+        int want = (a % 3 == 0) ? 0 : 1;
+        if (sys->species[a] != want) return SSCF_ERR_INVALID_ARG;
+        for (int d = 0; d < 3; ++d)
+            if (!std::isfinite(sys->xyz[3 * a + d])) return SSCF_ERR_NONFINITE;
+    }
+    sscf_ctx* h = new (std::nothrow) sscf_ctx();
+    if (!h) return SSCF_ERR_OOM;
+    Ctx& c = h->c;
+    c.prm = *prm;
+    c.stream = (cudaStream_t)cuda_stream;
+    c.prec = prm->precision;
+    c.tsize = c.prec == SSCF_FP64 ? 8 : 4;
+    c.n_atoms = sys->n_atoms;
+    c.n_mol = sys->n_atoms / 3;
+    c.n_ao = 6 * c.n_mol;
+    c.n_occ = 4 * c.n_mol;
+    c.n_mo = 6 * c.n_mol;
+    c.h_species.assign(sys->species, sys->species + c.n_atoms);
+    c.h_xyz.assign(sys->xyz, sys->xyz + 3 * c.n_atoms);
+    c.h_mol_group.assign(sys->group_of_mol, sys->group_of_mol + c.n_mol);
+    int G = 0;
+    for (int m = 0; m < c.n_mol; ++m) {
+        if (c.h_mol_group[m] < 0) {
+            delete h;
+            return SSCF_ERR_INVALID_ARG;
+        }
+        G = std::max(G, c.h_mol_group[m] + 1);
+    }
+    c.n_groups = G;
+    int st = build_structure(c, sys);
+    if (st != SSCF_OK) {
+        delete h;
+        return st;
+    }
+    auto fail = [&](int s) {
+        dev_free_all(&c);
+        if (c.h_sc) cudaFreeHost(c.h_sc);
+        delete h;
+        return s;
+    };
+    c.cap = prm->cap_tiles > 0 ? std::min(prm->cap_tiles, c.n_tiles) : c.n_tiles;
+    c.cap = std::max(c.cap, 2);
+    if (c.n_tiles > 32768) {   // tile ids and slots are packed into 16 bits in the sweep kernel
+        delete h;
+        return SSCF_ERR_INVALID_ARG;
+    }
+    c.capY = c.n_mol;
+    // uploads
+#define UP(d, v)                        \
+    do {                                \
+        int s_ = upload(c, &d, v);      \
+        if (s_ != SSCF_OK) return fail(s_); \
+    } while (0)
+    UP(c.d_xyz, c.h_xyz);
+    UP(c.d_species, c.h_species);
+    UP(c.d_mp_ptr, c.h_mp_ptr);
+    UP(c.d_mp_col, c.h_mp_col);
+    {
+        std::vector<int> row(c.n_mp);
+        for (int m = 0; m < c.n_mol; ++m)
+            for (int k = c.h_mp_ptr[m]; k < c.h_mp_ptr[m + 1]; ++k) row[k] = m;
+        UP(c.d_mp_row, row);
+    }
+    UP(c.d_mol_group, c.h_mol_group);
+    UP(c.d_mol_local, c.h_mol_local);
+    UP(c.d_group_nmol, c.h_group_nmol);
+    UP(c.d_group_ot0, c.h_group_ot0);
+    UP(c.d_group_not, c.h_group_not);
+    UP(c.d_group_vt0, c.h_group_vt0);
+    UP(c.d_group_nvt, c.h_group_nvt);
+    UP(c.d_group_occ0_mo, c.h_group_occ0);
+    UP(c.d_group_virt0_mo, c.h_group_virt0);
+    c.h_self_blk.assign(c.n_groups, -1);
+    for (int e = 0; e < c.n_gnb; ++e)
+        if (c.h_gnb_row[e] == c.h_gnb_col[e]) c.h_self_blk[c.h_gnb_row[e]] = e;
+    UP(c.d_self_blk, c.h_self_blk);
+    UP(c.d_tile_group, c.h_tile_group);
+    UP(c.d_tile_kind, c.h_tile_kind);
+    UP(c.d_tile_loc0, c.h_tile_loc0);
+    UP(c.d_tile_nmo, c.h_tile_nmo);
+    UP(c.d_tile_mo0, c.h_tile_mo0);
+    UP(c.d_gnb_row, c.h_gnb_row);
+    UP(c.d_gnb_col, c.h_gnb_col);
+    UP(c.d_colour_ptr, c.h_colour_ptr);
+    UP(c.d_colour_blk, c.h_colour_blk);
+    UP(c.d_ocolour_ptr, c.h_ocolour_ptr);
+    UP(c.d_ocolour_blk, c.h_ocolour_blk);
+    UP(c.d_rot_tp_ptr, c.h_rot_tp_ptr);
+    UP(c.d_rot_tp_b, c.h_rot_tp_b);
+    UP(c.d_rot_tp_out, c.h_rot_tp_out);
+    UP(c.d_rot_blk_tp0, c.h_rot_blk_tp0);
+    {
+        std::vector<int> dp(c.n_tiles + 1), db(c.n_tiles), dout(c.n_tiles);
+        for (int t = 0; t <= c.n_tiles; ++t) dp[t] = t;
+        for (int t = 0; t < c.n_tiles; ++t) db[t] = dout[t] = t;
+        UP(c.d_diag_tp_ptr, dp);
+        UP(c.d_diag_tp_b, db);
+        UP(c.d_diag_tp_out, dout);
+    }
+    int max_ort = 0;
+    for (int w = 0; w < 2; ++w) {
+        std::vector<int> p, b, o;
+        ortho_lists(c, w, p, b, o, c.h_ort_blk_tp[w], c.n_ort_tp[w]);
+        UP(c.d_ort_tp_ptr[w], p);
+        UP(c.d_ort_tp_b[w], b);
+        UP(c.d_ort_tp_out[w], o);
+        UP(c.d_ort_blk_tp[w], c.h_ort_blk_tp[w]);
+        max_ort = std::max(max_ort, c.n_ort_tp[w]);
+    }
+#undef UP
+    const size_t ts = c.tsize;
+#define AL(p, n)                                    \
+    do {                                            \
+        int s_ = dev_alloc(&c, (void**)&(p), (n));  \
+        if (s_ != SSCF_OK) return fail(s_);         \
+    } while (0)
+    AL(c.d_H0b, (size_t)c.n_mp * 36 * 8);
+    AL(c.d_Sb, (size_t)c.n_mp * 36 * 8);
+    AL(c.d_Hb, (size_t)c.n_mp * 36 * ts);
+    AL(c.d_Sbt, (size_t)c.n_mp * 36 * ts);
+    for (int b = 0; b < 2; ++b) {
+        AL(c.d_c_nt[b], (size_t)c.n_mol * 4);
+        AL(c.d_c_tile[b], (size_t)c.n_mol * c.cap * 4);
+        AL(c.d_c_val[b], (size_t)c.n_mol * c.cap * kTileVals * ts);
+    }
+    AL(c.d_cci_ptr, (size_t)(c.n_tiles + 1) * 4);
+    AL(c.d_cci_cnt, (size_t)c.n_tiles * 4);
+    AL(c.d_cci_row, (size_t)c.n_mol * c.cap * 4);
+    AL(c.d_cci_slot, (size_t)c.n_mol * c.cap * 4);
+    AL(c.d_y_n, (size_t)c.n_tiles * 4);
+    AL(c.d_y_row, (size_t)c.n_tiles * c.capY * 4);
+    AL(c.d_y_val, (size_t)c.n_tiles * c.capY * kTileVals * ts);
+    AL(c.d_F, (size_t)std::max(c.n_rot_tp, 1) * 256 * ts);
+    AL(c.d_Fdiag_tiles, (size_t)c.n_tiles * 256 * ts);
+    AL(c.d_Fd, (size_t)c.n_mo * 8);
+    AL(c.d_sig, (size_t)std::max(max_ort, 1) * 256 * ts);
+    AL(c.d_scale, (size_t)c.n_mo * 8);
+    AL(c.d_pr_n, (size_t)c.n_gnb * 4);
+    AL(c.d_pr_lvl, (size_t)c.n_gnb * (kMaxSub + 1) * 4);
+    AL(c.d_pr_ij, (size_t)c.n_gnb * kOrthoCap * 2);
+    AL(c.d_pr_cs, (size_t)c.n_gnb * kOrthoCap * 2 * ts);
+    AL(c.d_pr_touch, (size_t)c.n_gnb * 4);
+    AL(c.d_q, (size_t)c.n_atoms * 8);
+    AL(c.d_q_prev, (size_t)c.n_atoms * 8);
+    AL(c.d_dq_in, (size_t)c.n_atoms * 8);
+    AL(c.d_Q_in, (size_t)c.n_atoms * 8);
+    AL(c.d_dq, (size_t)c.n_atoms * 8);
+    AL(c.d_Q, (size_t)c.n_atoms * 8);
+    AL(c.d_e_mol, (size_t)c.n_mol * 8);
+    AL(c.d_red, (size_t)(c.n_mol + 4096) * 8);
+    AL(c.d_sc, sizeof(DeviceScalars));
+#undef AL
+    if (cudaMallocHost((void**)&c.h_sc, sizeof(DeviceScalars)) != cudaSuccess) {
+        cudaGetLastError();
+        c.h_sc = nullptr;
+        return fail(SSCF_ERR_OOM);
+    }
+    if (cudaMemsetAsync(c.d_sc, 0, sizeof(DeviceScalars), c.stream) != cudaSuccess) return fail(SSCF_ERR_CUDA);
+    for (double* p : {c.d_q, c.d_q_prev, c.d_dq_in, c.d_Q_in, c.d_dq, c.d_Q})
+        if (cudaMemsetAsync(p, 0, (size_t)c.n_atoms * 8, c.stream) != cudaSuccess) return fail(SSCF_ERR_CUDA);
+    for (int b = 0; b < 2; ++b)
+        if (cudaMemsetAsync(c.d_c_nt[b], 0, (size_t)c.n_mol * 4, c.stream) != cudaSuccess) return fail(SSCF_ERR_CUDA);
+    if (launch_sk_blocks(&c) != cudaSuccess) return fail(SSCF_ERR_CUDA);
+    if (launch_build_h(&c) != cudaSuccess) return fail(SSCF_ERR_CUDA);
+    if (cudaStreamSynchronize(c.stream) != cudaSuccess) return fail(SSCF_ERR_CUDA);
+    *out = h;
+    return SSCF_OK;
+}
+
+void sscf_destroy(sscf_ctx* h) {
+    if (!h) return;
+    cudaStreamSynchronize(h->c.stream);
+    dev_free_all(&h->c);
+    if (h->c.h_sc) cudaFreeHost(h->c.h_sc);
+    delete h;
+}
+
+int sscf_set_thresholds(sscf_ctx* h, double eps, double dq_tol, double e_tol) {
+    if (!h || !(eps >= 0) || !(dq_tol >= 0) || !(e_tol >= 0)) return SSCF_ERR_INVALID_ARG;
+    h->c.prm.eps = eps;
+    h->c.prm.dq_tol = dq_tol;
+    h->c.prm.e_tol = e_tol;
+    return SSCF_OK;
+}
+
+int sscf_get_dims(const sscf_ctx* h, int* n_ao, int* n_mo, int* n_occ, int* n_groups, int* n_tiles,
+                  int* n_colours) {
+    if (!h) return SSCF_ERR_INVALID_ARG;
+    const Ctx& c = h->c;
+    if (n_ao) *n_ao = c.n_ao;
+    if (n_mo) *n_mo = c.n_mo;
+    if (n_occ) *n_occ = c.n_occ;
+    if (n_groups) *n_groups = c.n_groups;
+    if (n_tiles) *n_tiles = c.n_tiles;
+    if (n_colours) *n_colours = c.n_colours;
+    return SSCF_OK;
+}
+
+int sscf_guess(sscf_ctx* h) {
+    if (!h) return SSCF_ERR_INVALID_ARG;
+    Ctx& c = h->c;
+    CK(cudaMemsetAsync(c.d_sc, 0, sizeof(unsigned), c.stream));
+    CK(launch_guess(&c));
+    CKS(sync_scalars(c));
+    c.have_guess = true;
+    c.have_e_prev = false;
+    c.iteration = 0;
+    return SSCF_OK;
+}
+
+int sscf_build_fock(sscf_ctx* h) {
+    if (!h) return SSCF_ERR_INVALID_ARG;
+    CK(launch_build_h(&h->c));
+    return SSCF_OK;
+}
+
+static int rotate_sweep_async(Ctx& c) {
+    CK(launch_colindex(&c));
+    CK(launch_xc(&c, true, 0, c.n_tiles));
+    CK(launch_transform_rot(&c));
+    CK(launch_select_rot(&c));
+    CK(launch_apply(&c, 0, 0));
+    CK(launch_compact(&c));
+    c.last_sched_kind = 1;
+    return SSCF_OK;
+}
+
+int sscf_rotate_sweep(sscf_ctx* h, int64_t* n_rot_out, double* max_fov_out) {
+    if (!h) return SSCF_ERR_INVALID_ARG;
+    Ctx& c = h->c;
+    if (!c.have_guess) return SSCF_ERR_STATE;
+    CK(cudaMemsetAsync(c.d_sc, 0, offsetof(DeviceScalars, eta), c.stream));
+    CKS(rotate_sweep_async(c));
+    CKS(sync_scalars(c));
+    if (n_rot_out) *n_rot_out = (int64_t)c.h_sc->n_rot;
+    if (max_fov_out) *max_fov_out = c.h_sc->max_fov;
+    return SSCF_OK;
+}
+
+static int ortho_pass_async(Ctx& c, int which, double tol) {
+    const int w = which == SSCF_ORTHO_OCC ? 1 : 0;
+    CK(launch_colindex(&c));
+    CK(launch_xc(&c, false, 0, w == 1 ? c.n_occ_tiles : c.n_tiles));
+    CK(launch_transform_ortho(&c, w));
+    CK(launch_ortho_prepare(&c, w, tol));
+    CK(launch_apply(&c, 1, w));
+    CK(launch_compact(&c));
+    c.last_sched_kind = 2;
+    c.last_ortho_which = w;
+    return SSCF_OK;
+}
+
+int sscf_orthonormalise(sscf_ctx* h, int which, int max_pass, int* passes_out, double* eta_out) {
+    if (!h || (which != SSCF_ORTHO_ALL && which != SSCF_ORTHO_OCC) || max_pass < 1) return SSCF_ERR_INVALID_ARG;
+    Ctx& c = h->c;
+    if (!c.have_guess) return SSCF_ERR_STATE;
+    const double tol = c.prm.eps / 100.0;
+    int k = 0;
+    double eta = 0.0;
+    for (k = 1; k <= max_pass; ++k) {
+        CK(cudaMemsetAsync(c.d_sc, 0, offsetof(DeviceScalars, e_band), c.stream));
+        CKS(ortho_pass_async(c, which, tol));
+        CKS(sync_scalars(c));
+        eta = c.h_sc->eta;
+        if (eta < tol) break;
+    }
+    if (k > max_pass) k = max_pass;
+    if (passes_out) *passes_out = k;
+    if (eta_out) *eta_out = eta;
+    return SSCF_OK;
+}
+
+static int density_async(Ctx& c, bool mix) {
+    CK(launch_density(&c));
+    CK(launch_charges_finish(&c, mix));
+    return SSCF_OK;
+}
+
+static int finish_charges(Ctx& c, double* q_out, double* E_out, double* dq_max_out) {
+    CKS(sync_scalars(c));
+    if (q_out) {
+        CK(cudaMemcpy(q_out, c.d_q_prev, (size_t)c.n_atoms * 8, cudaMemcpyDeviceToHost));
+    }
+    if (!std::isfinite(c.h_sc->energy)) return SSCF_ERR_NONFINITE;
+    if (E_out) *E_out = c.h_sc->energy;
+    if (dq_max_out) *dq_max_out = c.h_sc->dq_max;
+    return SSCF_OK;
+}
+
+int sscf_density(sscf_ctx* h, double* q_out, double* E_out, double* dq_max_out) {
+    if (!h) return SSCF_ERR_INVALID_ARG;
+    Ctx& c = h->c;
+    if (!c.have_guess) return SSCF_ERR_STATE;
+    CK(cudaMemsetAsync(c.d_sc, 0, sizeof(unsigned), c.stream));
+    CKS(density_async(c, true));
+    CKS(finish_charges(c, q_out, E_out, dq_max_out));
+    c.e_prev = c.h_sc->energy;
+    c.have_e_prev = true;
+    return SSCF_OK;
+}
+
+int sscf_reset_charges(sscf_ctx* h, double* E_out) {
+    if (!h) return SSCF_ERR_INVALID_ARG;
+    Ctx& c = h->c;
+    if (!c.have_guess) return SSCF_ERR_STATE;
+    CK(cudaMemsetAsync(c.d_sc, 0, sizeof(unsigned), c.stream));
+    CKS(density_async(c, false));
+    CKS(finish_charges(c, nullptr, E_out, nullptr));
+    c.e_prev = c.h_sc->energy;
+    c.have_e_prev = true;
+    return SSCF_OK;
+}
+
+int sscf_step(sscf_ctx* h, sscf_step_info* info) {
+    if (!h) return SSCF_ERR_INVALID_ARG;
+    Ctx& c = h->c;
+    if (!c.have_guess) return SSCF_ERR_STATE;
+    CK(cudaMemsetAsync(c.d_sc, 0, offsetof(DeviceScalars, hist), c.stream));
+    CK(launch_build_h(&c));
+    CKS(rotate_sweep_async(c));
+    unsigned long long n_rot_dummy = 0;
+    (void)n_rot_dummy;
+    if (c.prm.ortho_every) CKS(ortho_pass_async(c, SSCF_ORTHO_OCC, c.prm.eps / 100.0));
+    CKS(density_async(c, true));
+    CKS(sync_scalars(c));
+    c.iteration++;
+    if (info) {
+        info->energy = c.h_sc->energy;
+        info->dq_max = c.h_sc->dq_max;
+        info->dE = c.have_e_prev ? c.h_sc->energy - c.e_prev : c.h_sc->energy;
+        info->max_fov = c.h_sc->max_fov;
+        info->eta = c.h_sc->eta;
+        info->n_rot = (int64_t)c.h_sc->n_rot;
+        info->n_combo = (int64_t)c.h_sc->n_combo;
+        long long tiles = 0;
+        std::vector<int> nt(c.n_mol);
+        CK(cudaMemcpy(nt.data(), c.d_c_nt[c.cur], (size_t)c.n_mol * 4, cudaMemcpyDeviceToHost));
+        for (int v : nt) tiles += v;
+        info->nnz_c = (int64_t)tiles * kTileVals;
+        info->iteration = c.iteration;
+    }
+    if (!std::isfinite(c.h_sc->energy)) return SSCF_ERR_NONFINITE;
+    c.e_prev = c.h_sc->energy;
+    c.have_e_prev = true;
+    return SSCF_OK;
+}
+
+int sscf_run(sscf_ctx* h, sscf_step_info* info) {
+    if (!h) return SSCF_ERR_INVALID_ARG;
+    Ctx& c = h->c;
+    const double eps_u = c.prm.eps, dq_u = c.prm.dq_tol, e_u = c.prm.e_tol;
+    CKS(sscf_guess(h));
+    struct Stage {
+        double eps, dq, e;
+    } stages[2] = {{1e-3, 1e-1, INFINITY}, {eps_u, dq_u, e_u}};
+    sscf_step_info last{};
+    bool converged = false;
+    for (int s = 0; s < 2; ++s) {
+        c.prm.eps = stages[s].eps;
+        CKS(sscf_orthonormalise(h, SSCF_ORTHO_ALL, 200, nullptr, nullptr));
+        if (s == 0) CKS(sscf_reset_charges(h, nullptr));
+        converged = false;
+        for (int it = 0; it < c.prm.max_scc; ++it) {
+            CKS(sscf_step(h, &last));
+            if (last.dq_max <= stages[s].dq && std::fabs(last.dE) <= stages[s].e) {
+                converged = true;
+                break;
+            }
+        }
+    }
+    c.prm.eps = eps_u;
+    c.prm.dq_tol = dq_u;
+    c.prm.e_tol = e_u;
+    CKS(sscf_orthonormalise(h, SSCF_ORTHO_OCC, 200, nullptr, nullptr));
+    double E = 0.0;
+    CK(cudaMemsetAsync(c.d_sc, 0, sizeof(unsigned), c.stream));
+    CKS(density_async(c, false));
+    CKS(finish_charges(c, nullptr, &E, nullptr));
+    last.energy = E;
+    if (info) *info = last;
+    return converged ? SSCF_OK : SSCF_ERR_NOT_CONVERGED;
+}
+
+}  // extern "C"

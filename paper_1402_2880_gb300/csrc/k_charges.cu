@@ -1,0 +1,71 @@
+// Charge update of one SCC iteration: dq = q - q0, Q = gamma dq, the
+// energy E = sum P*H0 + 1/2 dq^T Q, delta q_max = max |q - q_prev|
+// (Section "Sparsity and numerical accuracy") and linear charge mixing.
+#include "sscf_internal.h"
+
+namespace sscf {
+
+namespace {
+
+__global__ void k_dq(int n, const double* __restrict__ q, const int* __restrict__ species, double q0O, double q0H,
+                     double* __restrict__ dq) {
+    int a = blockIdx.x * blockDim.x + threadIdx.x;
+    if (a < n) dq[a] = q[a] - (species[a] == 0 ? q0O : q0H);
+}
+
+// One CTA: fixed-order reductions (deterministic) and the mixing update.
+__global__ void k_finish(int n_atoms, int n_mol, int mix, double beta, const double* __restrict__ e_mol,
+                         double* __restrict__ q, double* __restrict__ q_prev, const double* __restrict__ dq,
+                         const double* __restrict__ Q, double* __restrict__ dq_in, double* __restrict__ Q_in,
+                         DeviceScalars* sc) {
+    __shared__ double s_band[1024], s_coul[1024], s_max[1024];
+    double band = 0.0, coul = 0.0, mx = 0.0;
+    for (int m = threadIdx.x; m < n_mol; m += blockDim.x) band += e_mol[m];
+    for (int a = threadIdx.x; a < n_atoms; a += blockDim.x) {
+        coul += dq[a] * Q[a];
+        mx = fmax(mx, fabs(q[a] - q_prev[a]));
+    }
+    s_band[threadIdx.x] = band;
+    s_coul[threadIdx.x] = coul;
+    s_max[threadIdx.x] = mx;
+    __syncthreads();
+    for (int off = blockDim.x / 2; off > 0; off >>= 1) {
+        if ((int)threadIdx.x < off) {
+            s_band[threadIdx.x] += s_band[threadIdx.x + off];
+            s_coul[threadIdx.x] += s_coul[threadIdx.x + off];
+            s_max[threadIdx.x] = fmax(s_max[threadIdx.x], s_max[threadIdx.x + off]);
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        sc->e_band = s_band[0];
+        sc->e_coul = 0.5 * s_coul[0];
+        sc->energy = s_band[0] + 0.5 * s_coul[0];
+        sc->dq_max = s_max[0];
+        if (!isfinite(sc->energy)) atomicOr(&sc->err, kErrNonFinite);
+    }
+    for (int a = threadIdx.x; a < n_atoms; a += blockDim.x) {
+        q_prev[a] = q[a];
+        if (mix) {
+            dq_in[a] = dq_in[a] + beta * (dq[a] - dq_in[a]);
+            Q_in[a] = Q_in[a] + beta * (Q[a] - Q_in[a]);
+        } else {
+            dq_in[a] = dq[a];
+            Q_in[a] = Q[a];
+        }
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_charges_finish(Ctx* c, bool mix) {
+    k_dq<<<(c->n_atoms + 255) / 256, 256, 0, c->stream>>>(c->n_atoms, c->d_q, c->d_species, c->prm.q0[0],
+                                                         c->prm.q0[1], c->d_dq);
+    cudaError_t e = launch_gamma(c, c->d_dq, c->d_Q);
+    if (e != cudaSuccess) return e;
+    k_finish<<<1, 1024, 0, c->stream>>>(c->n_atoms, c->n_mol, mix ? 1 : 0, c->prm.mix_beta, c->d_e_mol, c->d_q,
+                                        c->d_q_prev, c->d_dq, c->d_Q, c->d_dq_in, c->d_Q_in, c->d_sc);
+    return cudaGetLastError();
+}
+
+}  // namespace sscf

@@ -1,0 +1,499 @@
+// Sparse products of the C^T X C kernel (Section "Computation kernel for the
+// matrix products C^T X C") and the density / Mulliken charges (Eq. pop).
+//
+// The paper builds C^T X C from 16-column strips of X C computed with dense
+// 16x16 blocks. Here the 16-column strip is a tile: Y = X C is formed per
+// tile column (column-major, only the row blocks reachable through X), and
+// every kept block of C^T X C is one output-stationary 16x16 tile pair
+// reduced over the row blocks the two columns share.
+#include "sscf_internal.h"
+
+namespace sscf {
+
+namespace {
+
+template <typename T> struct Acc;
+template <> struct Acc<double> { using type = double; };
+template <> struct Acc<float> { using type = float; };
+
+// ---------------------------------------------------------------------------
+// Column index of C: per tile, the (row block, slot) pairs sorted by row.
+// ---------------------------------------------------------------------------
+__global__ void k_ci_count(int n_mol, int cap, const int* __restrict__ c_nt, const int* __restrict__ c_tile,
+                           int* __restrict__ cnt) {
+    int r = blockIdx.x;
+    for (int s = threadIdx.x; s < c_nt[r]; s += blockDim.x) atomicAdd(&cnt[c_tile[(size_t)r * cap + s]], 1);
+}
+
+// exclusive scan of n counts into ptr (n + 1 entries); one CTA of 1024 threads
+__global__ void k_scan(int n, const int* __restrict__ cnt, int* __restrict__ ptr) {
+    __shared__ int part[1024];
+    const int per = (n + blockDim.x - 1) / blockDim.x;
+    const int lo = threadIdx.x * per, hi = min(n, lo + per);
+    int s = 0;
+    for (int i = lo; i < hi; ++i) s += cnt[i];
+    part[threadIdx.x] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int run = 0;
+        for (int i = 0; i < (int)blockDim.x; ++i) {
+            int v = part[i];
+            part[i] = run;
+            run += v;
+        }
+        ptr[n] = run;
+    }
+    __syncthreads();
+    int run = part[threadIdx.x];
+    for (int i = lo; i < hi; ++i) {
+        ptr[i] = run;
+        run += cnt[i];
+    }
+}
+
+__global__ void k_ci_fill(int n_mol, int cap, const int* __restrict__ c_nt, const int* __restrict__ c_tile,
+                          const int* __restrict__ ptr, int* __restrict__ cursor, int* __restrict__ row,
+                          int* __restrict__ slot) {
+    int r = blockIdx.x;
+    for (int s = threadIdx.x; s < c_nt[r]; s += blockDim.x) {
+        int t = c_tile[(size_t)r * cap + s];
+        int pos = ptr[t] + atomicAdd(&cursor[t], 1);
+        row[pos] = r;
+        slot[pos] = s;
+    }
+}
+
+// Sort every tile's segment by row (bitonic sort in shared memory).
+constexpr int kSortMax = 8192;
+__global__ void k_ci_sort(const int* __restrict__ ptr, int* __restrict__ row, int* __restrict__ slot,
+                          unsigned* __restrict__ err) {
+    extern __shared__ unsigned long long keys[];
+    const int t = blockIdx.x;
+    const int lo = ptr[t], n = ptr[t + 1] - lo;
+    if (n <= 1) return;
+    if (n > kSortMax) {
+        if (threadIdx.x == 0) atomicOr(err, kErrSortSize);
+        return;
+    }
+    int np = 1;
+    while (np < n) np <<= 1;
+    for (int i = threadIdx.x; i < np; i += blockDim.x)
+        keys[i] = i < n ? ((unsigned long long)(unsigned)row[lo + i] << 32) | (unsigned)slot[lo + i]
+                        : ~0ull;
+    __syncthreads();
+    for (int k = 2; k <= np; k <<= 1)
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int i = threadIdx.x; i < np; i += blockDim.x) {
+                int l = i ^ j;
+                if (l > i) {
+                    bool up = (i & k) == 0;
+                    unsigned long long a = keys[i], b = keys[l];
+                    if ((a > b) == up) {
+                        keys[i] = b;
+                        keys[l] = a;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        row[lo + i] = (int)(keys[i] >> 32);
+        slot[lo + i] = (int)(keys[i] & 0xffffffffu);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Y[:, t] = X C[:, t] for tiles t in [tile_lo, tile_hi), column-major output.
+// One CTA per tile: mark the row blocks reachable from the tile's rows
+// through the molecule-pair pattern, then one warp per output row block sums
+// X[r, n] (6x6) C[n, t] (6x16) over the pattern neighbours n holding t.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void k_xc(int tile_lo, int n_mol, int cap, int capY, const int* __restrict__ cci_ptr,
+                     const int* __restrict__ cci_row, const int* __restrict__ cci_slot,
+                     const T* __restrict__ c_val, const int* __restrict__ mp_ptr, const int* __restrict__ mp_col,
+                     const T* __restrict__ Xb, int* __restrict__ y_n, int* __restrict__ y_row,
+                     T* __restrict__ y_val, unsigned* __restrict__ err) {
+    extern __shared__ int sm[];
+    int* rowpos = sm;                            // n_mol: index into the tile's column list or -1
+    unsigned* bits = (unsigned*)(sm + n_mol);    // n_mol bits
+    int* wpre = (int*)(bits + (n_mol + 31) / 32);  // prefix of popcounts per word
+    __shared__ int s_total;
+    const int t = tile_lo + blockIdx.x;
+    const int lo = cci_ptr[t], nc = cci_ptr[t + 1] - lo;
+    const int nw = (n_mol + 31) / 32;
+    for (int i = threadIdx.x; i < n_mol; i += blockDim.x) rowpos[i] = -1;
+    for (int i = threadIdx.x; i < nw; i += blockDim.x) bits[i] = 0u;
+    __syncthreads();
+    for (int k = threadIdx.x; k < nc; k += blockDim.x) rowpos[cci_row[lo + k]] = k;
+    for (int k = threadIdx.x; k < nc; k += blockDim.x) {
+        int r = cci_row[lo + k];
+        for (int e = mp_ptr[r]; e < mp_ptr[r + 1]; ++e) {
+            int n = mp_col[e];
+            atomicOr(&bits[n >> 5], 1u << (n & 31));
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int run = 0;
+        for (int w = 0; w < nw; ++w) {
+            wpre[w] = run;
+            run += __popc(bits[w]);
+        }
+        s_total = run;
+    }
+    __syncthreads();
+    const int ny = s_total;
+    if (ny > capY) {
+        if (threadIdx.x == 0) {
+            atomicOr(err, kErrCapacity);
+            y_n[t] = 0;
+        }
+        return;
+    }
+    if (threadIdx.x == 0) y_n[t] = ny;
+    // write sorted row list
+    for (int w = threadIdx.x; w < nw; w += blockDim.x) {
+        unsigned b = bits[w];
+        int p = wpre[w];
+        while (b) {
+            int i = __ffs(b) - 1;
+            b &= b - 1;
+            y_row[(size_t)t * capY + p++] = w * 32 + i;
+        }
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const int col = lane & 15, r0 = lane >> 4;   // rows r0, r0+2, r0+4
+    using A = typename Acc<T>::type;
+    for (int k = warp; k < ny; k += nwarps) {
+        const int r = y_row[(size_t)t * capY + k];
+        A acc0 = 0, acc1 = 0, acc2 = 0;
+        for (int e = mp_ptr[r]; e < mp_ptr[r + 1]; ++e) {
+            const int n = mp_col[e];
+            const int j = rowpos[n];
+            if (j < 0) continue;
+            const T* cv = c_val + ((size_t)n * cap + cci_slot[lo + j]) * kTileVals + col;
+            const T* xb = Xb + (size_t)e * 36;
+            A c6[6];
+#pragma unroll
+            for (int q = 0; q < 6; ++q) c6[q] = (A)cv[q * kTileW];
+#pragma unroll
+            for (int q = 0; q < 6; ++q) {
+                acc0 += (A)xb[(r0)*6 + q] * c6[q];
+                acc1 += (A)xb[(r0 + 2) * 6 + q] * c6[q];
+                acc2 += (A)xb[(r0 + 4) * 6 + q] * c6[q];
+            }
+        }
+        T* yv = y_val + ((size_t)t * capY + k) * kTileVals;
+        yv[(r0)*kTileW + col] = (T)acc0;
+        yv[(r0 + 2) * kTileW + col] = (T)acc1;
+        yv[(r0 + 4) * kTileW + col] = (T)acc2;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Tile-pair transform: out[p] (16x16) = C[:, a]^T Y[:, b] for every listed
+// pair (a, b). One CTA per tile a; a shared map row block -> slot of a; one
+// warp per pair walks b's rows (sorted) and accumulates the rows present in
+// a (ascending row order, fixed sum order).
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void k_transform(int n_mol, int cap, int capY, const int* __restrict__ tp_ptr,
+                            const int* __restrict__ tp_b, const int* __restrict__ tp_out,
+                            const int* __restrict__ cci_ptr, const int* __restrict__ cci_row,
+                            const int* __restrict__ cci_slot, const T* __restrict__ c_val,
+                            const int* __restrict__ y_n, const int* __restrict__ y_row,
+                            const T* __restrict__ y_val, T* __restrict__ out) {
+    extern __shared__ int slot_of[];   // n_mol
+    const int a = blockIdx.x;
+    const int p0 = tp_ptr[a], p1 = tp_ptr[a + 1];
+    if (p0 == p1) return;
+    const int lo = cci_ptr[a], nc = cci_ptr[a + 1] - lo;
+    for (int i = threadIdx.x; i < n_mol; i += blockDim.x) slot_of[i] = -1;
+    __syncthreads();
+    for (int k = threadIdx.x; k < nc; k += blockDim.x) slot_of[cci_row[lo + k]] = cci_slot[lo + k];
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const int i = lane >> 1, j0 = (lane & 1) * 8;
+    using A = typename Acc<T>::type;
+    for (int p = p0 + warp; p < p1; p += nwarps) {
+        const int b = tp_b[p];
+        const int nb = y_n[b];
+        double accd[8];
+        A acc[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            acc[q] = 0;
+            accd[q] = 0.0;
+        }
+        for (int k0 = 0; k0 < nb; k0 += 32) {
+            int k = k0 + lane;
+            int s = -1;
+            if (k < nb) s = slot_of[y_row[(size_t)b * capY + k]];
+            unsigned m = __ballot_sync(0xffffffffu, s >= 0);
+            while (m) {
+                const int src = __ffs(m) - 1;
+                m &= m - 1;
+                const int ss = __shfl_sync(0xffffffffu, s, src);
+                const int rr = __shfl_sync(0xffffffffu, k, src);
+                const int r = y_row[(size_t)b * capY + rr];
+                const T* cv = c_val + ((size_t)r * cap + ss) * kTileVals;
+                const T* yv = y_val + ((size_t)b * capY + rr) * kTileVals;
+#pragma unroll
+                for (int q = 0; q < 6; ++q) {
+                    A ci = (A)cv[q * kTileW + i];
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) acc[u] += ci * (A)yv[q * kTileW + j0 + u];
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                accd[u] += (double)acc[u];
+                acc[u] = 0;
+            }
+        }
+        T* o = out + (size_t)tp_out[p] * 256 + i * 16 + j0;
+#pragma unroll
+        for (int u = 0; u < 8; ++u) o[u] = (T)accd[u];
+    }
+}
+
+// diag(F) per MO from the diagonal tile pairs
+template <typename T>
+__global__ void k_extract_diag(int n_tiles, const int* __restrict__ tile_mo0, const int* __restrict__ tile_nmo,
+                               const T* __restrict__ Ft, double* __restrict__ Fd) {
+    int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= n_tiles * 16) return;
+    int t = idx >> 4, c = idx & 15;
+    if (c < tile_nmo[t]) Fd[tile_mo0[t] + c] = (double)Ft[(size_t)t * 256 + c * 17];
+}
+
+// ---------------------------------------------------------------------------
+// Density: P_mn = 2 sum_{occ tiles t in rows m and n} C[m,t] C[n,t]^T on the
+// molecule-pair pattern; q_a += sum_{mu in a} sum_nu P_mu,nu S_mu,nu and the
+// band energy sum P*H0 per molecule (Eq. pop). One CTA per row block m, one
+// warp per neighbour n, results combined in neighbour order.
+// ---------------------------------------------------------------------------
+constexpr int kDensWarps = 8;
+constexpr int kDensFlush = 8;   // tiles per lane between FP64 flushes
+template <typename T>
+__global__ void __launch_bounds__(kDensWarps * 32)
+k_density(int n_occ_tiles, int cap, const int* __restrict__ c_nt, const int* __restrict__ c_tile,
+          const T* __restrict__ c_val, const int* __restrict__ mp_ptr, const int* __restrict__ mp_col,
+          const double* __restrict__ H0b, const double* __restrict__ Sb, double* __restrict__ q,
+          double* __restrict__ e_mol) {
+    extern __shared__ int smap[];   // n_occ_tiles: slot of tile in row m or -1
+    __shared__ double part[kDensWarps][4];
+    const int m = blockIdx.x;
+    for (int i = threadIdx.x; i < n_occ_tiles; i += blockDim.x) smap[i] = -1;
+    __syncthreads();
+    const int ntm = c_nt[m];
+    for (int s = threadIdx.x; s < ntm; s += blockDim.x) {
+        int t = c_tile[(size_t)m * cap + s];
+        if (t < n_occ_tiles) smap[t] = s;
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int e0 = mp_ptr[m], ne = mp_ptr[m + 1] - e0;
+    using A = typename Acc<T>::type;
+    const int col = lane & 15, half = lane >> 4;
+    double wq[3] = {0, 0, 0}, we = 0.0;
+    for (int w = warp; w < ne; w += kDensWarps) {
+        const int e = e0 + w;
+        const int n = mp_col[e];
+        double accd[36];
+        A acc[36];
+#pragma unroll
+        for (int u = 0; u < 36; ++u) {
+            accd[u] = 0.0;
+            acc[u] = 0;
+        }
+        const int ntn = c_nt[n];
+        int since = 0;
+        for (int s = half; s < ntn; s += 2) {
+            const int t = c_tile[(size_t)n * cap + s];
+            if (t >= n_occ_tiles) break;   // tiles are sorted: occupied tiles first
+            const int sm_ = smap[t];
+            if (sm_ < 0) continue;
+            const T* cm = c_val + ((size_t)m * cap + sm_) * kTileVals + col;
+            const T* cn = c_val + ((size_t)n * cap + s) * kTileVals + col;
+            A a6[6], b6[6];
+#pragma unroll
+            for (int k = 0; k < 6; ++k) {
+                a6[k] = (A)cm[k * kTileW];
+                b6[k] = (A)cn[k * kTileW];
+            }
+#pragma unroll
+            for (int k = 0; k < 6; ++k)
+#pragma unroll
+                for (int l = 0; l < 6; ++l) acc[k * 6 + l] += a6[k] * b6[l];
+            if (++since == kDensFlush) {
+                since = 0;
+#pragma unroll
+                for (int u = 0; u < 36; ++u) {
+                    accd[u] += (double)acc[u];
+                    acc[u] = 0;
+                }
+            }
+        }
+        // reduce the 36 partial products over the 32 lanes
+        double qa[3] = {0, 0, 0}, eb = 0.0;
+#pragma unroll
+        for (int u = 0; u < 36; ++u) {
+            double v = accd[u] + (double)acc[u];
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+            const double P = 2.0 * v;
+            const int k = u / 6;
+            const int atom = k < 4 ? 0 : k - 3;
+            qa[atom] += P * Sb[(size_t)e * 36 + u];
+            eb += P * H0b[(size_t)e * 36 + u];
+        }
+        wq[0] += qa[0];
+        wq[1] += qa[1];
+        wq[2] += qa[2];
+        we += eb;
+    }
+    if (lane == 0) {
+        part[warp][0] = wq[0];
+        part[warp][1] = wq[1];
+        part[warp][2] = wq[2];
+        part[warp][3] = we;
+    }
+    __syncthreads();
+    if (threadIdx.x < 4) {
+        double s = 0.0;
+        for (int w = 0; w < kDensWarps; ++w) s += part[w][threadIdx.x];
+        if (threadIdx.x < 3)
+            q[3 * m + threadIdx.x] = s;
+        else
+            e_mol[m] = s;
+    }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------
+static cudaError_t ensure_attrs();
+
+cudaError_t launch_colindex(Ctx* c) {
+    cudaError_t ea = ensure_attrs();
+    if (ea != cudaSuccess) return ea;
+    const int b = c->cur;
+    cudaMemsetAsync(c->d_cci_cnt, 0, (size_t)c->n_tiles * 4, c->stream);
+    k_ci_count<<<c->n_mol, 128, 0, c->stream>>>(c->n_mol, c->cap, c->d_c_nt[b], c->d_c_tile[b], c->d_cci_cnt);
+    k_scan<<<1, 1024, 0, c->stream>>>(c->n_tiles, c->d_cci_cnt, c->d_cci_ptr);
+    cudaMemsetAsync(c->d_cci_cnt, 0, (size_t)c->n_tiles * 4, c->stream);
+    k_ci_fill<<<c->n_mol, 128, 0, c->stream>>>(c->n_mol, c->cap, c->d_c_nt[b], c->d_c_tile[b], c->d_cci_ptr,
+                                               c->d_cci_cnt, c->d_cci_row, c->d_cci_slot);
+    k_ci_sort<<<c->n_tiles, 512, kSortMax * 8, c->stream>>>(c->d_cci_ptr, c->d_cci_row, c->d_cci_slot,
+                                                            &c->d_sc->err);
+    return cudaGetLastError();
+}
+
+static bool g_attr_done = false;
+
+template <typename T>
+static cudaError_t set_attrs() {
+    cudaError_t e;
+    e = cudaFuncSetAttribute(k_ci_sort, cudaFuncAttributeMaxDynamicSharedMemorySize, kSortMax * 8);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k_xc<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k_transform<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k_density<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
+    return e;
+}
+
+static cudaError_t ensure_attrs() {
+    if (g_attr_done) return cudaSuccess;
+    cudaError_t e = set_attrs<double>();
+    if (e != cudaSuccess) return e;
+    e = set_attrs<float>();
+    if (e == cudaSuccess) g_attr_done = true;
+    return e;
+}
+
+cudaError_t launch_xc(Ctx* c, bool use_h, int tile_lo, int tile_hi) {
+    cudaError_t e = ensure_attrs();
+    if (e != cudaSuccess) return e;
+    const int b = c->cur;
+    const int n = tile_hi - tile_lo;
+    if (n <= 0) return cudaSuccess;
+    const size_t smem = (size_t)c->n_mol * 4 + (size_t)((c->n_mol + 31) / 32) * 8 + 64;
+    if (smem > 200 * 1024) return cudaErrorInvalidValue;
+    if (c->prec == SSCF_FP64)
+        k_xc<double><<<n, 256, smem, c->stream>>>(tile_lo, c->n_mol, c->cap, c->capY, c->d_cci_ptr, c->d_cci_row,
+                                                  c->d_cci_slot, (const double*)c->d_c_val[b], c->d_mp_ptr,
+                                                  c->d_mp_col, (const double*)(use_h ? c->d_Hb : c->d_Sbt),
+                                                  c->d_y_n, c->d_y_row, (double*)c->d_y_val, &c->d_sc->err);
+    else
+        k_xc<float><<<n, 256, smem, c->stream>>>(tile_lo, c->n_mol, c->cap, c->capY, c->d_cci_ptr, c->d_cci_row,
+                                                 c->d_cci_slot, (const float*)c->d_c_val[b], c->d_mp_ptr,
+                                                 c->d_mp_col, (const float*)(use_h ? c->d_Hb : c->d_Sbt),
+                                                 c->d_y_n, c->d_y_row, (float*)c->d_y_val, &c->d_sc->err);
+    return cudaGetLastError();
+}
+
+template <typename T>
+static cudaError_t transform_t(Ctx* c, const int* ptr, const int* bl, const int* outl, void* out) {
+    const size_t smem = (size_t)c->n_mol * 4;
+    k_transform<T><<<c->n_tiles, 256, smem, c->stream>>>(c->n_mol, c->cap, c->capY, ptr, bl, outl, c->d_cci_ptr,
+                                                         c->d_cci_row, c->d_cci_slot, (const T*)c->d_c_val[c->cur],
+                                                         c->d_y_n, c->d_y_row, (const T*)c->d_y_val, (T*)out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_transform_rot(Ctx* c) {
+    cudaError_t e = ensure_attrs();
+    if (e != cudaSuccess) return e;
+    if ((size_t)c->n_mol * 4 > 200 * 1024) return cudaErrorInvalidValue;
+    if (c->prec == SSCF_FP64) {
+        e = transform_t<double>(c, c->d_rot_tp_ptr, c->d_rot_tp_b, c->d_rot_tp_out, c->d_F);
+        if (e == cudaSuccess)
+            e = transform_t<double>(c, c->d_diag_tp_ptr, c->d_diag_tp_b, c->d_diag_tp_out, c->d_Fdiag_tiles);
+        if (e == cudaSuccess)
+            k_extract_diag<double><<<(c->n_tiles * 16 + 255) / 256, 256, 0, c->stream>>>(
+                c->n_tiles, c->d_tile_mo0, c->d_tile_nmo, (const double*)c->d_Fdiag_tiles, c->d_Fd);
+    } else {
+        e = transform_t<float>(c, c->d_rot_tp_ptr, c->d_rot_tp_b, c->d_rot_tp_out, c->d_F);
+        if (e == cudaSuccess)
+            e = transform_t<float>(c, c->d_diag_tp_ptr, c->d_diag_tp_b, c->d_diag_tp_out, c->d_Fdiag_tiles);
+        if (e == cudaSuccess)
+            k_extract_diag<float><<<(c->n_tiles * 16 + 255) / 256, 256, 0, c->stream>>>(
+                c->n_tiles, c->d_tile_mo0, c->d_tile_nmo, (const float*)c->d_Fdiag_tiles, c->d_Fd);
+    }
+    if (e != cudaSuccess) return e;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_transform_ortho(Ctx* c, int w) {
+    cudaError_t e = ensure_attrs();
+    if (e != cudaSuccess) return e;
+    if (c->prec == SSCF_FP64)
+        return transform_t<double>(c, c->d_ort_tp_ptr[w], c->d_ort_tp_b[w], c->d_ort_tp_out[w], c->d_sig);
+    return transform_t<float>(c, c->d_ort_tp_ptr[w], c->d_ort_tp_b[w], c->d_ort_tp_out[w], c->d_sig);
+}
+
+cudaError_t launch_density(Ctx* c) {
+    cudaError_t e = ensure_attrs();
+    if (e != cudaSuccess) return e;
+    const size_t smem = (size_t)c->n_occ_tiles * 4;
+    if (smem > 160 * 1024) return cudaErrorInvalidValue;
+    const int b = c->cur;
+    if (c->prec == SSCF_FP64)
+        k_density<double><<<c->n_mol, kDensWarps * 32, smem, c->stream>>>(c->n_occ_tiles, c->cap, c->d_c_nt[b], c->d_c_tile[b],
+                                                              (const double*)c->d_c_val[b], c->d_mp_ptr,
+                                                              c->d_mp_col, c->d_H0b, c->d_Sb, c->d_q, c->d_e_mol);
+    else
+        k_density<float><<<c->n_mol, kDensWarps * 32, smem, c->stream>>>(c->n_occ_tiles, c->cap, c->d_c_nt[b], c->d_c_tile[b],
+                                                             (const float*)c->d_c_val[b], c->d_mp_ptr, c->d_mp_col,
+                                                             c->d_H0b, c->d_Sb, c->d_q, c->d_e_mol);
+    return cudaGetLastError();
+}
+
+}  // namespace sscf

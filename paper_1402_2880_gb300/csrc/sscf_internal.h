@@ -1,0 +1,229 @@
+// Internal state and kernel launchers of libsscf.
+//
+// Data layout in HBM (one context = one cluster):
+//   * row block      = one molecule = 6 AO rows (O s, px, py, pz, H1 s, H2 s);
+//   * tile           = 16 consecutive MOs of one group's occupied (or virtual)
+//                      list; occupied tiles come first (group-major), then
+//                      the virtual tiles;
+//   * C (MO coefficients) is stored row-major by row block: row block r holds
+//     c_nt[r] tiles, ids sorted ascending in c_tile[r*cap + s], values
+//     c_val[((r*cap + s)*6 + k)*16 + col] for AO row k of the molecule. The
+//     paper's list-of-lists columns padded to s_m (Section "Sparse storage")
+//     become rows padded to `cap` tiles: rotations are row-local, so a row is
+//     the unit that grows and shrinks.
+//   * H0, S, H are stored as dense 6x6 blocks on the molecule-pair pattern
+//     (any atom pair within r_cut), CSR over the first molecule.
+//   * the column index of C lists, per tile, the row blocks holding it
+//     (sorted) and the slot inside each row.
+//   * Y = X C (X = H or S) is stored column-major by tile: y_row[t*capY+k],
+//     values y_val[((t*capY + k)*6 + row)*16 + col].
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/sscf.h"
+
+namespace sscf {
+
+constexpr int kAoPerMol = 6;
+constexpr int kTileW = 16;
+constexpr int kTileVals = kAoPerMol * kTileW;  // 96
+constexpr int kMaxSub = 48;                    // in-block colours (<= MOs per group side)
+constexpr int kRotCap = 32 * 16;               // pairs of one occupied-virtual block
+constexpr int kOrthoCap = 48 * 48;             // pairs of one orthonormalisation block
+
+// Error word bits set by kernels (read back by the host after a step).
+enum : unsigned {
+    kErrCapacity = 1u,       // a row of C or a column of Y ran out of slots
+    kErrSortSize = 2u,       // a column segment exceeded the in-smem sort size
+    kErrNonFinite = 4u,      // NaN / Inf produced
+    kErrGuess = 8u,          // per-molecule eigensolve failed (S not positive definite)
+};
+
+struct DeviceScalars {
+    unsigned err;
+    unsigned long long cand;      // candidate rotation pairs |F| >= tau
+    unsigned long long n_rot;     // rotations kept
+    unsigned long long n_combo;   // ortho combinations kept
+    unsigned long long thr_key;   // bit pattern of the smallest kept |F| (double)
+    unsigned long long sel_prefix;
+    unsigned long long sel_mask;
+    unsigned long long sel_k;     // rank still to find inside the prefix
+    double max_fov;               // bits via atomicMax on the double's pattern
+    double eta;
+    double e_band;
+    double e_coul;
+    double dq_max;
+    double energy;
+    unsigned long long hist[256];
+};
+
+struct Ctx {
+    sscf_params prm;
+    cudaStream_t stream = nullptr;
+    int prec = SSCF_FP64;
+    size_t tsize = 8;  // bytes of one stored C / H / Y value
+
+    // sizes
+    int n_atoms = 0, n_mol = 0, n_ao = 0, n_occ = 0, n_mo = 0;
+    int n_groups = 0, n_tiles = 0, n_occ_tiles = 0, n_colours = 0;
+    int n_mp = 0;        // molecule-pair blocks, including (m, m)
+    int n_gnb = 0;       // group-graph entries (directed, including (A, A))
+    int cap = 0;         // tiles per row block of C
+    int capY = 0;        // row blocks per tile of Y
+    bool have_guess = false;
+    int iteration = 0;
+    double e_prev = 0.0;
+    bool have_e_prev = false;
+    int last_sched_kind = 0;   // 0 none, 1 rotations, 2 combinations
+    int last_ortho_which = 0;
+
+    // host copies of the structure
+    std::vector<int> h_species;
+    std::vector<double> h_xyz;
+    std::vector<int> h_mol_group, h_mol_local;
+    std::vector<int> h_mp_ptr, h_mp_col;
+    std::vector<int> h_group_nmol, h_group_occ0, h_group_virt0;
+    std::vector<int> h_group_ot0, h_group_not, h_group_vt0, h_group_nvt;
+    std::vector<int> h_tile_group, h_tile_kind, h_tile_loc0, h_tile_nmo, h_tile_mo0;
+    std::vector<int> h_gnb_ptr, h_gnb_col, h_gnb_row, h_gnb_colour;
+    std::vector<int> h_colour_ptr, h_colour_blk;        // all directed blocks by colour
+    std::vector<int> h_ocolour_ptr, h_ocolour_blk;      // blocks with A <= B by colour
+    // tile-pair lists of the transforms
+    std::vector<int> h_rot_tp_ptr;   // per a-tile CSR into (b, out) for the F_ov blocks
+    std::vector<int> h_rot_tp_b, h_rot_tp_out;
+    std::vector<int> h_rot_blk_tp0;  // first tile pair of every directed block
+    int n_rot_tp = 0;
+
+    // device: geometry and model
+    double* d_xyz = nullptr;
+    int* d_species = nullptr;
+    int* d_mp_ptr = nullptr;
+    int* d_mp_col = nullptr;
+    int* d_mp_row = nullptr;
+    double* d_H0b = nullptr;
+    double* d_Sb = nullptr;
+    void* d_Hb = nullptr;       // T
+    void* d_Sbt = nullptr;      // S in T precision (for S C in mixed mode)
+
+    // device: groups, tiles, group graph
+    int* d_mol_group = nullptr;
+    int* d_mol_local = nullptr;
+    int* d_group_nmol = nullptr;
+    int* d_group_ot0 = nullptr;
+    int* d_group_not = nullptr;
+    int* d_group_vt0 = nullptr;
+    int* d_group_nvt = nullptr;
+    int* d_group_occ0_mo = nullptr;   // global index of the group's first occupied MO
+    int* d_group_virt0_mo = nullptr;  // global index of the group's first virtual MO
+    int* d_self_blk = nullptr;        // group-graph entry of (g, g)
+    std::vector<int> h_self_blk;
+    int* d_tile_group = nullptr;
+    int* d_tile_kind = nullptr;
+    int* d_tile_loc0 = nullptr;
+    int* d_tile_nmo = nullptr;
+    int* d_tile_mo0 = nullptr;
+    int* d_gnb_row = nullptr;
+    int* d_gnb_col = nullptr;
+    int* d_colour_ptr = nullptr;
+    int* d_colour_blk = nullptr;
+    int* d_ocolour_ptr = nullptr;
+    int* d_ocolour_blk = nullptr;
+
+    // device: C (two buffers), its column index
+    int* d_c_nt[2] = {nullptr, nullptr};
+    int* d_c_tile[2] = {nullptr, nullptr};
+    void* d_c_val[2] = {nullptr, nullptr};
+    int cur = 0;
+    int* d_cci_ptr = nullptr;     // n_tiles + 1
+    int* d_cci_cnt = nullptr;     // n_tiles
+    int* d_cci_row = nullptr;     // n_mol * cap
+    int* d_cci_slot = nullptr;
+
+    // device: Y = X C column-major
+    int* d_y_n = nullptr;         // n_tiles
+    int* d_y_row = nullptr;       // n_tiles * capY
+    void* d_y_val = nullptr;      // n_tiles * capY * 96
+
+    // device: transform outputs
+    int* d_rot_tp_ptr = nullptr;
+    int* d_rot_tp_b = nullptr;
+    int* d_rot_tp_out = nullptr;
+    int* d_rot_blk_tp0 = nullptr;
+    void* d_F = nullptr;          // n_rot_tp * 256 (T)
+    int* d_diag_tp_ptr = nullptr; // identity lists for the diagonal tile pairs
+    int* d_diag_tp_b = nullptr;
+    int* d_diag_tp_out = nullptr;
+    void* d_Fdiag_tiles = nullptr;   // n_tiles * 256 (T)
+    double* d_Fd = nullptr;       // n_mo
+
+    // device: orthonormalisation tile-pair lists
+    int n_ort_tp[2] = {0, 0};     // [0] all MOs, [1] occupied only
+    int* d_ort_tp_ptr[2] = {nullptr, nullptr};
+    int* d_ort_tp_b[2] = {nullptr, nullptr};
+    int* d_ort_tp_out[2] = {nullptr, nullptr};
+    int* d_ort_blk_tp[2] = {nullptr, nullptr};   // per directed block: 3x3 tile-pair ids (-1 none)
+    std::vector<int> h_ort_blk_tp[2];
+    void* d_sig = nullptr;        // max(n_ort_tp) * 256 (T)
+    double* d_scale = nullptr;    // n_mo: 1/sqrt(sigma_ii)
+
+    // device: pair schedules (rotations and combinations share the storage)
+    int* d_pr_n = nullptr;        // n_gnb
+    int* d_pr_lvl = nullptr;      // n_gnb * (kMaxSub + 1)
+    uint16_t* d_pr_ij = nullptr;  // n_gnb * kOrthoCap
+    void* d_pr_cs = nullptr;      // n_gnb * kOrthoCap * 2 (T)
+    int* d_pr_touch = nullptr;    // n_gnb: side tiles touched (bits 0-2 side A, 3-5 side B)
+
+    // device: charges
+    double* d_q = nullptr;        // n_atoms, new charges
+    double* d_q_prev = nullptr;
+    double* d_dq_in = nullptr;
+    double* d_Q_in = nullptr;
+    double* d_dq = nullptr;
+    double* d_Q = nullptr;
+    double* d_e_mol = nullptr;    // n_mol band-energy partials
+    double* d_red = nullptr;      // reduction scratch (n_mol + 1024)
+    DeviceScalars* d_sc = nullptr;
+    DeviceScalars* h_sc = nullptr;   // pinned mirror
+
+    std::vector<void*> allocations;
+};
+
+// ---- memory -----------------------------------------------------------------
+int dev_alloc(Ctx* c, void** p, size_t bytes);
+void dev_free_all(Ctx* c);
+
+template <typename P>
+inline int dalloc(Ctx* c, P** p, size_t n) {
+    return dev_alloc(c, reinterpret_cast<void**>(p), n * sizeof(P));
+}
+
+// ---- kernel launchers (defined in the .cu files) ------------------------------
+// model
+cudaError_t launch_sk_blocks(Ctx* c);
+cudaError_t launch_gamma(Ctx* c, const double* dq, double* Q);
+cudaError_t launch_build_h(Ctx* c);
+cudaError_t launch_guess(Ctx* c);
+// sparse structure and products
+cudaError_t launch_colindex(Ctx* c);
+cudaError_t launch_xc(Ctx* c, bool use_h, int tile_lo, int tile_hi);
+cudaError_t launch_transform_rot(Ctx* c);
+cudaError_t launch_transform_ortho(Ctx* c, int which);
+cudaError_t launch_density(Ctx* c);
+// schedules and sweeps
+cudaError_t launch_select_rot(Ctx* c);
+cudaError_t launch_ortho_prepare(Ctx* c, int which, double tol);
+cudaError_t launch_apply(Ctx* c, int mode, int which);   // mode 0 rotations, 1 combinations
+cudaError_t launch_compact(Ctx* c);
+// charges
+cudaError_t launch_charges_finish(Ctx* c, bool mix);
+
+}  // namespace sscf
+
+struct sscf_ctx {
+    sscf::Ctx c;
+};

@@ -1,0 +1,240 @@
+"""Parity of the CUDA path (through the C-ABI) with the FP64 oracle, step by step.
+
+Every case feeds both sides the same seeded inputs and compares element by
+element: integer work (neighbour colouring, pair lists) bit-exactly, FP64
+values to a few ulps of the quantities involved, and the FP32 storage of the
+mixed path to the FP32 rounding budget stated per test. Sizes: 32 molecules
+(one 4x4x2 cluster, four full groups), 100 molecules (ragged: partial groups
+and a partial top layer) and 216 molecules (27 groups, several tiles and
+colours).
+"""
+import numpy as np
+import pytest
+
+from gpu_common import P, context, oracle_scf, rel_err, water
+from oracle import model, sparse
+
+pytestmark = pytest.mark.gpu
+
+SIZES = [32, 100, 216]
+
+
+def fresh(n, precision=0, **kw):
+    return water(n), oracle_scf(n), context(water(n), precision=precision, **kw)
+
+
+@pytest.mark.parametrize("n", SIZES)
+def test_structure_colouring_and_model_blocks(n):
+    s, sc, ctx = fresh(n)
+    assert ctx.n_groups == sc.st.n_groups and ctx.n_colours == sc.st.n_colours
+    assert np.array_equal(ctx.colouring(), sc.st.colour)
+    H, H0, S = ctx.get_H()
+    assert np.abs(H0 - sc.H0).max() < 1e-14
+    assert np.abs(S - sc.S).max() < 1e-14
+    assert np.array_equal(H0 != 0, sc.H0 != 0)
+    assert np.array_equal(H, sparse.fock(sc.H0, sc.S, np.zeros(s.n_atoms), sc.atom_of_ao, P["eps_mo"])) or \
+        np.abs(H - sparse.fock(sc.H0, sc.S, np.zeros(s.n_atoms), sc.atom_of_ao, P["eps_mo"])).max() < 1e-15
+
+
+@pytest.mark.parametrize("n", SIZES)
+def test_fock_build(n):
+    s, sc, ctx = fresh(n)
+    rng = np.random.default_rng(n)
+    Q = rng.normal(0.0, 0.1, s.n_atoms)
+    ctx.set_charges(Q_in=Q)
+    ctx.build_fock()
+    H, _, _ = ctx.get_H()
+    ref = sparse.fock(sc.H0, sc.S, Q, sc.atom_of_ao, P["eps_mo"])
+    assert np.abs(H - ref).max() < 1e-15
+    assert np.array_equal(H != 0, ref != 0)
+
+
+@pytest.mark.parametrize("n", SIZES)
+def test_guess(n):
+    s, sc, ctx = fresh(n)
+    ctx.guess()
+    C = ctx.get_C()
+    ref = sparse.initial_guess(s, sc.st, sc.H0, sc.S)
+    assert np.abs(C - ref).max() < 1e-12
+    assert np.array_equal(C != 0, ref != 0)
+
+
+def _prepared(n, eps, precision=0):
+    """Both sides after the guess and a full orthonormalisation (GPU C copied to the oracle)."""
+    s, sc, ctx = fresh(n, precision)
+    ctx.set_thresholds(eps, 10 * eps, 1e-8)
+    ctx.guess()
+    ctx.orthonormalise(0)
+    return s, sc, ctx, ctx.get_C()
+
+
+@pytest.mark.parametrize("n", SIZES)
+def test_orthonormalise_all_matches_oracle(n):
+    s, sc, ctx = fresh(n)
+    eps = 1e-5
+    ctx.set_thresholds(eps, 1e-4, 1e-8)
+    ctx.guess()
+    passes, eta = ctx.orthonormalise(0)
+    C = ctx.get_C()
+    ref = sparse.initial_guess(s, sc.st, sc.H0, sc.S)
+    rp, reta = sparse.orthonormalise(ref, sc.S, sc.st, "all", eps)
+    assert passes == rp
+    assert eta < eps / 100
+    assert abs(eta - reta) <= 1e-12 + 1e-9 * reta
+    assert np.abs(C - ref).max() < 1e-11
+    sig = C.T @ sc.S @ C
+    assert np.abs(sig - np.eye(sig.shape[0])).max() < 1e-6
+
+
+@pytest.mark.parametrize("n", SIZES)
+def test_ortho_single_pass_and_pairs(n):
+    s, sc, ctx, C0 = _prepared(n, 1e-4)
+    # perturb the occupied block so that a pass has work, identically on both sides
+    rng = np.random.default_rng(7)
+    C1 = C0.copy()
+    no = sc.st.n_occ
+    C1[:, :no] += 1e-3 * rng.standard_normal(C1[:, :no].shape) * (C1[:, :no] != 0)
+    ctx.set_C(C1)
+    passes, eta = ctx.orthonormalise(1, max_pass=1)
+    col, sub, i, j = ctx.pairs()
+    C = ctx.get_C()
+    ref = C1.copy()
+    reta, ncombo = sparse.ortho_pass(ref, sc.S, sc.st, "occ", 1e-4 / 100, 1e-3 * 1e-4)
+    assert abs(eta - reta) <= 1e-12 * max(1.0, reta)
+    assert ncombo == i.size
+    mos = np.arange(no)
+    sig = C1[:, mos].T @ sc.S @ C1[:, mos]
+    sig = np.where(sparse.overlap_mask(sc.st, mos), sig, 0.0)
+    d = np.sqrt(np.diag(sig))
+    sel = sparse.overlap_mask(sc.st, mos) & (np.abs(sig / np.outer(d, d)) >= 1e-3 * reta)
+    np.fill_diagonal(sel, False)
+    pa, pb = sparse.ortho_schedule(sc.st, "occ", mos, sel)
+    got = sorted(zip(col.tolist(), sub.tolist(), i.tolist(), j.tolist()))
+    g = sc.st.mo_group
+    loc = sparse.pass_local(sc.st, "occ", mos)
+    size = sparse.pass_group_size(sc.st, "occ")
+    want = sorted((int(sc.st.colour[g[a], g[b]]), int((loc[a] + loc[b]) % max(size[g[a]], size[g[b]])),
+                   int(a), int(b)) for a, b in zip(pa.tolist(), pb.tolist()))
+    assert got == want
+    assert np.abs(C - ref).max() < 1e-12
+
+
+@pytest.mark.parametrize("n", SIZES)
+def test_transform_selection_and_sweep(n):
+    s, sc, ctx, C0 = _prepared(n, 1e-5)
+    rng = np.random.default_rng(n + 1)
+    Q = rng.normal(0.0, 0.05, s.n_atoms)
+    ctx.set_charges(Q_in=Q)
+    ctx.build_fock()
+    n_rot, max_fov = ctx.rotate_sweep()
+    F, Fd = ctx.get_F()
+    H = sparse.fock(sc.H0, sc.S, Q, sc.atom_of_ao, 1e-5)
+    F_ref, Fd_ref, mask = sparse.transform_ov(C0, H, sc.st)
+    scale = np.abs(F_ref).max()
+    assert np.abs(F - F_ref).max() < 1e-12 * max(scale, 1.0)
+    assert np.abs(Fd - Fd_ref).max() < 1e-12
+    assert max_fov == pytest.approx(np.abs(F_ref).max(), rel=1e-12)
+    # selection and schedule on the GPU's own F values: bit-exact
+    k_max = int(P["rot_cap_factor"] * sc.st.n_occ)
+    sel = sparse.select_pairs(F, mask, 1e-5, k_max)
+    assert n_rot == sel.sum()
+    order = sparse.rotation_schedule(sc.st, sel)
+    col, sub, i, j = ctx.pairs()
+    nv = np.array([v.size for v in sc.st.virt_of_group])
+    no = np.array([o.size for o in sc.st.occ_of_group])
+    want = sorted((int(sc.st.colour[sc.st.mo_group[a], sc.st.mo_group[b]]),
+                   int((sc.st.mo_local[a] + sc.st.mo_local[b]) %
+                       max(no[sc.st.mo_group[a]], nv[sc.st.mo_group[b]])), a, b) for a, b in order)
+    assert sorted(zip(col.tolist(), sub.tolist(), i.tolist(), j.tolist())) == want
+    # the sweep itself
+    ref = C0.copy()
+    sparse.rotate_sweep(ref, F, Fd, sc.st, sel, 1e-5)
+    C = ctx.get_C()
+    assert np.abs(C - ref).max() < 1e-11
+    near = np.abs(np.abs(ref) - 1e-5) < 1e-12
+    assert np.array_equal((C != 0) | near, (ref != 0) | near)
+
+
+def test_rotation_cap_radix_select():
+    n = 216
+    s, sc, ctx, C0 = _prepared(n, 1e-6)
+    rng = np.random.default_rng(3)
+    Q = rng.normal(0.0, 0.2, s.n_atoms)
+    ctx.set_charges(Q_in=Q)
+    ctx.build_fock()
+    n_rot, _ = ctx.rotate_sweep()
+    F, Fd = ctx.get_F()
+    _, _, mask = sparse.transform_ov(C0, sparse.fock(sc.H0, sc.S, Q, sc.atom_of_ao, 1e-6), sc.st)
+    k_max = int(P["rot_cap_factor"] * sc.st.n_occ)
+    cand = (mask & (np.abs(F) >= 1e-6) & (F != 0)).sum()
+    assert cand > k_max, "case must exercise the cap"
+    sel = sparse.select_pairs(F, mask, 1e-6, k_max)
+    assert n_rot == sel.sum() and n_rot >= k_max
+
+
+@pytest.mark.parametrize("n", SIZES)
+def test_density_charges_energy(n):
+    s, sc, ctx, C0 = _prepared(n, 1e-5)
+    E = ctx.reset_charges()
+    q, dq, Q = ctx.get_charges()
+    rq, rdq, rQ, rE = sc.charges_energy(C0)
+    assert np.abs(q - rq).max() < 1e-11
+    assert np.abs(Q - rQ).max() < 1e-11
+    assert E == pytest.approx(rE, abs=1e-9)
+    assert q.sum() == pytest.approx(8 * s.n_mol, rel=1e-10)
+
+
+@pytest.mark.parametrize("n", [32, 100])
+def test_scc_steps_follow_oracle(n):
+    s, sc, ctx = fresh(n)
+    eps = 1e-5
+    ctx.set_thresholds(eps, 1e-4, 1e-8)
+    ctx.guess()
+    ctx.orthonormalise(0)
+    ctx.reset_charges()
+    st = sc.start(eps)
+    assert np.abs(ctx.get_C() - st.C).max() < 1e-11
+    for k in range(4):
+        info = ctx.step()
+        ref = sc.step(st, eps)
+        assert info["energy"] == pytest.approx(ref.energy, abs=1e-8 * s.n_atoms)
+        assert info["n_rot"] == ref.n_rot
+        q, _, _ = ctx.get_charges()
+        assert np.abs(q - st.q_prev).max() < 1e-8
+        assert np.abs(ctx.get_C() - st.C).max() < 1e-8
+
+
+def test_run_config1_fp64_matches_oracle_and_dense():
+    from oracle import dense
+    s = water(32)
+    ctx = context(s)
+    out = ctx.run()
+    ref = oracle_scf(32).run()
+    assert out["converged"] and ref["converged"]
+    assert out["energy"] == pytest.approx(ref["energy"], abs=1e-7)
+    d = dense.solve(s, P)
+    assert abs(out["energy"] - d.energy) / s.n_atoms < 1e-6
+
+
+def test_run_config1_mixed_within_tolerance():
+    s = water(32)
+    ctx = context(s, precision=1)
+    out = ctx.run(allow_not_converged=True)
+    ref = oracle_scf(32).run()
+    assert abs(out["energy"] - ref["energy"]) / s.n_atoms < 1e-6
+    q, _, _ = ctx.get_charges()
+    assert np.abs(q - ref["q"]).max() < 1e-4
+
+
+@pytest.mark.parametrize("n", [32, 216])
+def test_mixed_single_step_close_to_fp64(n):
+    eps = 1e-5
+    outs = []
+    for prec in (0, 1):
+        s, sc, ctx = fresh(n, prec)
+        ctx.set_thresholds(eps, 10 * eps, 1e-8)
+        ctx.guess()
+        ctx.orthonormalise(0)
+        ctx.reset_charges()
+        outs.append(ctx.step())
+    assert abs(outs[0]["energy"] - outs[1]["energy"]) / water(n).n_atoms < 1e-5
