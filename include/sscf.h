@@ -162,6 +162,17 @@ int sscf_step(sscf_ctx* ctx, sscf_step_info* info);
  * state kept if max_scc is reached. */
 int sscf_run(sscf_ctx* ctx, sscf_step_info* info);
 
+/* Tracing --------------------------------------------------------------- */
+
+/* Per-launcher device times: when enabled, every kernel launcher of the steps
+ * above is bracketed by CUDA events on the context's stream. */
+int sscf_profile(sscf_ctx* ctx, int enable);
+/* Summed milliseconds and call counts per launcher name since the last read
+ * (then reset). names receives max_entries * 32 bytes, NUL-terminated; any
+ * output may be NULL; n_out receives the number of names. Synchronises the
+ * context's stream. */
+int sscf_profile_read(sscf_ctx* ctx, int max_entries, char* names, double* ms, int64_t* calls, int* n_out);
+
 /* State access (checkpoint / restart and tests) -------------------------- */
 
 /* Dense copies for small systems: C is n_ao x n_mo, row-major (C[mu*n_mo+i]). */

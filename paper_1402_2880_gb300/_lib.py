@@ -31,7 +31,7 @@ EXPORTED = [
     "sscf_get_dims", "sscf_guess", "sscf_orthonormalise", "sscf_build_fock", "sscf_rotate_sweep",
     "sscf_density", "sscf_reset_charges", "sscf_step", "sscf_run", "sscf_get_C_dense",
     "sscf_set_C_dense", "sscf_get_H_dense", "sscf_get_F_dense", "sscf_get_charges",
-    "sscf_set_charges", "sscf_get_colouring", "sscf_get_pairs",
+    "sscf_set_charges", "sscf_get_colouring", "sscf_get_pairs", "sscf_profile", "sscf_profile_read",
 ]
 
 
@@ -104,6 +104,8 @@ def load() -> ctypes.CDLL:
         "sscf_get_colouring": (c_int, [c_vp, P(c_int)]),
         "sscf_get_pairs": (c_int, [c_vp, c_i64, P(ctypes.c_int32), P(ctypes.c_int32), P(ctypes.c_int32),
                                    P(ctypes.c_int32), P(c_i64)]),
+        "sscf_profile": (c_int, [c_vp, c_int]),
+        "sscf_profile_read": (c_int, [c_vp, c_int, ctypes.c_char_p, P(c_double), P(c_i64), P(c_int)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -255,6 +257,23 @@ class Context:
         C = np.empty((self.n_groups, self.n_groups), dtype=np.int32)
         _check(self.lib.sscf_get_colouring(self.h, _ptr(C, ctypes.c_int)), "sscf_get_colouring")
         return C
+
+    def profile(self, enable: bool = True):
+        _check(self.lib.sscf_profile(self.h, 1 if enable else 0), "sscf_profile")
+
+    def profile_read(self) -> dict:
+        """{launcher name: (milliseconds, calls)} since the last read."""
+        n = ctypes.c_int()
+        _check(self.lib.sscf_profile_read(self.h, 0, None, None, None, ctypes.byref(n)), "sscf_profile_read")
+        m = n.value
+        names = ctypes.create_string_buffer(32 * max(m, 1))
+        ms = np.zeros(max(m, 1))
+        calls = np.zeros(max(m, 1), dtype=np.int64)
+        _check(self.lib.sscf_profile_read(self.h, m, names, _ptr(ms), _ptr(calls, ctypes.c_int64),
+                                          ctypes.byref(n)), "sscf_profile_read")
+        raw = names.raw
+        return {raw[32 * i:32 * i + 32].split(b"\0")[0].decode(): (float(ms[i]), int(calls[i]))
+                for i in range(m)}
 
     def pairs(self):
         n = ctypes.c_int64()

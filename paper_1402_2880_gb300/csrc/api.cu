@@ -347,6 +347,63 @@ int upload(Ctx& c, V** d, const std::vector<V>& h) {
     return SSCF_OK;
 }
 
+// Records one CUDA event pair on the context's stream around a launcher when
+// profiling is on; the times are summed per name at the next sscf_profile_read.
+struct ProfScope {
+    Ctx& c;
+    int id = -1;
+    cudaEvent_t e0 = nullptr;
+    ProfScope(Ctx& cc, const char* name) : c(cc) {
+        if (!c.prof) return;
+        for (size_t i = 0; i < c.prof_names.size(); ++i)
+            if (c.prof_names[i] == name) id = (int)i;
+        if (id < 0) {
+            id = (int)c.prof_names.size();
+            c.prof_names.push_back(name);
+            c.prof_ms.push_back(0.0);
+            c.prof_calls.push_back(0);
+        }
+        if (cudaEventCreate(&e0) != cudaSuccess || cudaEventRecord(e0, c.stream) != cudaSuccess) {
+            cudaGetLastError();
+            e0 = nullptr;
+        }
+    }
+    ~ProfScope() {
+        if (!c.prof || !e0) return;
+        cudaEvent_t e1 = nullptr;
+        if (cudaEventCreate(&e1) != cudaSuccess || cudaEventRecord(e1, c.stream) != cudaSuccess) {
+            cudaGetLastError();
+            cudaEventDestroy(e0);
+            return;
+        }
+        c.prof_pending.push_back({id, e0, e1});
+    }
+};
+
+int prof_collect(Ctx& c) {
+    if (c.prof_pending.empty()) return SSCF_OK;
+    CK(cudaStreamSynchronize(c.stream));
+    for (auto& r : c.prof_pending) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, r.e0, r.e1) == cudaSuccess) {
+            c.prof_ms[r.id] += ms;
+            c.prof_calls[r.id] += 1;
+        } else {
+            cudaGetLastError();
+        }
+        cudaEventDestroy(r.e0);
+        cudaEventDestroy(r.e1);
+    }
+    c.prof_pending.clear();
+    return SSCF_OK;
+}
+
+#define PK(name, call)            \
+    do {                          \
+        ProfScope ps_(c, name);   \
+        CK(call);                 \
+    } while (0)
+
 int sync_scalars(Ctx& c) {
     CK(cudaMemcpyAsync(c.h_sc, c.d_sc, sizeof(DeviceScalars), cudaMemcpyDeviceToHost, c.stream));
     CK(cudaStreamSynchronize(c.stream));
@@ -600,6 +657,7 @@ int sscf_create(const sscf_system* sys, const sscf_params* prm, void* cuda_strea
 void sscf_destroy(sscf_ctx* h) {
     if (!h) return;
     cudaStreamSynchronize(h->c.stream);
+    prof_collect(h->c);
     dev_free_all(&h->c);
     if (h->c.h_sc) cudaFreeHost(h->c.h_sc);
     delete h;
@@ -640,17 +698,20 @@ int sscf_guess(sscf_ctx* h) {
 
 int sscf_build_fock(sscf_ctx* h) {
     if (!h) return SSCF_ERR_INVALID_ARG;
-    CK(launch_build_h(&h->c));
+    Ctx& c = h->c;
+    PK("build_fock", launch_build_h(&c));
     return SSCF_OK;
 }
 
 static int rotate_sweep_async(Ctx& c) {
-    CK(launch_colindex(&c));
-    CK(launch_xc(&c, true, 0, c.n_tiles));
-    CK(launch_transform_rot(&c));
-    CK(launch_select_rot(&c));
-    CK(launch_apply(&c, 0, 0));
-    CK(launch_compact(&c));
+    PK("colindex", launch_colindex(&c));
+    PK("xc_h", launch_xc(&c, true, 0, c.n_tiles));
+    PK("transform_ov", launch_transform_rot(&c));
+    PK("select_rot", launch_select_rot(&c));
+    PK("closure", launch_closure(&c, 0, 0));
+    PK("colindex", launch_colindex(&c));
+    PK("apply_rot", launch_apply(&c, 0, 0));
+    PK("compact", launch_compact(&c));
     c.last_sched_kind = 1;
     return SSCF_OK;
 }
@@ -669,12 +730,14 @@ int sscf_rotate_sweep(sscf_ctx* h, int64_t* n_rot_out, double* max_fov_out) {
 
 static int ortho_pass_async(Ctx& c, int which, double tol) {
     const int w = which == SSCF_ORTHO_OCC ? 1 : 0;
-    CK(launch_colindex(&c));
-    CK(launch_xc(&c, false, 0, w == 1 ? c.n_occ_tiles : c.n_tiles));
-    CK(launch_transform_ortho(&c, w));
-    CK(launch_ortho_prepare(&c, w, tol));
-    CK(launch_apply(&c, 1, w));
-    CK(launch_compact(&c));
+    PK("colindex", launch_colindex(&c));
+    PK("xc_s", launch_xc(&c, false, 0, w == 1 ? c.n_occ_tiles : c.n_tiles));
+    PK("transform_ss", launch_transform_ortho(&c, w));
+    PK("ortho_prepare", launch_ortho_prepare(&c, w, tol));
+    PK("closure", launch_closure(&c, 1, w));
+    PK("colindex", launch_colindex(&c));
+    PK("apply_ortho", launch_apply(&c, 1, w));
+    PK("compact", launch_compact(&c));
     c.last_sched_kind = 2;
     c.last_ortho_which = w;
     return SSCF_OK;
@@ -701,8 +764,8 @@ int sscf_orthonormalise(sscf_ctx* h, int which, int max_pass, int* passes_out, d
 }
 
 static int density_async(Ctx& c, bool mix) {
-    CK(launch_density(&c));
-    CK(launch_charges_finish(&c, mix));
+    PK("density", launch_density(&c));
+    PK("charges_gamma", launch_charges_finish(&c, mix));
     return SSCF_OK;
 }
 
@@ -746,7 +809,7 @@ int sscf_step(sscf_ctx* h, sscf_step_info* info) {
     Ctx& c = h->c;
     if (!c.have_guess) return SSCF_ERR_STATE;
     CK(cudaMemsetAsync(c.d_sc, 0, offsetof(DeviceScalars, hist), c.stream));
-    CK(launch_build_h(&c));
+    PK("build_fock", launch_build_h(&c));
     CKS(rotate_sweep_async(c));
     unsigned long long n_rot_dummy = 0;
     (void)n_rot_dummy;
@@ -772,6 +835,35 @@ int sscf_step(sscf_ctx* h, sscf_step_info* info) {
     if (!std::isfinite(c.h_sc->energy)) return SSCF_ERR_NONFINITE;
     c.e_prev = c.h_sc->energy;
     c.have_e_prev = true;
+    return SSCF_OK;
+}
+
+int sscf_profile(sscf_ctx* h, int enable) {
+    if (!h) return SSCF_ERR_INVALID_ARG;
+    Ctx& c = h->c;
+    CKS(prof_collect(c));
+    c.prof = enable != 0;
+    return SSCF_OK;
+}
+
+int sscf_profile_read(sscf_ctx* h, int max_entries, char* names, double* ms, int64_t* calls, int* n_out) {
+    if (!h || max_entries < 0) return SSCF_ERR_INVALID_ARG;
+    Ctx& c = h->c;
+    CKS(prof_collect(c));
+    const int n = (int)c.prof_names.size();
+    for (int i = 0; i < n && i < max_entries; ++i) {
+        if (names) {
+            std::memset(names + 32 * i, 0, 32);
+            std::strncpy(names + 32 * i, c.prof_names[i].c_str(), 31);
+        }
+        if (ms) ms[i] = c.prof_ms[i];
+        if (calls) calls[i] = c.prof_calls[i];
+    }
+    if (n_out) *n_out = n;
+    for (int i = 0; i < n; ++i) {
+        c.prof_ms[i] = 0.0;
+        c.prof_calls[i] = 0;
+    }
     return SSCF_OK;
 }
 

@@ -11,6 +11,8 @@
 // and reads and writes C once.
 #include <math.h>
 
+#include <vector>
+
 #include "sscf_internal.h"
 
 namespace sscf {
@@ -351,15 +353,23 @@ __global__ void k_ortho_lists(int w, double tol, const int* __restrict__ oblk, c
 }
 
 // --------------------------------------------------------------------------
-// row-local application of a whole sweep
+// Structural fill of a sweep (value-independent), then block-major apply.
+//
+// A unit is the set of tiles a block side touches: (group, occupied) and
+// (group, virtual) for rotations and occupied passes, the whole group for
+// passes over all MOs. A 2x2 update of an active block (one with pairs) can
+// fill one side from the other, so before the sweep every row block is
+// closed under "a block with pairs has both of its sides or neither"; all
+// tiles of the units it holds are inserted as zero tiles. After that no
+// update creates a tile: the sweep runs colour by colour, block-major, in
+// place, and a final compaction drops the tiles left all-zero.
 // --------------------------------------------------------------------------
-struct ApplyArgs {
-    int mode;        // 0 rotations (occupied A x virtual B), 1 combinations
-    int which;       // combinations: 0 all MOs, 1 occupied
-    int n_tiles, n_occ_tiles, n_groups, cap, n_colours;
+struct SweepArgs {
+    int mode;        // 0 rotations (A occupied | B virtual), 1 combinations
+    int which;       // combinations: 0 all MOs, 1 occupied MOs
+    int n_tiles, n_groups, cap, n_blk;
     double trunc;
-    const int* colour_ptr;
-    const int* colour_blk;
+    const int* blk;          // blocks of the pass (any order for the closure)
     const int* gnb_row;
     const int* gnb_col;
     const int* group_nmol;
@@ -375,8 +385,10 @@ struct ApplyArgs {
     const int* pr_lvl;
     const uint16_t* pr_ij;
     const void* pr_cs;
-    const int* pr_touch;
-    const double* dsc;    // mode 1: divide the pass's MOs by d_i first
+    const double* dsc;       // combinations: divide the pass's MOs by d_i first
+    const int* cci_ptr;
+    const int* cci_row;
+    const int* cci_slot;
     const int* in_nt;
     const int* in_tile;
     const void* in_val;
@@ -386,182 +398,251 @@ struct ApplyArgs {
     unsigned* err;
 };
 
-constexpr int kApplyWarps = 8;
+constexpr int kClosureIters = 256;
 
 template <typename T>
-__global__ void __launch_bounds__(kApplyWarps * 32) k_apply(ApplyArgs a) {
+__global__ void __launch_bounds__(256) k_closure(SweepArgs a) {
     extern __shared__ unsigned char smraw[];
-    const int cap = a.cap;
-    int np2 = 1;
-    while (np2 < cap) np2 <<= 1;
-    T* vals = (T*)smraw;                                        // cap * 16
-    unsigned* keys = (unsigned*)(vals + (size_t)cap * 16);      // np2 (tile << 16 | slot)
-    short* map = (short*)(keys + np2);                          // n_tiles
-    unsigned* pres = (unsigned*)(map + ((a.n_tiles + 1) & ~1));  // 2 * ceil(G/32)
-    __shared__ int s_n, s_abort;
     const int gw = (a.n_groups + 31) >> 5;
-    const int r = blockIdx.x / 6, krow = blockIdx.x % 6;
-    const T* inv = (const T*)a.in_val;
+    unsigned* occ = (unsigned*)smraw;
+    unsigned* vir = occ + gw;
+    short* map = (short*)(vir + gw);             // n_tiles: old slot or -1
+    __shared__ int part[256];
+    __shared__ int s_total;
+    const int r = blockIdx.x;
+    for (int i = threadIdx.x; i < gw; i += blockDim.x) occ[i] = vir[i] = 0u;
     for (int i = threadIdx.x; i < a.n_tiles; i += blockDim.x) map[i] = -1;
-    for (int i = threadIdx.x; i < 2 * gw; i += blockDim.x) pres[i] = 0u;
-    if (threadIdx.x == 0) {
-        s_n = a.in_nt[r];
-        s_abort = 0;
-    }
     __syncthreads();
-    const int n0 = s_n;
+    const int n0 = a.in_nt[r];
     for (int s = threadIdx.x; s < n0; s += blockDim.x) {
-        const int t = a.in_tile[(size_t)r * cap + s];
+        const int t = a.in_tile[(size_t)r * a.cap + s];
         map[t] = (short)s;
         const int g = a.tile_group[t];
-        atomicOr(&pres[a.tile_kind[t] * gw + (g >> 5)], 1u << (g & 31));
-    }
-    for (int idx = threadIdx.x; idx < n0 * 16; idx += blockDim.x) {
-        const int s = idx >> 4, c = idx & 15;
-        T v = inv[(((size_t)r * cap + s) * 6 + krow) * 16 + c];
-        if (a.mode == 1) {
-            const int t = a.in_tile[(size_t)r * cap + s];
-            const bool in_pass = a.which == 0 || a.tile_kind[t] == 0;
-            if (in_pass && c < a.tile_nmo[t]) v = (T)((double)v / a.dsc[a.tile_mo0[t] + c]);
+        const unsigned bit = 1u << (g & 31);
+        if (a.mode == 1 && a.which == 0) {
+            atomicOr(&occ[g >> 5], bit);
+            atomicOr(&vir[g >> 5], bit);
+        } else if (a.tile_kind[t] == 0) {
+            atomicOr(&occ[g >> 5], bit);
+        } else {
+            atomicOr(&vir[g >> 5], bit);
         }
-        vals[idx] = v;
     }
     __syncthreads();
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const T* cs = (const T*)a.pr_cs;
-    for (int col = 0; col < a.n_colours; ++col) {
-        const int b0 = a.colour_ptr[col], b1 = a.colour_ptr[col + 1];
-        for (int jb = b0 + warp; jb < b1; jb += kApplyWarps) {
-            const int e = a.colour_blk[jb];
-            const int np = a.pr_n[e];
-            if (np == 0) continue;
+    for (int it = 0; it < kClosureIters; ++it) {
+        int changed = 0;
+        for (int j = threadIdx.x; j < a.n_blk; j += blockDim.x) {
+            const int e = a.blk[j];
+            if (a.pr_n[e] == 0) continue;
             const int A = a.gnb_row[e], B = a.gnb_col[e];
-            const int touch = a.pr_touch[e];
-            // side tiles: rotations: A occ | B virt; combinations: occ (+ virt) of A | of B
-            int st[6];
-            int nsa = 0, nsb = 0;
-            for (int i = 0; i < a.group_not[A]; ++i) st[nsa++] = a.group_ot0[A] + i;
-            if (a.mode == 1 && a.which == 0)
-                for (int i = 0; i < a.group_nvt[A]; ++i) st[nsa++] = a.group_vt0[A] + i;
-            if (a.mode == 1) {
-                for (int i = 0; i < a.group_not[B]; ++i) st[3 + nsb++] = a.group_ot0[B] + i;
-                if (a.which == 0)
-                    for (int i = 0; i < a.group_nvt[B]; ++i) st[3 + nsb++] = a.group_vt0[B] + i;
+            const unsigned ba = 1u << (A & 31), bb = 1u << (B & 31);
+            const bool ha = (occ[A >> 5] & ba) != 0;
+            const bool hb = a.mode == 0 ? (vir[B >> 5] & bb) != 0 : (occ[B >> 5] & bb) != 0;
+            if (ha == hb) continue;
+            changed = 1;
+            atomicOr(&occ[A >> 5], ba);
+            if (a.mode == 0) {
+                atomicOr(&vir[B >> 5], bb);
             } else {
-                for (int i = 0; i < a.group_nvt[B]; ++i) st[3 + nsb++] = a.group_vt0[B] + i;
-            }
-            bool relevant = false;
-            for (int i = 0; i < 6; ++i) {
-                const bool in_side = i < 3 ? i < nsa : (i - 3) < nsb;
-                if (in_side && ((touch >> i) & 1) && map[st[i]] >= 0) relevant = true;
-            }
-            if (!relevant) continue;
-            int slot[6];
-            if (lane == 0) {
-                for (int i = 0; i < 6; ++i) {
-                    slot[i] = -1;
-                    const bool in_side = i < 3 ? i < nsa : (i - 3) < nsb;
-                    if (!in_side || !((touch >> i) & 1)) continue;
-                    const int t = st[i];
-                    int s = map[t];
-                    if (s < 0) {
-                        s = atomicAdd(&s_n, 1);
-                        if (s >= cap) {
-                            atomicOr(a.err, kErrCapacity);
-                            s_abort = 1;
-                            s = -1;
-                        } else {
-                            for (int c = 0; c < 16; ++c) vals[(size_t)s * 16 + c] = (T)0;
-                            map[t] = (short)s;
-                            const int g = a.tile_group[t];
-                            atomicOr(&pres[a.tile_kind[t] * gw + (g >> 5)], 1u << (g & 31));
-                        }
-                    }
-                    slot[i] = s;
+                atomicOr(&occ[B >> 5], bb);
+                if (a.which == 0) {
+                    atomicOr(&vir[A >> 5], ba);
+                    atomicOr(&vir[B >> 5], bb);
                 }
             }
-#pragma unroll
-            for (int i = 0; i < 6; ++i) slot[i] = __shfl_sync(0xffffffffu, slot[i], 0);
-            __syncwarp();
-            bool bad = false;
-            for (int i = 0; i < 6; ++i) {
-                const bool in_side = i < 3 ? i < nsa : (i - 3) < nsb;
-                if (in_side && ((touch >> i) & 1) && slot[i] < 0) bad = true;
+        }
+        if (!__syncthreads_or(changed)) break;
+    }
+    // new sorted tile list: occupied units by group, then virtual units
+    const int per = (2 * a.n_groups + blockDim.x - 1) / blockDim.x;
+    const int u0 = threadIdx.x * per, u1 = min(2 * a.n_groups, u0 + per);
+    int cnt = 0;
+    for (int u = u0; u < u1; ++u) {
+        const int g = u < a.n_groups ? u : u - a.n_groups;
+        const bool on = u < a.n_groups ? (occ[g >> 5] >> (g & 31)) & 1 : (vir[g >> 5] >> (g & 31)) & 1;
+        if (on) cnt += u < a.n_groups ? a.group_not[g] : a.group_nvt[g];
+    }
+    part[threadIdx.x] = cnt;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int run = 0;
+        for (int i = 0; i < (int)blockDim.x; ++i) {
+            int v = part[i];
+            part[i] = run;
+            run += v;
+        }
+        s_total = run;
+    }
+    __syncthreads();
+    const int n1 = s_total;
+    if (n1 > a.cap) {
+        if (threadIdx.x == 0) atomicOr(a.err, kErrCapacity);
+        return;
+    }
+    int pos = part[threadIdx.x];
+    for (int u = u0; u < u1; ++u) {
+        const int g = u < a.n_groups ? u : u - a.n_groups;
+        const bool on = u < a.n_groups ? (occ[g >> 5] >> (g & 31)) & 1 : (vir[g >> 5] >> (g & 31)) & 1;
+        if (!on) continue;
+        const int t0 = u < a.n_groups ? a.group_ot0[g] : a.group_vt0[g];
+        const int nt = u < a.n_groups ? a.group_not[g] : a.group_nvt[g];
+        for (int i = 0; i < nt; ++i) a.out_tile[(size_t)r * a.cap + pos++] = t0 + i;
+    }
+    if (threadIdx.x == 0) a.out_nt[r] = n1;
+    __syncthreads();
+    const T* inv = (const T*)a.in_val;
+    T* outv = (T*)a.out_val;
+    for (int idx = threadIdx.x; idx < n1 * kTileVals; idx += blockDim.x) {
+        const int s = idx / kTileVals, e = idx % kTileVals, col = e & 15;
+        const int t = a.out_tile[(size_t)r * a.cap + s];
+        const int os = map[t];
+        T v = os >= 0 ? inv[((size_t)r * a.cap + os) * kTileVals + e] : (T)0;
+        if (a.mode == 1 && os >= 0 && (a.which == 0 || a.tile_kind[t] == 0) && col < a.tile_nmo[t])
+            v = (T)((double)v / a.dsc[a.tile_mo0[t] + col]);
+        outv[((size_t)r * a.cap + s) * kTileVals + e] = v;
+    }
+}
+
+size_t closure_smem_bytes(const Ctx* c) {
+    return (size_t)2 * ((c->n_groups + 31) / 32) * 4 + (size_t)((c->n_tiles + 1) & ~1) * 2 + 16;
+}
+
+// side tiles of a block: up to 3 per side, as (first tile of a run, offset)
+struct Side {
+    int n;           // tiles on the side
+    int run0;        // first tile of the occupied (or only) run
+    int nrun0;       // tiles in that run
+    int run1;        // first tile of the virtual run (all-MO passes) or -1
+};
+
+__device__ __forceinline__ Side side_of(const SweepArgs& a, int g, bool virt_only, bool with_virt) {
+    Side s;
+    if (virt_only) {
+        s.run0 = a.group_vt0[g];
+        s.nrun0 = a.group_nvt[g];
+        s.run1 = -1;
+        s.n = s.nrun0;
+    } else {
+        s.run0 = a.group_ot0[g];
+        s.nrun0 = a.group_not[g];
+        s.run1 = with_virt ? a.group_vt0[g] : -1;
+        s.n = s.nrun0 + (with_virt ? a.group_nvt[g] : 0);
+    }
+    return s;
+}
+
+constexpr int kChunk = 16;                 // row blocks per CTA
+constexpr int kNR = kChunk * kAoPerMol;    // AO rows per CTA
+constexpr int kNRp = kNR + 1;              // padded panel stride (bank spread)
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_apply_colour(SweepArgs a, int p0) {
+    extern __shared__ unsigned char smraw[];
+    T* panel = (T*)smraw;                                    // [6 tiles][16][kNR]
+    T* pcs = panel + 6 * 16 * kNRp;                           // np * 2
+    uint16_t* pij = (uint16_t*)(pcs + 2 * kOrthoCap);        // np
+    __shared__ int s_lvl[kMaxSub + 1];
+    __shared__ int s_row[kChunk];
+    __shared__ int s_slot[kChunk][6];
+    const int e = a.blk[p0 + blockIdx.y];
+    const int np = a.pr_n[e];
+    if (np == 0) return;
+    const int A = a.gnb_row[e], B = a.gnb_col[e];
+    const bool with_virt = a.mode == 1 && a.which == 0;
+    const Side sa = side_of(a, A, false, with_virt);
+    const Side sb = side_of(a, B, a.mode == 0, with_virt);
+    const int pa = a.cci_ptr[sa.run0], n_rows = a.cci_ptr[sa.run0 + 1] - pa;
+    const int pb = a.cci_ptr[sb.run0];
+    const int k0 = blockIdx.x * kChunk;
+    if (k0 >= n_rows) return;
+    if (a.cci_ptr[sb.run0 + 1] - pb != n_rows) {
+        if (threadIdx.x == 0) atomicOr(a.err, kErrCapacity);
+        return;
+    }
+    const int nk = min(kChunk, n_rows - k0);
+    const int pav = sa.run1 >= 0 ? a.cci_ptr[sa.run1] : 0;
+    const int pbv = sb.run1 >= 0 ? a.cci_ptr[sb.run1] : 0;
+    if (threadIdx.x < nk) {
+        const int k = k0 + threadIdx.x;
+        s_row[threadIdx.x] = a.cci_row[pa + k];
+        const int so = a.cci_slot[pa + k];
+        const int sv = sa.run1 >= 0 ? a.cci_slot[pav + k] : 0;
+        const int bo = a.cci_slot[pb + k];
+        const int bv = sb.run1 >= 0 ? a.cci_slot[pbv + k] : 0;
+        for (int i = 0; i < 3; ++i) {
+            s_slot[threadIdx.x][i] = i < sa.nrun0 ? so + i : (i < sa.n ? sv + (i - sa.nrun0) : -1);
+            s_slot[threadIdx.x][3 + i] = i < sb.nrun0 ? bo + i : (i < sb.n ? bv + (i - sb.nrun0) : -1);
+        }
+    }
+    const int* lvl = a.pr_lvl + (size_t)e * (kMaxSub + 1);
+    for (int i = threadIdx.x; i <= kMaxSub; i += blockDim.x) s_lvl[i] = lvl[i];
+    const T* cs = (const T*)a.pr_cs + (size_t)e * kOrthoCap * 2;
+    const uint16_t* ij = a.pr_ij + (size_t)e * kOrthoCap;
+    for (int i = threadIdx.x; i < np; i += blockDim.x) {
+        pij[i] = ij[i];
+        pcs[2 * i] = cs[2 * i];
+        pcs[2 * i + 1] = cs[2 * i + 1];
+    }
+    __syncthreads();
+    T* val = (T*)a.out_val;   // in place
+    // load the panel: tile position p, column col, AO row kr of row block rb
+    for (int idx = threadIdx.x; idx < nk * 6 * kTileVals; idx += blockDim.x) {
+        const int rb = idx / (6 * kTileVals);
+        const int rem = idx % (6 * kTileVals);
+        const int p = rem / kTileVals, v = rem % kTileVals;
+        const int kr = v >> 4, col = v & 15;
+        const int sl = s_slot[rb][p];
+        T x = (T)0;
+        if (sl >= 0) x = val[((size_t)s_row[rb] * a.cap + sl) * kTileVals + v];
+        panel[(p * 16 + col) * kNRp + rb * 6 + kr] = x;
+    }
+    __syncthreads();
+    const int noA = 4 * a.group_nmol[A], noB = 4 * a.group_nmol[B];
+    const int nr = nk * 6;
+    for (int sub = 0; sub < kMaxSub; ++sub) {
+        const int q0 = s_lvl[sub], q1 = s_lvl[sub + 1];
+        if (q0 == np) break;
+        const int items = (q1 - q0) * nr;
+        for (int it = threadIdx.x; it < items; it += blockDim.x) {
+            const int q = q0 + it / nr, row = it % nr;
+            const unsigned w = pij[q];
+            const int il = w & 255, jl = w >> 8;
+            int ta, ca, tb, cb;
+            if (a.mode == 0) {
+                ta = il >> 4;
+                ca = il & 15;
+                tb = 3 + (jl >> 4);
+                cb = jl & 15;
+            } else {
+                side_pos(il, noA, sa.nrun0, ta, ca);
+                side_pos(jl, noB, sb.nrun0, tb, cb);
+                tb += 3;
             }
-            if (bad) continue;
-            const int noA = 4 * a.group_nmol[A], noB = 4 * a.group_nmol[B];
-            const int* lvl = a.pr_lvl + (size_t)e * (kMaxSub + 1);
-            for (int sub = 0; sub < kMaxSub; ++sub) {
-                const int q0 = lvl[sub], q1 = lvl[sub + 1];
-                if (q0 == np) break;
-                for (int q = q0 + lane; q < q1; q += 32) {
-                    const size_t qq = (size_t)e * kOrthoCap + q;
-                    const unsigned ij = a.pr_ij[qq];
-                    const int il = ij & 255, jl = ij >> 8;
-                    int ta, ca, tb, cb;
-                    if (a.mode == 0) {
-                        ta = il >> 4;
-                        ca = il & 15;
-                        tb = 3 + (jl >> 4);
-                        cb = jl & 15;
-                    } else {
-                        side_pos(il, noA, a.group_not[A], ta, ca);
-                        side_pos(jl, noB, a.group_not[B], tb, cb);
-                        tb += 3;
-                    }
-                    T* pi = vals + (size_t)slot[ta] * 16 + ca;
-                    T* pj = vals + (size_t)slot[tb] * 16 + cb;
-                    const T x = *pi, y = *pj;
-                    T xn, yn;
-                    if (a.mode == 0) {
-                        const T c = cs[2 * qq], s = cs[2 * qq + 1];
-                        xn = c * x + s * y;
-                        yn = -s * x + c * y;
-                    } else {
-                        const T h = cs[2 * qq];
-                        xn = x - h * y;
-                        yn = y - h * x;
-                    }
-                    *pi = fabs((double)xn) < a.trunc ? (T)0 : xn;
-                    *pj = fabs((double)yn) < a.trunc ? (T)0 : yn;
-                }
-                __syncwarp();
+            T* pi = panel + (ta * 16 + ca) * kNRp + row;
+            T* pj = panel + (tb * 16 + cb) * kNRp + row;
+            const T x = *pi, y = *pj;
+            T xn, yn;
+            if (a.mode == 0) {
+                const T c = pcs[2 * q], s = pcs[2 * q + 1];
+                xn = c * x + s * y;
+                yn = -s * x + c * y;
+            } else {
+                const T h = pcs[2 * q];
+                xn = x - h * y;
+                yn = y - h * x;
             }
+            *pi = fabs((double)xn) < a.trunc ? (T)0 : xn;
+            *pj = fabs((double)yn) < a.trunc ? (T)0 : yn;
         }
         __syncthreads();
-        if (s_abort) return;
     }
-    // write back, tiles sorted by id
-    const int n = s_n;
-    for (int i = threadIdx.x; i < np2; i += blockDim.x) keys[i] = 0xffffffffu;
-    __syncthreads();
-    for (int t = threadIdx.x; t < a.n_tiles; t += blockDim.x)
-        if (map[t] >= 0) keys[map[t]] = ((unsigned)t << 16) | (unsigned)map[t];
-    __syncthreads();
-    for (int k = 2; k <= np2; k <<= 1)
-        for (int j = k >> 1; j > 0; j >>= 1) {
-            for (int i = threadIdx.x; i < np2; i += blockDim.x) {
-                int l = i ^ j;
-                if (l > i) {
-                    bool up = (i & k) == 0;
-                    unsigned x = keys[i], y = keys[l];
-                    if ((x > y) == up) {
-                        keys[i] = y;
-                        keys[l] = x;
-                    }
-                }
-            }
-            __syncthreads();
-        }
-    T* outv = (T*)a.out_val;
-    if (krow == 0) {
-        for (int s = threadIdx.x; s < n; s += blockDim.x) a.out_tile[(size_t)r * cap + s] = (int)(keys[s] >> 16);
-        if (threadIdx.x == 0) a.out_nt[r] = n;
-    }
-    for (int idx = threadIdx.x; idx < n * 16; idx += blockDim.x) {
-        const int s = idx >> 4, c = idx & 15;
-        const int src = keys[s] & 0xffffu;
-        outv[(((size_t)r * cap + s) * 6 + krow) * 16 + c] = vals[(size_t)src * 16 + c];
+    for (int idx = threadIdx.x; idx < nk * 6 * kTileVals; idx += blockDim.x) {
+        const int rb = idx / (6 * kTileVals);
+        const int rem = idx % (6 * kTileVals);
+        const int p = rem / kTileVals, v = rem % kTileVals;
+        const int kr = v >> 4, col = v & 15;
+        const int sl = s_slot[rb][p];
+        if (sl >= 0) val[((size_t)s_row[rb] * a.cap + sl) * kTileVals + v] = panel[(p * 16 + col) * kNRp + rb * 6 + kr];
     }
 }
 
@@ -659,31 +740,16 @@ cudaError_t launch_ortho_prepare(Ctx* c, int w, double tol) {
     return c->prec == SSCF_FP64 ? ortho_prepare_t<double>(c, w, tol) : ortho_prepare_t<float>(c, w, tol);
 }
 
-size_t apply_smem_bytes(const Ctx* c) {
-    int np2 = 1;
-    while (np2 < c->cap) np2 <<= 1;
-    size_t b = (size_t)c->cap * 16 * c->tsize + (size_t)np2 * 4 + (size_t)((c->n_tiles + 1) & ~1) * 2 +
-               (size_t)2 * ((c->n_groups + 31) / 32) * 4;
-    return (b + 15) & ~(size_t)15;
-}
-
 template <typename T>
-static cudaError_t apply_t(Ctx* c, int mode, int which) {
-    const size_t smem = apply_smem_bytes(c);
-    if (smem > 220 * 1024) return cudaErrorInvalidValue;
-    cudaError_t e = cudaFuncSetAttribute(k_apply<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    ApplyArgs a;
+static void fill_args(Ctx* c, SweepArgs& a, int mode, int which) {
     a.mode = mode;
     a.which = which;
     a.n_tiles = c->n_tiles;
-    a.n_occ_tiles = c->n_occ_tiles;
     a.n_groups = c->n_groups;
     a.cap = c->cap;
-    a.n_colours = c->n_colours;
+    a.n_blk = mode == 0 ? c->n_gnb : (int)c->h_ocolour_blk.size();
     a.trunc = mode == 0 ? c->prm.eps : 1e-3 * c->prm.eps;
-    a.colour_ptr = mode == 0 ? c->d_colour_ptr : c->d_ocolour_ptr;
-    a.colour_blk = mode == 0 ? c->d_colour_blk : c->d_ocolour_blk;
+    a.blk = mode == 0 ? c->d_colour_blk : c->d_ocolour_blk;
     a.gnb_row = c->d_gnb_row;
     a.gnb_col = c->d_gnb_col;
     a.group_nmol = c->d_group_nmol;
@@ -699,8 +765,17 @@ static cudaError_t apply_t(Ctx* c, int mode, int which) {
     a.pr_lvl = c->d_pr_lvl;
     a.pr_ij = c->d_pr_ij;
     a.pr_cs = c->d_pr_cs;
-    a.pr_touch = c->d_pr_touch;
     a.dsc = c->d_scale;
+    a.cci_ptr = c->d_cci_ptr;
+    a.cci_row = c->d_cci_row;
+    a.cci_slot = c->d_cci_slot;
+    a.err = &c->d_sc->err;
+}
+
+template <typename T>
+static cudaError_t closure_t(Ctx* c, int mode, int which) {
+    SweepArgs a;
+    fill_args<T>(c, a, mode, which);
     const int in = c->cur, out = 1 - c->cur;
     a.in_nt = c->d_c_nt[in];
     a.in_tile = c->d_c_tile[in];
@@ -708,9 +783,38 @@ static cudaError_t apply_t(Ctx* c, int mode, int which) {
     a.out_nt = c->d_c_nt[out];
     a.out_tile = c->d_c_tile[out];
     a.out_val = c->d_c_val[out];
-    a.err = &c->d_sc->err;
-    k_apply<T><<<c->n_mol * 6, kApplyWarps * 32, smem, c->stream>>>(a);
+    const size_t smem = closure_smem_bytes(c);
+    if (smem > 200 * 1024) return cudaErrorInvalidValue;
+    cudaError_t e = cudaFuncSetAttribute(k_closure<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_closure<T><<<c->n_mol, 256, smem, c->stream>>>(a);
+    c->cur = out;
     return cudaGetLastError();
+}
+
+template <typename T>
+static cudaError_t apply_t(Ctx* c, int mode, int which) {
+    SweepArgs a;
+    fill_args<T>(c, a, mode, which);
+    a.in_nt = a.out_nt = c->d_c_nt[c->cur];
+    a.in_tile = a.out_tile = c->d_c_tile[c->cur];
+    a.in_val = a.out_val = c->d_c_val[c->cur];
+    const size_t smem = (size_t)6 * 16 * kNRp * sizeof(T) + (size_t)2 * kOrthoCap * sizeof(T) + (size_t)kOrthoCap * 2;
+    cudaError_t e = cudaFuncSetAttribute(k_apply_colour<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const std::vector<int>& ptr = mode == 0 ? c->h_colour_ptr : c->h_ocolour_ptr;
+    const int gx = (c->n_mol + kChunk - 1) / kChunk;
+    for (int col = 0; col < c->n_colours; ++col) {
+        const int nb = ptr[col + 1] - ptr[col];
+        if (nb == 0) continue;
+        dim3 grid(gx, nb);
+        k_apply_colour<T><<<grid, 256, smem, c->stream>>>(a, ptr[col]);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_closure(Ctx* c, int mode, int which) {
+    return c->prec == SSCF_FP64 ? closure_t<double>(c, mode, which) : closure_t<float>(c, mode, which);
 }
 
 cudaError_t launch_apply(Ctx* c, int mode, int which) {
@@ -718,7 +822,7 @@ cudaError_t launch_apply(Ctx* c, int mode, int which) {
 }
 
 cudaError_t launch_compact(Ctx* c) {
-    const int in = 1 - c->cur, out = c->cur;
+    const int in = c->cur, out = 1 - c->cur;
     if (c->prec == SSCF_FP64)
         k_compact<double><<<c->n_mol, 256, 0, c->stream>>>(c->cap, c->d_c_nt[in], c->d_c_tile[in],
                                                            (const double*)c->d_c_val[in], c->d_c_nt[out],
@@ -727,6 +831,7 @@ cudaError_t launch_compact(Ctx* c) {
         k_compact<float><<<c->n_mol, 256, 0, c->stream>>>(c->cap, c->d_c_nt[in], c->d_c_tile[in],
                                                           (const float*)c->d_c_val[in], c->d_c_nt[out],
                                                           c->d_c_tile[out], (float*)c->d_c_val[out]);
+    c->cur = out;
     return cudaGetLastError();
 }
 

@@ -191,6 +191,17 @@ struct Ctx {
     DeviceScalars* h_sc = nullptr;   // pinned mirror
 
     std::vector<void*> allocations;
+
+    // per-launcher CUDA-event timing (off by default)
+    bool prof = false;
+    struct ProfRec {
+        int id;
+        cudaEvent_t e0, e1;
+    };
+    std::vector<ProfRec> prof_pending;
+    std::vector<std::string> prof_names;
+    std::vector<double> prof_ms;
+    std::vector<long long> prof_calls;
 };
 
 // ---- memory -----------------------------------------------------------------
@@ -217,8 +228,9 @@ cudaError_t launch_density(Ctx* c);
 // schedules and sweeps
 cudaError_t launch_select_rot(Ctx* c);
 cudaError_t launch_ortho_prepare(Ctx* c, int which, double tol);
-cudaError_t launch_apply(Ctx* c, int mode, int which);   // mode 0 rotations, 1 combinations
-cudaError_t launch_compact(Ctx* c);
+cudaError_t launch_closure(Ctx* c, int mode, int which); // structural fill; cur <- other
+cudaError_t launch_apply(Ctx* c, int mode, int which);   // mode 0 rotations, 1 combinations; in place
+cudaError_t launch_compact(Ctx* c);                      // drop all-zero tiles; cur <- other
 // charges
 cudaError_t launch_charges_finish(Ctx* c, bool mix);
 
