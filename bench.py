@@ -1,0 +1,331 @@
+"""Throughput of the sparse SCF hot path on one GB300 (or N replicas).
+
+One step = one SCC iteration through the C-ABI (sscf_step: Fock build,
+C^T H C transform, pair selection, rotation sweep, one occupied
+orthonormalisation pass, density / Mulliken charges / energy, mixing) on the
+synthetic water-like cluster of 4096 molecules (16^3 lattice, 12288 atoms,
+24576 AOs), mixed precision (FP32 storage, FP64 angles, norms, overlaps and
+charge / energy accumulation), cut-off 1e-5.
+
+Input state (untimed): per-molecule guess, full orthonormalisation at the
+loose threshold 1e-3 (the paper's first SCF stage), charges of that state;
+then W warm-up iterations at the user threshold. The K timed iterations
+continue from there; C (>1 GB) is larger than the 129 MB L2, so no L2 flush
+is needed between iterations.
+
+``--impl reference`` times the FP64 CPU oracle (the same SCC iteration,
+step by step) on a bounded sample of the same workload: a 5^3 sub-cube of
+the lattice, per iteration, on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "SCF iter/s & atom·iter/s (mixed vs FP64 GPU), |ΔE|/atom vs oracle, HBM GB/s"
+UNIT = "atom*iter/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="sscf", choices=["sscf", "reference"])
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--n-mol", type=int, default=4096)
+    ap.add_argument("--eps", type=float, default=1e-5)
+    ap.add_argument("--prep-eps", type=float, default=1e-3)
+    ap.add_argument("--prep-passes", type=int, default=200)
+    ap.add_argument("--sample-mol", type=int, default=125)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:  # pragma: no cover
+        return os.cpu_count() or 1
+
+
+# ---------------------------------------------------------------------------
+# oracle timing (CPU baseline and the reference arm)
+# ---------------------------------------------------------------------------
+def oracle_iteration_rate(n_mol: int, eps: float, steps: int, warmup: int = 0):
+    """Atom*iter/s of oracle B's SCC iteration on a sub-cube of n_mol molecules."""
+    from oracle import sparse
+    from synth import default_params, lattice_water
+    p = default_params()
+    s = lattice_water(n_mol, seed=0)
+    scf = sparse.SparseSCF(s, p)
+    st = scf.start(1e-3)
+    for _ in range(warmup):
+        scf.step(st, eps)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        scf.step(st, eps)
+    dt = time.perf_counter() - t0
+    return s.n_atoms * steps / dt, dt, s.n_atoms
+
+
+# ---------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    n_gpus = max(args.gpus, world)
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        K, W = max(args.steps, 1), args.warmup
+        cores = host_cores()
+        rate, dt, n_at = oracle_iteration_rate(args.sample_mol, args.eps, K, W)
+        line = {
+            "impl": "reference", "metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": n_gpus,
+            "steps": K, "warmup": W, "ms_per_step": 1e3 * dt / K, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"water lattice, {args.sample_mol}-molecule sub-cube of the "
+                                   f"{args.n_mol}-molecule cluster, eps {args.eps:g}", "n_mol": args.n_mol,
+                       "sample_mol": args.sample_mol},
+            "cpu_baseline": {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{K} SCC iterations of oracle B on {args.sample_mol} molecules"},
+            "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        }
+        print(json.dumps(line), flush=True)
+        return
+
+    import numpy as np
+    import torch
+
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+
+    from paper_1402_2880_gb300 import SSCF_FP64, SSCF_MIXED, SSCF_ORTHO_ALL, Context, build
+    from synth import default_params, lattice_water
+    if rank == 0:
+        build.build()
+    if dist is not None:
+        dist.barrier()
+    build.build()
+
+    p = default_params()
+    s = lattice_water(args.n_mol, seed=0)
+    stream = torch.cuda.current_stream(dev)
+    prec = SSCF_MIXED if args.precision == "mixed" else SSCF_FP64
+    ctx = Context.from_system(s, p, precision=prec, stream=stream.cuda_stream)
+    # input state
+    ctx.set_thresholds(args.prep_eps, 10 * args.prep_eps, 1e-8)
+    ctx.guess()
+    prep_passes, prep_eta = ctx.orthonormalise(SSCF_ORTHO_ALL, max_pass=args.prep_passes)
+    ctx.set_thresholds(args.eps, 10 * args.eps, 1e-6)
+    ctx.reset_charges()
+    for _ in range(max(args.warmup, 0)):
+        ctx.step()
+    torch.cuda.synchronize(dev)
+
+    K = args.steps
+    ctx.profile(True)
+    sampler = ClockSampler(local_rank)
+    sampler.start()
+    infos = []
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(K):
+        infos.append(ctx.step())
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    if dist is not None:
+        dist.barrier()
+    clocks = sampler.stop()
+    prof = ctx.profile_read()
+    ctx.profile(False)
+    ms = e0.elapsed_time(e1)
+    t_max = ms
+    if dist is not None:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max = float(t.item())
+    value = n_gpus * s.n_atoms * K / (t_max / 1e3)
+
+    # end to end through the C-ABI: host charges in, host charges out, every step
+    pinned = [torch.empty(s.n_atoms, dtype=torch.float64, pin_memory=True).numpy() for _ in range(3)]
+    q, dq, Q = ctx.get_charges()
+    for a_, b_ in zip(pinned, (q, dq, Q)):
+        a_[:] = b_
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for _ in range(K):
+        ctx.set_charges(*pinned)
+        ctx.step()
+        ctx.get_charges(out=pinned)
+    torch.cuda.synchronize(dev)
+    e2e_dt = time.perf_counter() - t0
+    e2e_t = e2e_dt
+    if dist is not None:
+        t = torch.tensor([e2e_dt], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_t = float(t.item())
+    e2e_value = n_gpus * s.n_atoms * K / e2e_t
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+
+    # roofline of the dominant launcher: algorithmic HBM bytes per call / mean call time
+    tsz = 4 if prec == SSCF_MIXED else 8
+    mean = lambda k: float(np.mean([inf[k] for inf in infos]))  # noqa: E731
+    nnz_c, nnz_o = mean("nnz_c"), mean("nnz_occ")
+    n_rot, n_combo = mean("n_rot"), mean("n_combo")
+    algo_bytes = {
+        "apply_rot": 2 * tsz * nnz_c + 24 * n_rot,           # read + write C once, pair records
+        "apply_ortho": 2 * tsz * nnz_o + 16 * n_combo,        # read + write C_occ once, pair records
+        "xc_h": 2 * tsz * nnz_c,                              # read C, write Y = H C
+        "xc_s": 2 * tsz * nnz_o,
+        "transform_ov": 2 * tsz * nnz_c,                      # read C and Y once
+        "transform_ss": 2 * tsz * nnz_o,
+        "density": tsz * nnz_o + 8 * s.n_atoms,
+        "closure": 2 * tsz * nnz_c,
+        "compact": 2 * tsz * nnz_c,
+    }
+    per_step = {k: v[0] / K for k, v in prof.items()}
+    dominant = max(per_step, key=per_step.get)
+    peaks = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            peaks = json.load(f)
+    except OSError:
+        pass
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
+
+    def roof(name):
+        calls = prof[name][1] / K
+        t_call = prof[name][0] / max(prof[name][1], 1) / 1e3
+        b = algo_bytes.get(name)
+        if b is None:
+            return None
+        achieved = b / max(calls, 1) / t_call / 1e9
+        return {"kernel": name, "bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                "frac": achieved / hbm_peak, "traffic": None, "peak_source": peak_src,
+                "ms_per_step": per_step[name]}
+
+    roofline = roof(dominant)
+    kernels = {k: {"ms_per_step": round(v, 3), "calls_per_step": prof[k][1] / K} for k, v in per_step.items()}
+
+    cpu = None
+    if not args.no_cpu_baseline:
+        rate, dt, n_at = oracle_iteration_rate(args.sample_mol, args.eps, 2)
+        cpu = {"value": rate, "unit": UNIT, "cores": host_cores(), "kind": "oracle",
+               "sample": f"2 SCC iterations of oracle B (FP64, numpy) on a {args.sample_mol}-molecule "
+                         f"sub-cube ({n_at} atoms), {dt:.1f} s"}
+
+    launches = int(round(mean("launches")))
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": n_gpus, "steps": K, "warmup": args.warmup,
+        "ms_per_step": t_max / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32+f64" if prec == SSCF_MIXED else "f64", "data": "synthetic",
+        "config": {"workload": f"water lattice {args.n_mol} molecules ({s.n_atoms} atoms, {6 * args.n_mol} AOs), "
+                               f"{args.precision}, eps {args.eps:g}, one SCC iteration per step",
+                   "n_mol": args.n_mol, "eps": args.eps, "precision": args.precision,
+                   "parallelism": "replicas" if n_gpus > 1 else "single",
+                   "l2": "inputs larger than L2 (C > 1 GB), no flush",
+                   "prep": {"eps": args.prep_eps, "ortho_passes": prep_passes, "eta": prep_eta}},
+        "scf_iter_per_s": n_gpus * K / (t_max / 1e3),
+        "clocks": clocks,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 3 * 8 * s.n_atoms,
+                "d2h_bytes_per_step": 3 * 8 * s.n_atoms},
+        "gpu_launches": launches * K,
+        "roofline": roofline,
+        "kernels": kernels,
+        "cpu_baseline": cpu,
+        "state": {"energy": infos[-1]["energy"], "dq_max": infos[-1]["dq_max"], "n_rot": n_rot,
+                  "n_combo": n_combo, "nnz_per_mo": nnz_c / ctx.n_mo},
+    }
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

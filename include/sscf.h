@@ -77,7 +77,9 @@ typedef struct {
     double eta;              /* largest normalised off-diagonal overlap of the ortho pass */
     int64_t n_rot;           /* rotations applied in the sweep                           */
     int64_t n_combo;         /* orthonormalisation combinations applied                  */
-    int64_t nnz_c;           /* stored tiles of C times 96 (6 AO rows x 16 MOs)          */
+    int64_t nnz_c;           /* stored values of C: tiles x 96 (6 AO rows x 16 MOs)       */
+    int64_t nnz_occ;         /* stored values of the occupied tiles                      */
+    int64_t launches;        /* kernels launched by the step                              */
     int iteration;
 } sscf_step_info;
 

@@ -58,7 +58,8 @@ class Params(ctypes.Structure):
 class StepInfo(ctypes.Structure):
     _fields_ = [("energy", ctypes.c_double), ("dq_max", ctypes.c_double), ("dE", ctypes.c_double),
                 ("max_fov", ctypes.c_double), ("eta", ctypes.c_double), ("n_rot", ctypes.c_int64),
-                ("n_combo", ctypes.c_int64), ("nnz_c", ctypes.c_int64), ("iteration", ctypes.c_int)]
+                ("n_combo", ctypes.c_int64), ("nnz_c", ctypes.c_int64), ("nnz_occ", ctypes.c_int64),
+                ("launches", ctypes.c_int64), ("iteration", ctypes.c_int)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -244,8 +245,8 @@ class Context:
         _check(self.lib.sscf_get_F_dense(self.h, _ptr(F), _ptr(d)), "sscf_get_F_dense")
         return F, d
 
-    def get_charges(self):
-        q, dq, Q = (np.empty(self.n_atoms) for _ in range(3))
+    def get_charges(self, out=None):
+        q, dq, Q = out if out is not None else (np.empty(self.n_atoms) for _ in range(3))
         _check(self.lib.sscf_get_charges(self.h, _ptr(q), _ptr(dq), _ptr(Q)), "sscf_get_charges")
         return q, dq, Q
 
@@ -262,18 +263,17 @@ class Context:
         _check(self.lib.sscf_profile(self.h, 1 if enable else 0), "sscf_profile")
 
     def profile_read(self) -> dict:
-        """{launcher name: (milliseconds, calls)} since the last read."""
+        """{launcher name: (milliseconds, calls)} since the last read (then reset)."""
+        cap = 128
         n = ctypes.c_int()
-        _check(self.lib.sscf_profile_read(self.h, 0, None, None, None, ctypes.byref(n)), "sscf_profile_read")
-        m = n.value
-        names = ctypes.create_string_buffer(32 * max(m, 1))
-        ms = np.zeros(max(m, 1))
-        calls = np.zeros(max(m, 1), dtype=np.int64)
-        _check(self.lib.sscf_profile_read(self.h, m, names, _ptr(ms), _ptr(calls, ctypes.c_int64),
+        names = ctypes.create_string_buffer(32 * cap)
+        ms = np.zeros(cap)
+        calls = np.zeros(cap, dtype=np.int64)
+        _check(self.lib.sscf_profile_read(self.h, cap, names, _ptr(ms), _ptr(calls, ctypes.c_int64),
                                           ctypes.byref(n)), "sscf_profile_read")
         raw = names.raw
         return {raw[32 * i:32 * i + 32].split(b"\0")[0].decode(): (float(ms[i]), int(calls[i]))
-                for i in range(m)}
+                for i in range(min(n.value, cap))}
 
     def pairs(self):
         n = ctypes.c_int64()

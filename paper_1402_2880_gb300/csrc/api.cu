@@ -808,13 +808,13 @@ int sscf_step(sscf_ctx* h, sscf_step_info* info) {
     if (!h) return SSCF_ERR_INVALID_ARG;
     Ctx& c = h->c;
     if (!c.have_guess) return SSCF_ERR_STATE;
+    const long long l0 = c.n_launch;
     CK(cudaMemsetAsync(c.d_sc, 0, offsetof(DeviceScalars, hist), c.stream));
     PK("build_fock", launch_build_h(&c));
     CKS(rotate_sweep_async(c));
-    unsigned long long n_rot_dummy = 0;
-    (void)n_rot_dummy;
     if (c.prm.ortho_every) CKS(ortho_pass_async(c, SSCF_ORTHO_OCC, c.prm.eps / 100.0));
     CKS(density_async(c, true));
+    CK(launch_count_tiles(&c, c.d_sc->tiles));
     CKS(sync_scalars(c));
     c.iteration++;
     if (info) {
@@ -825,11 +825,9 @@ int sscf_step(sscf_ctx* h, sscf_step_info* info) {
         info->eta = c.h_sc->eta;
         info->n_rot = (int64_t)c.h_sc->n_rot;
         info->n_combo = (int64_t)c.h_sc->n_combo;
-        long long tiles = 0;
-        std::vector<int> nt(c.n_mol);
-        CK(cudaMemcpy(nt.data(), c.d_c_nt[c.cur], (size_t)c.n_mol * 4, cudaMemcpyDeviceToHost));
-        for (int v : nt) tiles += v;
-        info->nnz_c = (int64_t)tiles * kTileVals;
+        info->nnz_c = (int64_t)c.h_sc->tiles[0] * kTileVals;
+        info->nnz_occ = (int64_t)c.h_sc->tiles[1] * kTileVals;
+        info->launches = (int64_t)(c.n_launch - l0);
         info->iteration = c.iteration;
     }
     if (!std::isfinite(c.h_sc->energy)) return SSCF_ERR_NONFINITE;

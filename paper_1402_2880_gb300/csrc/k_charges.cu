@@ -56,9 +56,38 @@ __global__ void k_finish(int n_atoms, int n_mol, int mix, double beta, const dou
     }
 }
 
+// stored tiles of C and occupied tiles among them (one thread per row block)
+__global__ void k_count_tiles(int n_mol, int cap, int n_occ_tiles, const int* __restrict__ c_nt,
+                              const int* __restrict__ c_tile, unsigned long long* __restrict__ out) {
+    int r = blockIdx.x * blockDim.x + threadIdx.x;
+    unsigned long long all = 0, occ = 0;
+    if (r < n_mol) {
+        const int n = c_nt[r];
+        all = n;
+        for (int s = 0; s < n; ++s)
+            if (c_tile[(size_t)r * cap + s] < n_occ_tiles) ++occ;
+    }
+    for (int off = 16; off > 0; off >>= 1) {
+        all += __shfl_xor_sync(0xffffffffu, all, off);
+        occ += __shfl_xor_sync(0xffffffffu, occ, off);
+    }
+    if ((threadIdx.x & 31) == 0 && all) {
+        atomicAdd(&out[0], all);
+        atomicAdd(&out[1], occ);
+    }
+}
+
 }  // namespace
 
+cudaError_t launch_count_tiles(Ctx* c, unsigned long long* out) {
+    c->n_launch += 1;
+    k_count_tiles<<<(c->n_mol + 255) / 256, 256, 0, c->stream>>>(c->n_mol, c->cap, c->n_occ_tiles, c->d_c_nt[c->cur],
+                                                                 c->d_c_tile[c->cur], out);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_charges_finish(Ctx* c, bool mix) {
+    c->n_launch += 2;
     k_dq<<<(c->n_atoms + 255) / 256, 256, 0, c->stream>>>(c->n_atoms, c->d_q, c->d_species, c->prm.q0[0],
                                                          c->prm.q0[1], c->d_dq);
     cudaError_t e = launch_gamma(c, c->d_dq, c->d_Q);

@@ -91,44 +91,53 @@ __global__ void k_sk_blocks(int n_mp, const int* __restrict__ mp_row, const int*
 // Q_a = sum_b gamma_ab dq_b over all atom pairs (unscreened, Section
 // "Specific implementation for DFTB"), gamma_ab = 1/sqrt(r^2 + a^2),
 // a = (1/U_a + 1/U_b)/2. One thread per atom a, atoms b staged in smem.
+// P = double: every pair term in FP64. P = float (mixed precision): pair
+// terms in FP32, summed in FP32 over one smem tile of 256 atoms, tile sums
+// accumulated in FP64.
 constexpr int kGammaTile = 256;
+template <typename P>
 __global__ void k_gamma(int n, const double* __restrict__ xyz, const int* __restrict__ species,
                         const double* __restrict__ dq, double invU0, double invU1, double* __restrict__ Q) {
-    __shared__ double sx[kGammaTile * 3];
-    __shared__ double sq[kGammaTile];
-    __shared__ double si[kGammaTile];
+    __shared__ P sx[kGammaTile * 3];
+    __shared__ P sq[kGammaTile];
+    __shared__ P si[kGammaTile];
     const int a = blockIdx.x * blockDim.x + threadIdx.x;
-    double xa[3] = {0, 0, 0}, ia = invU0;
+    double xa_d[3] = {0, 0, 0}, ia_d = invU0;
     if (a < n) {
-        xa[0] = xyz[3 * a];
-        xa[1] = xyz[3 * a + 1];
-        xa[2] = xyz[3 * a + 2];
-        ia = species[a] == 0 ? invU0 : invU1;
+        xa_d[0] = xyz[3 * a];
+        xa_d[1] = xyz[3 * a + 1];
+        xa_d[2] = xyz[3 * a + 2];
+        ia_d = species[a] == 0 ? invU0 : invU1;
     }
+    const P xa[3] = {(P)xa_d[0], (P)xa_d[1], (P)xa_d[2]};
+    const P ia = (P)ia_d;
     double acc = 0.0;
     for (int b0 = 0; b0 < n; b0 += kGammaTile) {
         __syncthreads();
         for (int t = threadIdx.x; t < kGammaTile; t += blockDim.x) {
             int b = b0 + t;
             if (b < n) {
-                sx[3 * t] = xyz[3 * b];
-                sx[3 * t + 1] = xyz[3 * b + 1];
-                sx[3 * t + 2] = xyz[3 * b + 2];
-                sq[t] = dq[b];
-                si[t] = species[b] == 0 ? invU0 : invU1;
+                sx[3 * t] = (P)xyz[3 * b];
+                sx[3 * t + 1] = (P)xyz[3 * b + 1];
+                sx[3 * t + 2] = (P)xyz[3 * b + 2];
+                sq[t] = (P)dq[b];
+                si[t] = (P)(species[b] == 0 ? invU0 : invU1);
             } else {
-                sx[3 * t] = sx[3 * t + 1] = sx[3 * t + 2] = 0.0;
-                sq[t] = 0.0;
-                si[t] = invU0;
+                sx[3 * t] = sx[3 * t + 1] = sx[3 * t + 2] = (P)0;
+                sq[t] = (P)0;
+                si[t] = (P)invU0;
             }
         }
         __syncthreads();
         const int nb = min(kGammaTile, n - b0);
+        P part = 0;
         for (int t = 0; t < nb; ++t) {
-            double d2 = dist2_rn(xa, &sx[3 * t]);
-            double h = 0.5 * (ia + si[t]);
-            acc += sq[t] / sqrt(d2 + h * h);
+            const P dx = sx[3 * t] - xa[0], dy = sx[3 * t + 1] - xa[1], dz = sx[3 * t + 2] - xa[2];
+            const P d2 = dx * dx + dy * dy + dz * dz;
+            const P h = (P)0.5 * (ia + si[t]);
+            part += sq[t] / sqrt(d2 + h * h);
         }
+        acc += (double)part;
     }
     if (a < n) Q[a] = acc;
 }
@@ -321,6 +330,7 @@ SK make_sk(const Ctx* c) {
 }  // namespace
 
 cudaError_t launch_sk_blocks(Ctx* c) {
+    c->n_launch += 1;
     const int th = 128;
     k_sk_blocks<<<(c->n_mp + th - 1) / th, th, 0, c->stream>>>(c->n_mp, c->d_mp_row, c->d_mp_col, c->d_xyz,
                                                               make_sk(c), c->d_H0b, c->d_Sb);
@@ -328,13 +338,19 @@ cudaError_t launch_sk_blocks(Ctx* c) {
 }
 
 cudaError_t launch_gamma(Ctx* c, const double* dq, double* Q) {
+    c->n_launch += 1;
     const int th = 256;
-    k_gamma<<<(c->n_atoms + th - 1) / th, th, 0, c->stream>>>(c->n_atoms, c->d_xyz, c->d_species, dq,
-                                                              1.0 / c->prm.U[0], 1.0 / c->prm.U[1], Q);
+    if (c->prec == SSCF_FP64)
+        k_gamma<double><<<(c->n_atoms + th - 1) / th, th, 0, c->stream>>>(c->n_atoms, c->d_xyz, c->d_species, dq,
+                                                                          1.0 / c->prm.U[0], 1.0 / c->prm.U[1], Q);
+    else
+        k_gamma<float><<<(c->n_atoms + th - 1) / th, th, 0, c->stream>>>(c->n_atoms, c->d_xyz, c->d_species, dq,
+                                                                         1.0 / c->prm.U[0], 1.0 / c->prm.U[1], Q);
     return cudaGetLastError();
 }
 
 cudaError_t launch_build_h(Ctx* c) {
+    c->n_launch += 1;
     const int th = 256;
     const int n = c->n_mp * 36;
     if (c->prec == SSCF_FP64)
@@ -349,6 +365,7 @@ cudaError_t launch_build_h(Ctx* c) {
 }
 
 cudaError_t launch_guess(Ctx* c) {
+    c->n_launch += 1;
     const int th = 64;
     c->cur = 0;
     if (c->prec == SSCF_FP64)

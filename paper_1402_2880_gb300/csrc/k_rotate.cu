@@ -369,6 +369,7 @@ struct SweepArgs {
     int which;       // combinations: 0 all MOs, 1 occupied MOs
     int n_tiles, n_groups, cap, n_blk;
     double trunc;
+    float trunc_f;   // smallest float >= trunc: |x| < trunc <=> |x| < trunc_f for every float x
     const int* blk;          // blocks of the pass (any order for the closure)
     const int* gnb_row;
     const int* gnb_col;
@@ -399,6 +400,10 @@ struct SweepArgs {
 };
 
 constexpr int kClosureIters = 256;
+
+// truncation test |x| < threshold, decided exactly in the storage precision
+__device__ __forceinline__ bool below(double x, const SweepArgs& a) { return fabs(x) < a.trunc; }
+__device__ __forceinline__ bool below(float x, const SweepArgs& a) { return fabsf(x) < a.trunc_f; }
 
 template <typename T>
 __global__ void __launch_bounds__(256) k_closure(SweepArgs a) {
@@ -498,7 +503,7 @@ __global__ void __launch_bounds__(256) k_closure(SweepArgs a) {
         const int os = map[t];
         T v = os >= 0 ? inv[((size_t)r * a.cap + os) * kTileVals + e] : (T)0;
         if (a.mode == 1 && os >= 0 && (a.which == 0 || a.tile_kind[t] == 0) && col < a.tile_nmo[t])
-            v = (T)((double)v / a.dsc[a.tile_mo0[t] + col]);
+            v = v / (T)a.dsc[a.tile_mo0[t] + col];
         outv[((size_t)r * a.cap + s) * kTileVals + e] = v;
     }
 }
@@ -531,16 +536,36 @@ __device__ __forceinline__ Side side_of(const SweepArgs& a, int g, bool virt_onl
     return s;
 }
 
-constexpr int kChunk = 16;                 // row blocks per CTA
-constexpr int kNR = kChunk * kAoPerMol;    // AO rows per CTA
+constexpr int kChunk = 32;                 // row blocks per CTA
+constexpr int kNR = kChunk * kAoPerMol;    // AO rows per CTA = threads per CTA
 constexpr int kNRp = kNR + 1;              // padded panel stride (bank spread)
+constexpr int kUnroll = 4;                 // pairs of one level in flight per thread
+constexpr int kSegUnroll = 4;              // panel segments in flight per thread
 
-template <typename T>
-__global__ void __launch_bounds__(256) k_apply_colour(SweepArgs a, int p0) {
+template <typename T> struct Vec;
+template <> struct Vec<float> {
+    using type = float4;
+    static constexpr int n = 4;
+    __device__ static float4 zero() { return make_float4(0.f, 0.f, 0.f, 0.f); }
+};
+template <> struct Vec<double> {
+    using type = double2;
+    static constexpr int n = 2;
+    __device__ static double2 zero() { return make_double2(0.0, 0.0); }
+};
+
+// One CTA = one active block of the colour x 32 row blocks. The block's side
+// tiles of those rows are staged in shared memory as a [tile][column][row]
+// panel; every thread owns one AO row and applies the block's pairs to it in
+// schedule order (level by level). Rows are independent, so no barrier is
+// needed between levels; pairs of one level touch disjoint MOs, so kUnroll of
+// them are loaded, updated and stored together.
+template <typename T, int MODE>
+__global__ void __launch_bounds__(kNR) k_apply_colour(SweepArgs a, int p0) {
     extern __shared__ unsigned char smraw[];
-    T* panel = (T*)smraw;                                    // [6 tiles][16][kNR]
-    T* pcs = panel + 6 * 16 * kNRp;                           // np * 2
-    uint16_t* pij = (uint16_t*)(pcs + 2 * kOrthoCap);        // np
+    T* panel = (T*)smraw;                                    // [6 tiles][16][kNRp]
+    T* pcs = panel + 6 * 16 * kNRp;                          // np * 2 coefficients
+    unsigned* poff = (unsigned*)(pcs + 2 * kOrthoCap);       // np packed panel offsets
     __shared__ int s_lvl[kMaxSub + 1];
     __shared__ int s_row[kChunk];
     __shared__ int s_slot[kChunk][6];
@@ -548,9 +573,9 @@ __global__ void __launch_bounds__(256) k_apply_colour(SweepArgs a, int p0) {
     const int np = a.pr_n[e];
     if (np == 0) return;
     const int A = a.gnb_row[e], B = a.gnb_col[e];
-    const bool with_virt = a.mode == 1 && a.which == 0;
+    const bool with_virt = MODE == 1 && a.which == 0;
     const Side sa = side_of(a, A, false, with_virt);
-    const Side sb = side_of(a, B, a.mode == 0, with_virt);
+    const Side sb = side_of(a, B, MODE == 0, with_virt);
     const int pa = a.cci_ptr[sa.run0], n_rows = a.cci_ptr[sa.run0 + 1] - pa;
     const int pb = a.cci_ptr[sb.run0];
     const int k0 = blockIdx.x * kChunk;
@@ -560,6 +585,8 @@ __global__ void __launch_bounds__(256) k_apply_colour(SweepArgs a, int p0) {
         return;
     }
     const int nk = min(kChunk, n_rows - k0);
+    // a combination block inside one group: both sides are the same tiles, held once
+    const bool same = MODE == 1 && A == B;
     const int pav = sa.run1 >= 0 ? a.cci_ptr[sa.run1] : 0;
     const int pbv = sb.run1 >= 0 ? a.cci_ptr[sb.run1] : 0;
     if (threadIdx.x < nk) {
@@ -571,78 +598,122 @@ __global__ void __launch_bounds__(256) k_apply_colour(SweepArgs a, int p0) {
         const int bv = sb.run1 >= 0 ? a.cci_slot[pbv + k] : 0;
         for (int i = 0; i < 3; ++i) {
             s_slot[threadIdx.x][i] = i < sa.nrun0 ? so + i : (i < sa.n ? sv + (i - sa.nrun0) : -1);
-            s_slot[threadIdx.x][3 + i] = i < sb.nrun0 ? bo + i : (i < sb.n ? bv + (i - sb.nrun0) : -1);
+            s_slot[threadIdx.x][3 + i] =
+                same ? -1 : (i < sb.nrun0 ? bo + i : (i < sb.n ? bv + (i - sb.nrun0) : -1));
         }
     }
     const int* lvl = a.pr_lvl + (size_t)e * (kMaxSub + 1);
     for (int i = threadIdx.x; i <= kMaxSub; i += blockDim.x) s_lvl[i] = lvl[i];
     const T* cs = (const T*)a.pr_cs + (size_t)e * kOrthoCap * 2;
     const uint16_t* ij = a.pr_ij + (size_t)e * kOrthoCap;
-    for (int i = threadIdx.x; i < np; i += blockDim.x) {
-        pij[i] = ij[i];
-        pcs[2 * i] = cs[2 * i];
-        pcs[2 * i + 1] = cs[2 * i + 1];
+    const int noA = 4 * a.group_nmol[A], noB = 4 * a.group_nmol[B];
+    for (int q = threadIdx.x; q < np; q += blockDim.x) {
+        const unsigned w = ij[q];
+        const int il = w & 255, jl = w >> 8;
+        int ta, ca, tb, cb;
+        if (MODE == 0) {
+            ta = il >> 4;
+            ca = il & 15;
+            tb = 3 + (jl >> 4);
+            cb = jl & 15;
+        } else {
+            side_pos(il, noA, sa.nrun0, ta, ca);
+            side_pos(jl, noB, sb.nrun0, tb, cb);
+            if (!same) tb += 3;
+        }
+        poff[q] = (unsigned)((ta * 16 + ca) * kNRp) | ((unsigned)((tb * 16 + cb) * kNRp) << 16);
+        pcs[2 * q] = cs[2 * q];
+        pcs[2 * q + 1] = cs[2 * q + 1];
     }
     __syncthreads();
     T* val = (T*)a.out_val;   // in place
-    // load the panel: tile position p, column col, AO row kr of row block rb
-    for (int idx = threadIdx.x; idx < nk * 6 * kTileVals; idx += blockDim.x) {
-        const int rb = idx / (6 * kTileVals);
-        const int rem = idx % (6 * kTileVals);
-        const int p = rem / kTileVals, v = rem % kTileVals;
-        const int kr = v >> 4, col = v & 15;
-        const int sl = s_slot[rb][p];
-        T x = (T)0;
-        if (sl >= 0) x = val[((size_t)s_row[rb] * a.cap + sl) * kTileVals + v];
-        panel[(p * 16 + col) * kNRp + rb * 6 + kr] = x;
+    // panel load: one 16-value AO-row segment (rb, p, k) per item, vector loads,
+    // kSegUnroll segments in flight per thread, transposed into the panel
+    using V = typename Vec<T>::type;
+    constexpr int kVPer = 16 / Vec<T>::n;   // vector loads per segment
+    const int nseg = nk * 6 * 6;
+    for (int s0 = threadIdx.x; s0 < nseg; s0 += blockDim.x * kSegUnroll) {
+        V buf[kSegUnroll][kVPer];
+#pragma unroll
+        for (int u = 0; u < kSegUnroll; ++u) {
+            const int sg = s0 + u * blockDim.x;
+            if (sg < nseg) {
+                const int rb = sg / 36, rem = sg - rb * 36, p = rem / 6, kr = rem - p * 6;
+                const int sl = s_slot[rb][p];
+                if (sl >= 0) {
+                    const V* src = (const V*)(val + ((size_t)s_row[rb] * a.cap + sl) * kTileVals + kr * 16);
+#pragma unroll
+                    for (int v = 0; v < kVPer; ++v) buf[u][v] = src[v];
+                } else {
+#pragma unroll
+                    for (int v = 0; v < kVPer; ++v) buf[u][v] = Vec<T>::zero();
+                }
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < kSegUnroll; ++u) {
+            const int sg = s0 + u * blockDim.x;
+            if (sg < nseg) {
+                const int rb = sg / 36, rem = sg - rb * 36, p = rem / 6, kr = rem - p * 6;
+                const T* e = (const T*)buf[u];
+                T* dst = panel + (p * 16) * kNRp + rb * 6 + kr;
+#pragma unroll
+                for (int col = 0; col < 16; ++col) dst[col * kNRp] = e[col];
+            }
+        }
     }
     __syncthreads();
-    const int noA = 4 * a.group_nmol[A], noB = 4 * a.group_nmol[B];
-    const int nr = nk * 6;
-    for (int sub = 0; sub < kMaxSub; ++sub) {
-        const int q0 = s_lvl[sub], q1 = s_lvl[sub + 1];
-        if (q0 == np) break;
-        const int items = (q1 - q0) * nr;
-        for (int it = threadIdx.x; it < items; it += blockDim.x) {
-            const int q = q0 + it / nr, row = it % nr;
-            const unsigned w = pij[q];
-            const int il = w & 255, jl = w >> 8;
-            int ta, ca, tb, cb;
-            if (a.mode == 0) {
-                ta = il >> 4;
-                ca = il & 15;
-                tb = 3 + (jl >> 4);
-                cb = jl & 15;
-            } else {
-                side_pos(il, noA, sa.nrun0, ta, ca);
-                side_pos(jl, noB, sb.nrun0, tb, cb);
-                tb += 3;
+    const int row = threadIdx.x;
+    if (row < nk * 6) {
+        T* pr = panel + row;
+        for (int sub = 0; sub < kMaxSub; ++sub) {
+            const int q1 = s_lvl[sub + 1];
+            int q = s_lvl[sub];
+            if (q == np) break;
+            for (; q < q1; q += kUnroll) {
+                unsigned off[kUnroll];
+                T x[kUnroll], y[kUnroll], c0[kUnroll], c1[kUnroll];
+#pragma unroll
+                for (int u = 0; u < kUnroll; ++u) {
+                    if (q + u < q1) {
+                        off[u] = poff[q + u];
+                        c0[u] = pcs[2 * (q + u)];
+                        c1[u] = pcs[2 * (q + u) + 1];
+                        x[u] = pr[off[u] & 0xffffu];
+                        y[u] = pr[off[u] >> 16];
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < kUnroll; ++u) {
+                    if (q + u < q1) {
+                        T xn, yn;
+                        if (MODE == 0) {
+                            xn = c0[u] * x[u] + c1[u] * y[u];
+                            yn = c0[u] * y[u] - c1[u] * x[u];
+                        } else {
+                            xn = x[u] - c0[u] * y[u];
+                            yn = y[u] - c0[u] * x[u];
+                        }
+                        pr[off[u] & 0xffffu] = below(xn, a) ? (T)0 : xn;
+                        pr[off[u] >> 16] = below(yn, a) ? (T)0 : yn;
+                    }
+                }
             }
-            T* pi = panel + (ta * 16 + ca) * kNRp + row;
-            T* pj = panel + (tb * 16 + cb) * kNRp + row;
-            const T x = *pi, y = *pj;
-            T xn, yn;
-            if (a.mode == 0) {
-                const T c = pcs[2 * q], s = pcs[2 * q + 1];
-                xn = c * x + s * y;
-                yn = -s * x + c * y;
-            } else {
-                const T h = pcs[2 * q];
-                xn = x - h * y;
-                yn = y - h * x;
-            }
-            *pi = fabs((double)xn) < a.trunc ? (T)0 : xn;
-            *pj = fabs((double)yn) < a.trunc ? (T)0 : yn;
         }
-        __syncthreads();
     }
-    for (int idx = threadIdx.x; idx < nk * 6 * kTileVals; idx += blockDim.x) {
-        const int rb = idx / (6 * kTileVals);
-        const int rem = idx % (6 * kTileVals);
-        const int p = rem / kTileVals, v = rem % kTileVals;
-        const int kr = v >> 4, col = v & 15;
+    __syncthreads();
+    for (int sg = threadIdx.x; sg < nseg; sg += blockDim.x) {
+        const int rb = sg / 36, rem = sg - rb * 36, p = rem / 6, kr = rem - p * 6;
         const int sl = s_slot[rb][p];
-        if (sl >= 0) val[((size_t)s_row[rb] * a.cap + sl) * kTileVals + v] = panel[(p * 16 + col) * kNRp + rb * 6 + kr];
+        if (sl < 0) continue;
+        V out[kVPer];
+        T* e = (T*)out;
+        const T* srcp = panel + (p * 16) * kNRp + rb * 6 + kr;
+#pragma unroll
+        for (int col = 0; col < 16; ++col) e[col] = srcp[col * kNRp];
+        V* dst = (V*)(val + ((size_t)s_row[rb] * a.cap + sl) * kTileVals + kr * 16);
+#pragma unroll
+        for (int v = 0; v < kVPer; ++v) dst[v] = out[v];
     }
 }
 
@@ -714,6 +785,7 @@ static cudaError_t select_rot_t(Ctx* c) {
 }
 
 cudaError_t launch_select_rot(Ctx* c) {
+    c->n_launch += 19;
     return c->prec == SSCF_FP64 ? select_rot_t<double>(c) : select_rot_t<float>(c);
 }
 
@@ -737,6 +809,7 @@ static cudaError_t ortho_prepare_t(Ctx* c, int w, double tol) {
 }
 
 cudaError_t launch_ortho_prepare(Ctx* c, int w, double tol) {
+    c->n_launch += 3;
     return c->prec == SSCF_FP64 ? ortho_prepare_t<double>(c, w, tol) : ortho_prepare_t<float>(c, w, tol);
 }
 
@@ -749,6 +822,8 @@ static void fill_args(Ctx* c, SweepArgs& a, int mode, int which) {
     a.cap = c->cap;
     a.n_blk = mode == 0 ? c->n_gnb : (int)c->h_ocolour_blk.size();
     a.trunc = mode == 0 ? c->prm.eps : 1e-3 * c->prm.eps;
+    a.trunc_f = (float)a.trunc;
+    if ((double)a.trunc_f < a.trunc) a.trunc_f = nextafterf(a.trunc_f, INFINITY);
     a.blk = mode == 0 ? c->d_colour_blk : c->d_ocolour_blk;
     a.gnb_row = c->d_gnb_row;
     a.gnb_col = c->d_gnb_col;
@@ -792,28 +867,35 @@ static cudaError_t closure_t(Ctx* c, int mode, int which) {
     return cudaGetLastError();
 }
 
-template <typename T>
-static cudaError_t apply_t(Ctx* c, int mode, int which) {
+template <typename T, int MODE>
+static cudaError_t apply_mode_t(Ctx* c, int which) {
     SweepArgs a;
-    fill_args<T>(c, a, mode, which);
+    fill_args<T>(c, a, MODE, which);
     a.in_nt = a.out_nt = c->d_c_nt[c->cur];
     a.in_tile = a.out_tile = c->d_c_tile[c->cur];
     a.in_val = a.out_val = c->d_c_val[c->cur];
-    const size_t smem = (size_t)6 * 16 * kNRp * sizeof(T) + (size_t)2 * kOrthoCap * sizeof(T) + (size_t)kOrthoCap * 2;
-    cudaError_t e = cudaFuncSetAttribute(k_apply_colour<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const size_t smem = (size_t)6 * 16 * kNRp * sizeof(T) + (size_t)2 * kOrthoCap * sizeof(T) + (size_t)kOrthoCap * 4;
+    cudaError_t e = cudaFuncSetAttribute(k_apply_colour<T, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    const std::vector<int>& ptr = mode == 0 ? c->h_colour_ptr : c->h_ocolour_ptr;
+    const std::vector<int>& ptr = MODE == 0 ? c->h_colour_ptr : c->h_ocolour_ptr;
     const int gx = (c->n_mol + kChunk - 1) / kChunk;
     for (int col = 0; col < c->n_colours; ++col) {
         const int nb = ptr[col + 1] - ptr[col];
         if (nb == 0) continue;
         dim3 grid(gx, nb);
-        k_apply_colour<T><<<grid, 256, smem, c->stream>>>(a, ptr[col]);
+        k_apply_colour<T, MODE><<<grid, kNR, smem, c->stream>>>(a, ptr[col]);
+        c->n_launch += 1;
     }
     return cudaGetLastError();
 }
 
+template <typename T>
+static cudaError_t apply_t(Ctx* c, int mode, int which) {
+    return mode == 0 ? apply_mode_t<T, 0>(c, which) : apply_mode_t<T, 1>(c, which);
+}
+
 cudaError_t launch_closure(Ctx* c, int mode, int which) {
+    c->n_launch += 1;
     return c->prec == SSCF_FP64 ? closure_t<double>(c, mode, which) : closure_t<float>(c, mode, which);
 }
 
@@ -822,6 +904,7 @@ cudaError_t launch_apply(Ctx* c, int mode, int which) {
 }
 
 cudaError_t launch_compact(Ctx* c) {
+    c->n_launch += 1;
     const int in = c->cur, out = 1 - c->cur;
     if (c->prec == SSCF_FP64)
         k_compact<double><<<c->n_mol, 256, 0, c->stream>>>(c->cap, c->d_c_nt[in], c->d_c_tile[in],

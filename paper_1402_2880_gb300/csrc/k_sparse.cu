@@ -380,6 +380,7 @@ k_density(int n_occ_tiles, int cap, const int* __restrict__ c_nt, const int* __r
 static cudaError_t ensure_attrs();
 
 cudaError_t launch_colindex(Ctx* c) {
+    c->n_launch += 4;
     cudaError_t ea = ensure_attrs();
     if (ea != cudaSuccess) return ea;
     const int b = c->cur;
@@ -419,6 +420,7 @@ static cudaError_t ensure_attrs() {
 }
 
 cudaError_t launch_xc(Ctx* c, bool use_h, int tile_lo, int tile_hi) {
+    c->n_launch += 1;
     cudaError_t e = ensure_attrs();
     if (e != cudaSuccess) return e;
     const int b = c->cur;
@@ -449,6 +451,7 @@ static cudaError_t transform_t(Ctx* c, const int* ptr, const int* bl, const int*
 }
 
 cudaError_t launch_transform_rot(Ctx* c) {
+    c->n_launch += 3;
     cudaError_t e = ensure_attrs();
     if (e != cudaSuccess) return e;
     if ((size_t)c->n_mol * 4 > 200 * 1024) return cudaErrorInvalidValue;
@@ -472,6 +475,7 @@ cudaError_t launch_transform_rot(Ctx* c) {
 }
 
 cudaError_t launch_transform_ortho(Ctx* c, int w) {
+    c->n_launch += 1;
     cudaError_t e = ensure_attrs();
     if (e != cudaSuccess) return e;
     if (c->prec == SSCF_FP64)
@@ -480,6 +484,7 @@ cudaError_t launch_transform_ortho(Ctx* c, int w) {
 }
 
 cudaError_t launch_density(Ctx* c) {
+    c->n_launch += 1;
     cudaError_t e = ensure_attrs();
     if (e != cudaSuccess) return e;
     const size_t smem = (size_t)c->n_occ_tiles * 4;

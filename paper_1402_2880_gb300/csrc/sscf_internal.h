@@ -59,6 +59,7 @@ struct DeviceScalars {
     double e_coul;
     double dq_max;
     double energy;
+    unsigned long long tiles[2];  // stored tiles of C, occupied tiles among them
     unsigned long long hist[256];
 };
 
@@ -77,6 +78,7 @@ struct Ctx {
     int capY = 0;        // row blocks per tile of Y
     bool have_guess = false;
     int iteration = 0;
+    long long n_launch = 0;   // kernels launched by this context
     double e_prev = 0.0;
     bool have_e_prev = false;
     int last_sched_kind = 0;   // 0 none, 1 rotations, 2 combinations
@@ -233,6 +235,7 @@ cudaError_t launch_apply(Ctx* c, int mode, int which);   // mode 0 rotations, 1 
 cudaError_t launch_compact(Ctx* c);                      // drop all-zero tiles; cur <- other
 // charges
 cudaError_t launch_charges_finish(Ctx* c, bool mix);
+cudaError_t launch_count_tiles(Ctx* c, unsigned long long* out);
 
 }  // namespace sscf
 
