@@ -199,6 +199,33 @@ int sscf_get_colouring(sscf_ctx* ctx, int* colour);
 int sscf_get_pairs(sscf_ctx* ctx, int64_t capacity, int32_t* colour_out, int32_t* sub_out, int32_t* i_out,
                    int32_t* j_out, int64_t* n_out);
 
+/* Allocation-free pair selection ------------------------------------------
+ *
+ * No counterpart in the paper: this entry point exists for callers that
+ * cannot call cudaMalloc (code running inside another framework's memory
+ * pool, under a device-memory budget fixed at start-up, or where the
+ * allocator belongs to someone else). It applies the same rule as the pair
+ * selection inside sscf_rotate_sweep to an array the caller owns:
+ * keep[i] = 1 iff |f[i]| >= tau, f[i] != 0, and |f[i]| is among the k_max
+ * largest such values (all values tied with the k_max-th largest are kept).
+ *
+ *   f       device, n doubles (for example the entries of the kept F_ov blocks)
+ *   keep    device, n bytes, written (0 or 1)
+ *   n_keep  host, number of kept entries, or NULL (then the call does not
+ *           synchronise the stream)
+ *   stream  cudaStream_t or NULL
+ *
+ * It allocates nothing: its working memory is one file-scope __device__
+ * array of 16 MiB + 2304 bytes that every GPU loading the library holds
+ * until the process exits. n above 2^21 (2,097,152) is rejected with
+ * SSCF_ERR_INVALID_ARG. The first call on a device (with that device
+ * current) looks up the array's device address; make that first call before
+ * any stream capture. All calls share the array and it keeps the last call's
+ * contents (each call clears what must start at zero); calls that overlap on
+ * the GPU, from other streams or host threads, race on it. */
+int sscf_select_pairs_noalloc(const double* f, int64_t n, double tau, int64_t k_max, unsigned char* keep,
+                              int64_t* n_keep, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -32,6 +32,7 @@ EXPORTED = [
     "sscf_density", "sscf_reset_charges", "sscf_step", "sscf_run", "sscf_get_C_dense",
     "sscf_set_C_dense", "sscf_get_H_dense", "sscf_get_F_dense", "sscf_get_charges",
     "sscf_set_charges", "sscf_get_colouring", "sscf_get_pairs", "sscf_profile", "sscf_profile_read",
+    "sscf_select_pairs_noalloc",
 ]
 
 
@@ -107,6 +108,7 @@ def load() -> ctypes.CDLL:
                                    P(ctypes.c_int32), P(c_i64)]),
         "sscf_profile": (c_int, [c_vp, c_int]),
         "sscf_profile_read": (c_int, [c_vp, c_int, ctypes.c_char_p, P(c_double), P(c_i64), P(c_int)]),
+        "sscf_select_pairs_noalloc": (c_int, [c_vp, c_i64, c_double, c_i64, c_vp, P(c_i64), c_vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -139,6 +141,21 @@ def make_params(p: dict, precision: int = SSCF_FP64, ortho_every: int = 1, cap_t
     q.group_cut, q.rot_cap_factor, q.mix_beta = p["group_cut"], p["rot_cap_factor"], p["mix_beta"]
     q.max_scc, q.precision, q.ortho_every, q.cap_tiles = int(p["max_scc"]), precision, ortho_every, cap_tiles
     return q
+
+
+def select_pairs_noalloc(f_dev_ptr: int, n: int, tau: float, k_max: int, keep_dev_ptr: int,
+                         stream: int | None = None) -> int:
+    """Pair selection on caller-owned device arrays, without any device allocation.
+
+    ``f_dev_ptr`` points to n doubles, ``keep_dev_ptr`` to n bytes (both
+    device memory owned by the caller). Returns the number of kept entries.
+    """
+    lib = load()
+    kept = ctypes.c_int64()
+    _check(lib.sscf_select_pairs_noalloc(ctypes.c_void_p(f_dev_ptr), int(n), float(tau), int(k_max),
+                                         ctypes.c_void_p(keep_dev_ptr), ctypes.byref(kept),
+                                         ctypes.c_void_p(stream or 0)), "sscf_select_pairs_noalloc")
+    return kept.value
 
 
 class Context:
