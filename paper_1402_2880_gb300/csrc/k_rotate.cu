@@ -539,7 +539,7 @@ __device__ __forceinline__ Side side_of(const SweepArgs& a, int g, bool virt_onl
 constexpr int kChunk = 32;                 // row blocks per CTA
 constexpr int kNR = kChunk * kAoPerMol;    // AO rows per CTA = threads per CTA
 constexpr int kNRp = kNR + 1;              // padded panel stride (bank spread)
-constexpr int kUnroll = 4;                 // pairs of one level in flight per thread
+constexpr int kUnroll = 8;                 // pairs of one level in flight per thread
 constexpr int kSegUnroll = 4;              // panel segments in flight per thread
 
 template <typename T> struct Vec;
@@ -560,15 +560,17 @@ template <> struct Vec<double> {
 // schedule order (level by level). Rows are independent, so no barrier is
 // needed between levels; pairs of one level touch disjoint MOs, so kUnroll of
 // them are loaded, updated and stored together.
-template <typename T, int MODE>
+template <typename T, int MODE, int NT, int PCAP>
 __global__ void __launch_bounds__(kNR) k_apply_colour(SweepArgs a, int p0) {
     extern __shared__ unsigned char smraw[];
-    T* panel = (T*)smraw;                                    // [6 tiles][16][kNRp]
-    T* pcs = panel + 6 * 16 * kNRp;                          // np * 2 coefficients
-    unsigned* poff = (unsigned*)(pcs + 2 * kOrthoCap);       // np packed panel offsets
+    T* panel = (T*)smraw;                                    // [NT tiles][16][kNRp]
+    T* pcs = panel + NT * 16 * kNRp;                         // np * 2 coefficients
+    unsigned* poff = (unsigned*)(pcs + 2 * PCAP);            // np packed panel offsets
     __shared__ int s_lvl[kMaxSub + 1];
     __shared__ int s_row[kChunk];
-    __shared__ int s_slot[kChunk][6];
+    __shared__ int s_slot[kChunk][NT];
+    // side A occupies panel tiles [0, kSideA), side B [kSideA, NT)
+    constexpr int kSideA = MODE == 0 ? 2 : NT / 2;
     const int e = a.blk[p0 + blockIdx.y];
     const int np = a.pr_n[e];
     if (np == 0) return;
@@ -596,10 +598,11 @@ __global__ void __launch_bounds__(kNR) k_apply_colour(SweepArgs a, int p0) {
         const int sv = sa.run1 >= 0 ? a.cci_slot[pav + k] : 0;
         const int bo = a.cci_slot[pb + k];
         const int bv = sb.run1 >= 0 ? a.cci_slot[pbv + k] : 0;
-        for (int i = 0; i < 3; ++i) {
-            s_slot[threadIdx.x][i] = i < sa.nrun0 ? so + i : (i < sa.n ? sv + (i - sa.nrun0) : -1);
-            s_slot[threadIdx.x][3 + i] =
-                same ? -1 : (i < sb.nrun0 ? bo + i : (i < sb.n ? bv + (i - sb.nrun0) : -1));
+        for (int i = 0; i < NT / 2 + (NT & 1); ++i) {
+            if (i < kSideA) s_slot[threadIdx.x][i] = i < sa.nrun0 ? so + i : (i < sa.n ? sv + (i - sa.nrun0) : -1);
+            if (i < NT - kSideA)
+                s_slot[threadIdx.x][kSideA + i] =
+                    same ? -1 : (i < sb.nrun0 ? bo + i : (i < sb.n ? bv + (i - sb.nrun0) : -1));
         }
     }
     const int* lvl = a.pr_lvl + (size_t)e * (kMaxSub + 1);
@@ -614,12 +617,12 @@ __global__ void __launch_bounds__(kNR) k_apply_colour(SweepArgs a, int p0) {
         if (MODE == 0) {
             ta = il >> 4;
             ca = il & 15;
-            tb = 3 + (jl >> 4);
+            tb = kSideA + (jl >> 4);
             cb = jl & 15;
         } else {
             side_pos(il, noA, sa.nrun0, ta, ca);
             side_pos(jl, noB, sb.nrun0, tb, cb);
-            if (!same) tb += 3;
+            if (!same) tb += kSideA;
         }
         poff[q] = (unsigned)((ta * 16 + ca) * kNRp) | ((unsigned)((tb * 16 + cb) * kNRp) << 16);
         pcs[2 * q] = cs[2 * q];
@@ -631,14 +634,14 @@ __global__ void __launch_bounds__(kNR) k_apply_colour(SweepArgs a, int p0) {
     // kSegUnroll segments in flight per thread, transposed into the panel
     using V = typename Vec<T>::type;
     constexpr int kVPer = 16 / Vec<T>::n;   // vector loads per segment
-    const int nseg = nk * 6 * 6;
+    const int nseg = nk * 6 * NT;
     for (int s0 = threadIdx.x; s0 < nseg; s0 += blockDim.x * kSegUnroll) {
         V buf[kSegUnroll][kVPer];
 #pragma unroll
         for (int u = 0; u < kSegUnroll; ++u) {
             const int sg = s0 + u * blockDim.x;
             if (sg < nseg) {
-                const int rb = sg / 36, rem = sg - rb * 36, p = rem / 6, kr = rem - p * 6;
+                const int rb = sg / (6 * NT), rem = sg - rb * (6 * NT), p = rem / 6, kr = rem - p * 6;
                 const int sl = s_slot[rb][p];
                 if (sl >= 0) {
                     const V* src = (const V*)(val + ((size_t)s_row[rb] * a.cap + sl) * kTileVals + kr * 16);
@@ -654,7 +657,7 @@ __global__ void __launch_bounds__(kNR) k_apply_colour(SweepArgs a, int p0) {
         for (int u = 0; u < kSegUnroll; ++u) {
             const int sg = s0 + u * blockDim.x;
             if (sg < nseg) {
-                const int rb = sg / 36, rem = sg - rb * 36, p = rem / 6, kr = rem - p * 6;
+                const int rb = sg / (6 * NT), rem = sg - rb * (6 * NT), p = rem / 6, kr = rem - p * 6;
                 const T* e = (const T*)buf[u];
                 T* dst = panel + (p * 16) * kNRp + rb * 6 + kr;
 #pragma unroll
@@ -703,7 +706,7 @@ __global__ void __launch_bounds__(kNR) k_apply_colour(SweepArgs a, int p0) {
     }
     __syncthreads();
     for (int sg = threadIdx.x; sg < nseg; sg += blockDim.x) {
-        const int rb = sg / 36, rem = sg - rb * 36, p = rem / 6, kr = rem - p * 6;
+        const int rb = sg / (6 * NT), rem = sg - rb * (6 * NT), p = rem / 6, kr = rem - p * 6;
         const int sl = s_slot[rb][p];
         if (sl < 0) continue;
         V out[kVPer];
@@ -867,15 +870,16 @@ static cudaError_t closure_t(Ctx* c, int mode, int which) {
     return cudaGetLastError();
 }
 
-template <typename T, int MODE>
+template <typename T, int MODE, int NT, int PCAP>
 static cudaError_t apply_mode_t(Ctx* c, int which) {
     SweepArgs a;
     fill_args<T>(c, a, MODE, which);
     a.in_nt = a.out_nt = c->d_c_nt[c->cur];
     a.in_tile = a.out_tile = c->d_c_tile[c->cur];
     a.in_val = a.out_val = c->d_c_val[c->cur];
-    const size_t smem = (size_t)6 * 16 * kNRp * sizeof(T) + (size_t)2 * kOrthoCap * sizeof(T) + (size_t)kOrthoCap * 4;
-    cudaError_t e = cudaFuncSetAttribute(k_apply_colour<T, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const size_t smem = (size_t)NT * 16 * kNRp * sizeof(T) + (size_t)2 * PCAP * sizeof(T) + (size_t)PCAP * 4;
+    cudaError_t e = cudaFuncSetAttribute(k_apply_colour<T, MODE, NT, PCAP>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const std::vector<int>& ptr = MODE == 0 ? c->h_colour_ptr : c->h_ocolour_ptr;
     const int gx = (c->n_mol + kChunk - 1) / kChunk;
@@ -883,15 +887,20 @@ static cudaError_t apply_mode_t(Ctx* c, int which) {
         const int nb = ptr[col + 1] - ptr[col];
         if (nb == 0) continue;
         dim3 grid(gx, nb);
-        k_apply_colour<T, MODE><<<grid, kNR, smem, c->stream>>>(a, ptr[col]);
+        k_apply_colour<T, MODE, NT, PCAP><<<grid, kNR, smem, c->stream>>>(a, ptr[col]);
         c->n_launch += 1;
     }
     return cudaGetLastError();
 }
 
+// side tiles and pair capacity per pass: rotations 2 occupied + 1 virtual
+// tiles, 32 x 16 pairs; occupied passes 2 + 2 tiles, 32 x 32 pairs; passes over
+// all MOs 3 + 3 tiles, 48 x 48 pairs
 template <typename T>
 static cudaError_t apply_t(Ctx* c, int mode, int which) {
-    return mode == 0 ? apply_mode_t<T, 0>(c, which) : apply_mode_t<T, 1>(c, which);
+    if (mode == 0) return apply_mode_t<T, 0, 3, kRotCap>(c, which);
+    if (which == 1) return apply_mode_t<T, 1, 4, 32 * 32>(c, which);
+    return apply_mode_t<T, 1, 6, kOrthoCap>(c, which);
 }
 
 cudaError_t launch_closure(Ctx* c, int mode, int which) {

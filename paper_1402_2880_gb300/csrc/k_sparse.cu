@@ -194,18 +194,30 @@ __global__ void k_xc(int tile_lo, int n_mol, int cap, int capY, const int* __res
 
 // ---------------------------------------------------------------------------
 // Tile-pair transform: out[p] (16x16) = C[:, a]^T Y[:, b] for every listed
-// pair (a, b). One CTA per tile a; a shared map row block -> slot of a; one
-// warp per pair walks b's rows (sorted) and accumulates the rows present in
-// a (ascending row order, fixed sum order).
+// pair (a, b). One CTA per tile a with a shared map row block -> slot of a.
+// One warp per pair: it walks b's rows (sorted), and for the rows present in
+// a it stages the two 6x16 tiles (C[r, a] and Y[r, b]) in a per-warp buffer
+// with 16-byte loads, kStage row blocks at a time; every lane then owns a 2x4
+// block of the 16x16 result and does 8 FMAs per K step from one 8-byte and
+// one 16-byte shared load. Rows are summed in ascending order (fixed order);
+// mixed precision flushes the FP32 partial sums to FP64 every 32 rows.
 // ---------------------------------------------------------------------------
+constexpr int kTfWarps = 8;
+constexpr int kStage = 8;   // row blocks staged per warp at a time
+
+template <typename T> struct V4;
+template <> struct V4<float> { using type = float4; };
+template <> struct V4<double> { using type = double2; };
+
 template <typename T>
-__global__ void k_transform(int n_mol, int cap, int capY, const int* __restrict__ tp_ptr,
-                            const int* __restrict__ tp_b, const int* __restrict__ tp_out,
-                            const int* __restrict__ cci_ptr, const int* __restrict__ cci_row,
-                            const int* __restrict__ cci_slot, const T* __restrict__ c_val,
-                            const int* __restrict__ y_n, const int* __restrict__ y_row,
-                            const T* __restrict__ y_val, T* __restrict__ out) {
-    extern __shared__ int slot_of[];   // n_mol
+__global__ void __launch_bounds__(kTfWarps * 32)
+k_transform(int n_mol, int cap, int capY, const int* __restrict__ tp_ptr, const int* __restrict__ tp_b,
+            const int* __restrict__ tp_out, const int* __restrict__ cci_ptr, const int* __restrict__ cci_row,
+            const int* __restrict__ cci_slot, const T* __restrict__ c_val, const int* __restrict__ y_n,
+            const int* __restrict__ y_row, const T* __restrict__ y_val, T* __restrict__ out) {
+    extern __shared__ __align__(16) unsigned char sraw[];
+    T* stage = (T*)sraw;                                        // [warps][kStage][2][96]
+    int* slot_of = (int*)(stage + (size_t)kTfWarps * kStage * 2 * kTileVals);   // n_mol
     const int a = blockIdx.x;
     const int p0 = tp_ptr[a], p1 = tp_ptr[a + 1];
     if (p0 == p1) return;
@@ -214,12 +226,17 @@ __global__ void k_transform(int n_mol, int cap, int capY, const int* __restrict_
     __syncthreads();
     for (int k = threadIdx.x; k < nc; k += blockDim.x) slot_of[cci_row[lo + k]] = cci_slot[lo + k];
     __syncthreads();
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-    const int i = lane >> 1, j0 = (lane & 1) * 8;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    T* buf = stage + (size_t)warp * kStage * 2 * kTileVals;
+    const int i0 = 2 * (lane >> 2), j0 = 4 * (lane & 3);
     using A = typename Acc<T>::type;
-    for (int p = p0 + warp; p < p1; p += nwarps) {
+    using VT = typename V4<T>::type;
+    constexpr int kVec = sizeof(VT) / sizeof(T);          // values per 16-byte load
+    constexpr int kPerTile = kTileVals / kVec;            // 16-byte loads per tile
+    for (int p = p0 + warp; p < p1; p += kTfWarps) {
         const int b = tp_b[p];
         const int nb = y_n[b];
+        const int* yr = y_row + (size_t)b * capY;
         double accd[8];
         A acc[8];
 #pragma unroll
@@ -228,34 +245,71 @@ __global__ void k_transform(int n_mol, int cap, int capY, const int* __restrict_
             accd[q] = 0.0;
         }
         for (int k0 = 0; k0 < nb; k0 += 32) {
-            int k = k0 + lane;
-            int s = -1;
-            if (k < nb) s = slot_of[y_row[(size_t)b * capY + k]];
+            const int k = k0 + lane;
+            const int s = k < nb ? slot_of[yr[k]] : -1;
             unsigned m = __ballot_sync(0xffffffffu, s >= 0);
             while (m) {
-                const int src = __ffs(m) - 1;
-                m &= m - 1;
-                const int ss = __shfl_sync(0xffffffffu, s, src);
-                const int rr = __shfl_sync(0xffffffffu, k, src);
-                const int r = y_row[(size_t)b * capY + rr];
-                const T* cv = c_val + ((size_t)r * cap + ss) * kTileVals;
-                const T* yv = y_val + ((size_t)b * capY + rr) * kTileVals;
+                // stage up to kStage matched row blocks
+                int rows[kStage];
+                int nst = 0;
 #pragma unroll
-                for (int q = 0; q < 6; ++q) {
-                    A ci = (A)cv[q * kTileW + i];
-#pragma unroll
-                    for (int u = 0; u < 8; ++u) acc[u] += ci * (A)yv[q * kTileW + j0 + u];
+                for (int g = 0; g < kStage; ++g) {
+                    rows[g] = -1;
+                    if (m) {
+                        const int src = __ffs(m) - 1;
+                        m &= m - 1;
+                        rows[g] = src;
+                        ++nst;
+                    }
                 }
+#pragma unroll
+                for (int g = 0; g < kStage; ++g) {
+                    if (g >= nst) break;
+                    const int ss = __shfl_sync(0xffffffffu, s, rows[g]);
+                    const int kk = k0 + rows[g];
+                    const int r = yr[kk];
+                    const VT* cs = (const VT*)(c_val + ((size_t)r * cap + ss) * kTileVals);
+                    const VT* ys = (const VT*)(y_val + ((size_t)b * capY + kk) * kTileVals);
+                    VT* bc = (VT*)(buf + (size_t)g * 2 * kTileVals);
+                    VT* by = (VT*)(buf + (size_t)g * 2 * kTileVals + kTileVals);
+                    for (int v = lane; v < kPerTile; v += 32) {
+                        bc[v] = cs[v];
+                        by[v] = ys[v];
+                    }
+                }
+                __syncwarp();
+                for (int g = 0; g < nst; ++g) {
+                    const T* bc = buf + (size_t)g * 2 * kTileVals;
+                    const T* by = bc + kTileVals;
+#pragma unroll
+                    for (int q = 0; q < 6; ++q) {
+                        const A c0 = (A)bc[q * 16 + i0], c1 = (A)bc[q * 16 + i0 + 1];
+                        const A y0 = (A)by[q * 16 + j0], y1 = (A)by[q * 16 + j0 + 1];
+                        const A y2 = (A)by[q * 16 + j0 + 2], y3 = (A)by[q * 16 + j0 + 3];
+                        acc[0] += c0 * y0;
+                        acc[1] += c0 * y1;
+                        acc[2] += c0 * y2;
+                        acc[3] += c0 * y3;
+                        acc[4] += c1 * y0;
+                        acc[5] += c1 * y1;
+                        acc[6] += c1 * y2;
+                        acc[7] += c1 * y3;
+                    }
+                }
+                __syncwarp();
             }
 #pragma unroll
-            for (int u = 0; u < 8; ++u) {
-                accd[u] += (double)acc[u];
-                acc[u] = 0;
+            for (int q = 0; q < 8; ++q) {
+                accd[q] += (double)acc[q];
+                acc[q] = 0;
             }
         }
-        T* o = out + (size_t)tp_out[p] * 256 + i * 16 + j0;
+        T* o = out + (size_t)tp_out[p] * 256;
 #pragma unroll
-        for (int u = 0; u < 8; ++u) o[u] = (T)accd[u];
+        for (int u = 0; u < 4; ++u) {
+            o[i0 * 16 + j0 + u] = (T)accd[u];
+            o[(i0 + 1) * 16 + j0 + u] = (T)accd[4 + u];
+        }
     }
 }
 
@@ -443,8 +497,8 @@ cudaError_t launch_xc(Ctx* c, bool use_h, int tile_lo, int tile_hi) {
 
 template <typename T>
 static cudaError_t transform_t(Ctx* c, const int* ptr, const int* bl, const int* outl, void* out) {
-    const size_t smem = (size_t)c->n_mol * 4;
-    k_transform<T><<<c->n_tiles, 256, smem, c->stream>>>(c->n_mol, c->cap, c->capY, ptr, bl, outl, c->d_cci_ptr,
+    const size_t smem = (size_t)kTfWarps * kStage * 2 * kTileVals * sizeof(T) + (size_t)c->n_mol * 4;
+    k_transform<T><<<c->n_tiles, kTfWarps * 32, smem, c->stream>>>(c->n_mol, c->cap, c->capY, ptr, bl, outl, c->d_cci_ptr,
                                                          c->d_cci_row, c->d_cci_slot, (const T*)c->d_c_val[c->cur],
                                                          c->d_y_n, c->d_y_row, (const T*)c->d_y_val, (T*)out);
     return cudaGetLastError();
@@ -454,7 +508,7 @@ cudaError_t launch_transform_rot(Ctx* c) {
     c->n_launch += 3;
     cudaError_t e = ensure_attrs();
     if (e != cudaSuccess) return e;
-    if ((size_t)c->n_mol * 4 > 200 * 1024) return cudaErrorInvalidValue;
+    if ((size_t)kTfWarps * kStage * 2 * kTileVals * 8 + (size_t)c->n_mol * 4 > 200 * 1024) return cudaErrorInvalidValue;
     if (c->prec == SSCF_FP64) {
         e = transform_t<double>(c, c->d_rot_tp_ptr, c->d_rot_tp_b, c->d_rot_tp_out, c->d_F);
         if (e == cudaSuccess)
