@@ -404,6 +404,7 @@ constexpr int kClosureIters = 256;
 // truncation test |x| < threshold, decided exactly in the storage precision
 __device__ __forceinline__ bool below(double x, const SweepArgs& a) { return fabs(x) < a.trunc; }
 __device__ __forceinline__ bool below(float x, const SweepArgs& a) { return fabsf(x) < a.trunc_f; }
+static_assert(sizeof(float) == 4, "");
 
 template <typename T>
 __global__ void __launch_bounds__(256) k_closure(SweepArgs a) {
@@ -536,9 +537,6 @@ __device__ __forceinline__ Side side_of(const SweepArgs& a, int g, bool virt_onl
     return s;
 }
 
-constexpr int kChunk = 32;                 // row blocks per CTA
-constexpr int kNR = kChunk * kAoPerMol;    // AO rows per CTA = threads per CTA
-constexpr int kNRp = kNR + 1;              // padded panel stride (bank spread)
 constexpr int kUnroll = 8;                 // pairs of one level in flight per thread
 constexpr int kSegUnroll = 4;              // panel segments in flight per thread
 
@@ -554,21 +552,43 @@ template <> struct Vec<double> {
     __device__ static double2 zero() { return make_double2(0.0, 0.0); }
 };
 
-// One CTA = one active block of the colour x 32 row blocks. The block's side
-// tiles of those rows are staged in shared memory as a [tile][column][row]
-// panel; every thread owns one AO row and applies the block's pairs to it in
-// schedule order (level by level). Rows are independent, so no barrier is
-// needed between levels; pairs of one level touch disjoint MOs, so kUnroll of
-// them are loaded, updated and stored together.
+// Rows per thread and row blocks per CTA: FP32 panels are processed two
+// adjacent AO rows per thread with packed f32x2 arithmetic; FP64 one row.
+template <typename T> struct ApplyShape;
+template <> struct ApplyShape<float> {
+    static constexpr int rows = 2, chunk = 64;
+};
+template <> struct ApplyShape<double> {
+    static constexpr int rows = 1, chunk = 32;
+};
+template <typename T> __host__ __device__ constexpr int apply_nr() { return ApplyShape<T>::chunk * kAoPerMol; }
+// even, bank-spread panel stride
+template <typename T> __host__ __device__ constexpr int apply_nrp() { return apply_nr<T>() + 2; }
+template <typename T> __host__ __device__ constexpr int apply_threads() { return apply_nr<T>() / ApplyShape<T>::rows; }
+
+__device__ __forceinline__ float2 trunc2(float2 v, float t) {
+    v.x = fabsf(v.x) < t ? 0.f : v.x;
+    v.y = fabsf(v.y) < t ? 0.f : v.y;
+    return v;
+}
+
+// One CTA = one active block of the colour x a chunk of row blocks. The
+// block's side tiles of those rows are staged in shared memory as a
+// [tile][column][row] panel; every thread owns one (FP64) or two adjacent
+// (FP32) AO rows and applies the block's pairs to them in schedule order,
+// level by level. Rows are independent, so no barrier is needed between
+// levels; pairs of one level touch disjoint MOs, so kUnroll of them are
+// loaded, updated and stored together.
 template <typename T, int MODE, int NT, int PCAP>
-__global__ void __launch_bounds__(kNR) k_apply_colour(SweepArgs a, int p0) {
+__global__ void __launch_bounds__(apply_threads<T>()) k_apply_colour(SweepArgs a, int p0) {
+    constexpr int CH = ApplyShape<T>::chunk, NRP = apply_nrp<T>();
     extern __shared__ unsigned char smraw[];
-    T* panel = (T*)smraw;                                    // [NT tiles][16][kNRp]
-    T* pcs = panel + NT * 16 * kNRp;                         // np * 2 coefficients
+    T* panel = (T*)smraw;                                    // [NT tiles][16][NRP]
+    T* pcs = panel + NT * 16 * NRP;                          // np * 2 coefficients
     unsigned* poff = (unsigned*)(pcs + 2 * PCAP);            // np packed panel offsets
     __shared__ int s_lvl[kMaxSub + 1];
-    __shared__ int s_row[kChunk];
-    __shared__ int s_slot[kChunk][NT];
+    __shared__ int s_row[CH];
+    __shared__ int s_slot[CH][NT];
     // side A occupies panel tiles [0, kSideA), side B [kSideA, NT)
     constexpr int kSideA = MODE == 0 ? 2 : NT / 2;
     const int e = a.blk[p0 + blockIdx.y];
@@ -580,29 +600,28 @@ __global__ void __launch_bounds__(kNR) k_apply_colour(SweepArgs a, int p0) {
     const Side sb = side_of(a, B, MODE == 0, with_virt);
     const int pa = a.cci_ptr[sa.run0], n_rows = a.cci_ptr[sa.run0 + 1] - pa;
     const int pb = a.cci_ptr[sb.run0];
-    const int k0 = blockIdx.x * kChunk;
+    const int k0 = blockIdx.x * CH;
     if (k0 >= n_rows) return;
     if (a.cci_ptr[sb.run0 + 1] - pb != n_rows) {
         if (threadIdx.x == 0) atomicOr(a.err, kErrCapacity);
         return;
     }
-    const int nk = min(kChunk, n_rows - k0);
+    const int nk = min(CH, n_rows - k0);
     // a combination block inside one group: both sides are the same tiles, held once
     const bool same = MODE == 1 && A == B;
     const int pav = sa.run1 >= 0 ? a.cci_ptr[sa.run1] : 0;
     const int pbv = sb.run1 >= 0 ? a.cci_ptr[sb.run1] : 0;
-    if (threadIdx.x < nk) {
-        const int k = k0 + threadIdx.x;
-        s_row[threadIdx.x] = a.cci_row[pa + k];
+    for (int t = threadIdx.x; t < nk; t += blockDim.x) {
+        const int k = k0 + t;
+        s_row[t] = a.cci_row[pa + k];
         const int so = a.cci_slot[pa + k];
         const int sv = sa.run1 >= 0 ? a.cci_slot[pav + k] : 0;
         const int bo = a.cci_slot[pb + k];
         const int bv = sb.run1 >= 0 ? a.cci_slot[pbv + k] : 0;
         for (int i = 0; i < NT / 2 + (NT & 1); ++i) {
-            if (i < kSideA) s_slot[threadIdx.x][i] = i < sa.nrun0 ? so + i : (i < sa.n ? sv + (i - sa.nrun0) : -1);
+            if (i < kSideA) s_slot[t][i] = i < sa.nrun0 ? so + i : (i < sa.n ? sv + (i - sa.nrun0) : -1);
             if (i < NT - kSideA)
-                s_slot[threadIdx.x][kSideA + i] =
-                    same ? -1 : (i < sb.nrun0 ? bo + i : (i < sb.n ? bv + (i - sb.nrun0) : -1));
+                s_slot[t][kSideA + i] = same ? -1 : (i < sb.nrun0 ? bo + i : (i < sb.n ? bv + (i - sb.nrun0) : -1));
         }
     }
     const int* lvl = a.pr_lvl + (size_t)e * (kMaxSub + 1);
@@ -624,7 +643,7 @@ __global__ void __launch_bounds__(kNR) k_apply_colour(SweepArgs a, int p0) {
             side_pos(jl, noB, sb.nrun0, tb, cb);
             if (!same) tb += kSideA;
         }
-        poff[q] = (unsigned)((ta * 16 + ca) * kNRp) | ((unsigned)((tb * 16 + cb) * kNRp) << 16);
+        poff[q] = (unsigned)((ta * 16 + ca) * NRP) | ((unsigned)((tb * 16 + cb) * NRP) << 16);
         pcs[2 * q] = cs[2 * q];
         pcs[2 * q + 1] = cs[2 * q + 1];
     }
@@ -658,15 +677,16 @@ __global__ void __launch_bounds__(kNR) k_apply_colour(SweepArgs a, int p0) {
             const int sg = s0 + u * blockDim.x;
             if (sg < nseg) {
                 const int rb = sg / (6 * NT), rem = sg - rb * (6 * NT), p = rem / 6, kr = rem - p * 6;
-                const T* e = (const T*)buf[u];
-                T* dst = panel + (p * 16) * kNRp + rb * 6 + kr;
+                const T* e2 = (const T*)buf[u];
+                T* dst = panel + (p * 16) * NRP + rb * 6 + kr;
 #pragma unroll
-                for (int col = 0; col < 16; ++col) dst[col * kNRp] = e[col];
+                for (int col = 0; col < 16; ++col) dst[col * NRP] = e2[col];
             }
         }
     }
     __syncthreads();
-    const int row = threadIdx.x;
+    constexpr int R = ApplyShape<T>::rows;
+    const int row = threadIdx.x * R;
     if (row < nk * 6) {
         T* pr = panel + row;
         for (int sub = 0; sub < kMaxSub; ++sub) {
@@ -674,31 +694,64 @@ __global__ void __launch_bounds__(kNR) k_apply_colour(SweepArgs a, int p0) {
             int q = s_lvl[sub];
             if (q == np) break;
             for (; q < q1; q += kUnroll) {
-                unsigned off[kUnroll];
-                T x[kUnroll], y[kUnroll], c0[kUnroll], c1[kUnroll];
+                if constexpr (R == 2) {
+                    unsigned off[kUnroll];
+                    float2 x[kUnroll], y[kUnroll];
+                    float c0[kUnroll], c1[kUnroll];
 #pragma unroll
-                for (int u = 0; u < kUnroll; ++u) {
-                    if (q + u < q1) {
-                        off[u] = poff[q + u];
-                        c0[u] = pcs[2 * (q + u)];
-                        c1[u] = pcs[2 * (q + u) + 1];
-                        x[u] = pr[off[u] & 0xffffu];
-                        y[u] = pr[off[u] >> 16];
-                    }
-                }
-#pragma unroll
-                for (int u = 0; u < kUnroll; ++u) {
-                    if (q + u < q1) {
-                        T xn, yn;
-                        if (MODE == 0) {
-                            xn = c0[u] * x[u] + c1[u] * y[u];
-                            yn = c0[u] * y[u] - c1[u] * x[u];
-                        } else {
-                            xn = x[u] - c0[u] * y[u];
-                            yn = y[u] - c0[u] * x[u];
+                    for (int u = 0; u < kUnroll; ++u) {
+                        if (q + u < q1) {
+                            off[u] = poff[q + u];
+                            c0[u] = pcs[2 * (q + u)];
+                            c1[u] = pcs[2 * (q + u) + 1];
+                            x[u] = *(const float2*)(pr + (off[u] & 0xffffu));
+                            y[u] = *(const float2*)(pr + (off[u] >> 16));
                         }
-                        pr[off[u] & 0xffffu] = below(xn, a) ? (T)0 : xn;
-                        pr[off[u] >> 16] = below(yn, a) ? (T)0 : yn;
+                    }
+#pragma unroll
+                    for (int u = 0; u < kUnroll; ++u) {
+                        if (q + u < q1) {
+                            float2 xn, yn;
+                            if (MODE == 0) {
+                                const float2 cc = make_float2(c0[u], c0[u]);
+                                xn = __ffma2_rn(cc, x[u], __fmul2_rn(make_float2(c1[u], c1[u]), y[u]));
+                                yn = __ffma2_rn(cc, y[u], __fmul2_rn(make_float2(-c1[u], -c1[u]), x[u]));
+                            } else {
+                                const float2 nh = make_float2(-c0[u], -c0[u]);
+                                xn = __ffma2_rn(nh, y[u], x[u]);
+                                yn = __ffma2_rn(nh, x[u], y[u]);
+                            }
+                            *(float2*)(pr + (off[u] & 0xffffu)) = trunc2(xn, a.trunc_f);
+                            *(float2*)(pr + (off[u] >> 16)) = trunc2(yn, a.trunc_f);
+                        }
+                    }
+                } else {
+                    unsigned off[kUnroll];
+                    T x[kUnroll], y[kUnroll], c0[kUnroll], c1[kUnroll];
+#pragma unroll
+                    for (int u = 0; u < kUnroll; ++u) {
+                        if (q + u < q1) {
+                            off[u] = poff[q + u];
+                            c0[u] = pcs[2 * (q + u)];
+                            c1[u] = pcs[2 * (q + u) + 1];
+                            x[u] = pr[off[u] & 0xffffu];
+                            y[u] = pr[off[u] >> 16];
+                        }
+                    }
+#pragma unroll
+                    for (int u = 0; u < kUnroll; ++u) {
+                        if (q + u < q1) {
+                            T xn, yn;
+                            if (MODE == 0) {
+                                xn = c0[u] * x[u] + c1[u] * y[u];
+                                yn = c0[u] * y[u] - c1[u] * x[u];
+                            } else {
+                                xn = x[u] - c0[u] * y[u];
+                                yn = y[u] - c0[u] * x[u];
+                            }
+                            pr[off[u] & 0xffffu] = below(xn, a) ? (T)0 : xn;
+                            pr[off[u] >> 16] = below(yn, a) ? (T)0 : yn;
+                        }
                     }
                 }
             }
@@ -710,10 +763,10 @@ __global__ void __launch_bounds__(kNR) k_apply_colour(SweepArgs a, int p0) {
         const int sl = s_slot[rb][p];
         if (sl < 0) continue;
         V out[kVPer];
-        T* e = (T*)out;
-        const T* srcp = panel + (p * 16) * kNRp + rb * 6 + kr;
+        T* e2 = (T*)out;
+        const T* srcp = panel + (p * 16) * NRP + rb * 6 + kr;
 #pragma unroll
-        for (int col = 0; col < 16; ++col) e[col] = srcp[col * kNRp];
+        for (int col = 0; col < 16; ++col) e2[col] = srcp[col * NRP];
         V* dst = (V*)(val + ((size_t)s_row[rb] * a.cap + sl) * kTileVals + kr * 16);
 #pragma unroll
         for (int v = 0; v < kVPer; ++v) dst[v] = out[v];
@@ -877,17 +930,18 @@ static cudaError_t apply_mode_t(Ctx* c, int which) {
     a.in_nt = a.out_nt = c->d_c_nt[c->cur];
     a.in_tile = a.out_tile = c->d_c_tile[c->cur];
     a.in_val = a.out_val = c->d_c_val[c->cur];
-    const size_t smem = (size_t)NT * 16 * kNRp * sizeof(T) + (size_t)2 * PCAP * sizeof(T) + (size_t)PCAP * 4;
+    const size_t smem = (size_t)NT * 16 * apply_nrp<T>() * sizeof(T) + (size_t)2 * PCAP * sizeof(T) + (size_t)PCAP * 4;
     cudaError_t e = cudaFuncSetAttribute(k_apply_colour<T, MODE, NT, PCAP>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const std::vector<int>& ptr = MODE == 0 ? c->h_colour_ptr : c->h_ocolour_ptr;
-    const int gx = (c->n_mol + kChunk - 1) / kChunk;
+    constexpr int CH = ApplyShape<T>::chunk;
+    const int gx = (c->n_mol + CH - 1) / CH;
     for (int col = 0; col < c->n_colours; ++col) {
         const int nb = ptr[col + 1] - ptr[col];
         if (nb == 0) continue;
         dim3 grid(gx, nb);
-        k_apply_colour<T, MODE, NT, PCAP><<<grid, kNR, smem, c->stream>>>(a, ptr[col]);
+        k_apply_colour<T, MODE, NT, PCAP><<<grid, apply_threads<T>(), smem, c->stream>>>(a, ptr[col]);
         c->n_launch += 1;
     }
     return cudaGetLastError();
