@@ -164,6 +164,17 @@ int sscf_step(sscf_ctx* ctx, sscf_step_info* info);
  * state kept if max_scc is reached. */
 int sscf_run(sscf_ctx* ctx, sscf_step_info* info);
 
+/* Adjoint (no counterpart in the paper, which computes energies only): the
+ * gradient of E = sum P*H0 + 1/2 dq^T gamma dq at the current MOs, assumed
+ * converged and orthonormal (F_ov = 0, C^T S C = I):
+ *   dE = sum P*dH0 + sum (1/2 P*(Q_a+Q_b) - W)*dS + 1/2 dq^T dgamma dq,
+ *   W = 1/2 P H P = 2 C_occ F_oo C_occ^T  (energy-weighted density),
+ * through the derivatives of the Slater-Koster blocks and of gamma.
+ * dE_dxyz: host, 3*n_atoms (Ha/bohr, atom-major x, y, z), or NULL.
+ * dE_dparams: host, 8: dE/dV0[0..3], dE/dS0[0..3], or NULL.
+ * The charges of the current MOs become the SCC input (as sscf_reset_charges). */
+int sscf_gradients(sscf_ctx* ctx, double* dE_dxyz, double* dE_dparams);
+
 /* Tracing --------------------------------------------------------------- */
 
 /* Per-launcher device times: when enabled, every kernel launcher of the steps

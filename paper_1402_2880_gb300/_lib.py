@@ -32,7 +32,7 @@ EXPORTED = [
     "sscf_density", "sscf_reset_charges", "sscf_step", "sscf_run", "sscf_get_C_dense",
     "sscf_set_C_dense", "sscf_get_H_dense", "sscf_get_F_dense", "sscf_get_charges",
     "sscf_set_charges", "sscf_get_colouring", "sscf_get_pairs", "sscf_profile", "sscf_profile_read",
-    "sscf_select_pairs_noalloc",
+    "sscf_select_pairs_noalloc", "sscf_gradients",
 ]
 
 
@@ -109,6 +109,7 @@ def load() -> ctypes.CDLL:
         "sscf_profile": (c_int, [c_vp, c_int]),
         "sscf_profile_read": (c_int, [c_vp, c_int, ctypes.c_char_p, P(c_double), P(c_i64), P(c_int)]),
         "sscf_select_pairs_noalloc": (c_int, [c_vp, c_i64, c_double, c_i64, c_vp, P(c_i64), c_vp]),
+        "sscf_gradients": (c_int, [c_vp, P(c_double), P(c_double)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -239,6 +240,13 @@ class Context:
         d = info.as_dict()
         d["converged"] = s == SSCF_OK
         return d
+
+    def gradients(self):
+        """(dE/dxyz (n_atoms, 3) in Ha/bohr, dE/d(V0[0..3], S0[0..3])) at the current MOs."""
+        g = np.empty((self.n_atoms, 3))
+        dp = np.empty(8)
+        _check(self.lib.sscf_gradients(self.h, _ptr(g), _ptr(dp)), "sscf_gradients")
+        return g, dp
 
     # ---- state ----
     def get_C(self) -> np.ndarray:

@@ -566,6 +566,7 @@ int sscf_create(const sscf_system* sys, const sscf_params* prm, void* cuda_strea
     UP(c.d_tile_loc0, c.h_tile_loc0);
     UP(c.d_tile_nmo, c.h_tile_nmo);
     UP(c.d_tile_mo0, c.h_tile_mo0);
+    UP(c.d_gnb_ptr, c.h_gnb_ptr);
     UP(c.d_gnb_row, c.h_gnb_row);
     UP(c.d_gnb_col, c.h_gnb_col);
     UP(c.d_colour_ptr, c.h_colour_ptr);
@@ -635,6 +636,10 @@ int sscf_create(const sscf_system* sys, const sscf_params* prm, void* cuda_strea
     AL(c.d_Q, (size_t)c.n_atoms * 8);
     AL(c.d_e_mol, (size_t)c.n_mol * 8);
     AL(c.d_red, (size_t)(c.n_mol + 4096) * 8);
+    AL(c.d_grad, (size_t)c.n_atoms * 3 * 8);
+    AL(c.d_par, 8 * 8);
+    AL(c.d_gmol, (size_t)c.n_mol * 9 * 8);
+    AL(c.d_pmol, (size_t)c.n_mol * 8 * 8);
     AL(c.d_sc, sizeof(DeviceScalars));
 #undef AL
     if (cudaMallocHost((void**)&c.h_sc, sizeof(DeviceScalars)) != cudaSuccess) {
@@ -648,7 +653,7 @@ int sscf_create(const sscf_system* sys, const sscf_params* prm, void* cuda_strea
     for (int b = 0; b < 2; ++b)
         if (cudaMemsetAsync(c.d_c_nt[b], 0, (size_t)c.n_mol * 4, c.stream) != cudaSuccess) return fail(SSCF_ERR_CUDA);
     if (launch_sk_blocks(&c) != cudaSuccess) return fail(SSCF_ERR_CUDA);
-    if (launch_build_h(&c) != cudaSuccess) return fail(SSCF_ERR_CUDA);
+    if (launch_build_h(&c, c.prm.eps) != cudaSuccess) return fail(SSCF_ERR_CUDA);
     if (cudaStreamSynchronize(c.stream) != cudaSuccess) return fail(SSCF_ERR_CUDA);
     *out = h;
     return SSCF_OK;
@@ -699,7 +704,7 @@ int sscf_guess(sscf_ctx* h) {
 int sscf_build_fock(sscf_ctx* h) {
     if (!h) return SSCF_ERR_INVALID_ARG;
     Ctx& c = h->c;
-    PK("build_fock", launch_build_h(&c));
+    PK("build_fock", launch_build_h(&c, c.prm.eps));
     return SSCF_OK;
 }
 
@@ -810,7 +815,7 @@ int sscf_step(sscf_ctx* h, sscf_step_info* info) {
     if (!c.have_guess) return SSCF_ERR_STATE;
     const long long l0 = c.n_launch;
     CK(cudaMemsetAsync(c.d_sc, 0, offsetof(DeviceScalars, hist), c.stream));
-    PK("build_fock", launch_build_h(&c));
+    PK("build_fock", launch_build_h(&c, c.prm.eps));
     CKS(rotate_sweep_async(c));
     if (c.prm.ortho_every) CKS(ortho_pass_async(c, SSCF_ORTHO_OCC, c.prm.eps / 100.0));
     CKS(density_async(c, true));
@@ -833,6 +838,27 @@ int sscf_step(sscf_ctx* h, sscf_step_info* info) {
     if (!std::isfinite(c.h_sc->energy)) return SSCF_ERR_NONFINITE;
     c.e_prev = c.h_sc->energy;
     c.have_e_prev = true;
+    return SSCF_OK;
+}
+
+int sscf_gradients(sscf_ctx* h, double* dE_dxyz, double* dE_dparams) {
+    if (!h) return SSCF_ERR_INVALID_ARG;
+    Ctx& c = h->c;
+    if (!c.have_guess) return SSCF_ERR_STATE;
+    CK(cudaMemsetAsync(c.d_sc, 0, offsetof(DeviceScalars, hist), c.stream));
+    // charges of the current MOs (they become the SCC input), H without threshold
+    CKS(density_async(c, false));
+    PK("build_fock", launch_build_h(&c, 0.0));
+    // F_oo on the occupied blocks of neighbouring groups
+    PK("colindex", launch_colindex(&c));
+    PK("xc_h", launch_xc(&c, true, 0, c.n_occ_tiles));
+    PK("transform_oo", launch_transform_ortho(&c, 1));
+    PK("adjoint", launch_adjoint(&c, c.d_grad, c.d_par, c.d_gmol, c.d_pmol));
+    CKS(sync_scalars(c));
+    if (dE_dxyz) CK(cudaMemcpy(dE_dxyz, c.d_grad, (size_t)c.n_atoms * 3 * 8, cudaMemcpyDeviceToHost));
+    if (dE_dparams) CK(cudaMemcpy(dE_dparams, c.d_par, 8 * 8, cudaMemcpyDeviceToHost));
+    // restore H with the SCF threshold for later steps
+    PK("build_fock", launch_build_h(&c, c.prm.eps));
     return SSCF_OK;
 }
 

@@ -349,17 +349,17 @@ cudaError_t launch_gamma(Ctx* c, const double* dq, double* Q) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_build_h(Ctx* c) {
+cudaError_t launch_build_h(Ctx* c, double eps_threshold) {
     c->n_launch += 1;
     const int th = 256;
     const int n = c->n_mp * 36;
     if (c->prec == SSCF_FP64)
         k_build_h<double><<<(n + th - 1) / th, th, 0, c->stream>>>(c->n_mp, c->d_mp_row, c->d_mp_col, c->d_H0b,
-                                                                    c->d_Sb, c->d_Q_in, c->prm.eps,
+                                                                    c->d_Sb, c->d_Q_in, eps_threshold,
                                                                     (double*)c->d_Hb, (double*)c->d_Sbt);
     else
         k_build_h<float><<<(n + th - 1) / th, th, 0, c->stream>>>(c->n_mp, c->d_mp_row, c->d_mp_col, c->d_H0b,
-                                                                   c->d_Sb, c->d_Q_in, c->prm.eps,
+                                                                   c->d_Sb, c->d_Q_in, eps_threshold,
                                                                    (float*)c->d_Hb, (float*)c->d_Sbt);
     return cudaGetLastError();
 }

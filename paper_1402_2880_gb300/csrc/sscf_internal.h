@@ -129,6 +129,7 @@ struct Ctx {
     int* d_tile_loc0 = nullptr;
     int* d_tile_nmo = nullptr;
     int* d_tile_mo0 = nullptr;
+    int* d_gnb_ptr = nullptr;
     int* d_gnb_row = nullptr;
     int* d_gnb_col = nullptr;
     int* d_colour_ptr = nullptr;
@@ -189,6 +190,10 @@ struct Ctx {
     double* d_Q = nullptr;
     double* d_e_mol = nullptr;    // n_mol band-energy partials
     double* d_red = nullptr;      // reduction scratch (n_mol + 1024)
+    double* d_grad = nullptr;     // 3 n_atoms: dE/dxyz
+    double* d_par = nullptr;      // 8: dE/d(V0, S0)
+    double* d_gmol = nullptr;     // 9 n_mol: per-molecule force partials
+    double* d_pmol = nullptr;     // 8 n_mol: per-molecule parameter partials
     DeviceScalars* d_sc = nullptr;
     DeviceScalars* h_sc = nullptr;   // pinned mirror
 
@@ -219,7 +224,7 @@ inline int dalloc(Ctx* c, P** p, size_t n) {
 // model
 cudaError_t launch_sk_blocks(Ctx* c);
 cudaError_t launch_gamma(Ctx* c, const double* dq, double* Q);
-cudaError_t launch_build_h(Ctx* c);
+cudaError_t launch_build_h(Ctx* c, double eps_threshold);
 cudaError_t launch_guess(Ctx* c);
 // sparse structure and products
 cudaError_t launch_colindex(Ctx* c);
@@ -236,6 +241,8 @@ cudaError_t launch_compact(Ctx* c);                      // drop all-zero tiles;
 // charges
 cudaError_t launch_charges_finish(Ctx* c, bool mix);
 cudaError_t launch_count_tiles(Ctx* c, unsigned long long* out);
+// adjoint
+cudaError_t launch_adjoint(Ctx* c, double* d_grad, double* d_par, double* d_gmol, double* d_pmol);
 
 }  // namespace sscf
 
