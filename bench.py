@@ -279,9 +279,25 @@ def main():
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
     peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
 
+    # FP32 (or FP64) ALU peak from unit counts and the maximum SM clock:
+    # 152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz; FP64 at 1/64 of it
+    sm_clk = float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
+    alu_peak = 152 * 128 * 2 * sm_clk / 1e12 * (1.0 if prec == SSCF_MIXED else 1.0 / 64)
+    upd = {"apply_rot": mean("upd_rot"), "apply_ortho": mean("upd_combo")}
+
     def roof(name):
         calls = prof[name][1] / K
         t_call = prof[name][0] / max(prof[name][1], 1) / 1e3
+        if name in upd:
+            # 2x2 updates: 2 FMAs (4 flops) per AO row and pair
+            achieved = 4.0 * upd[name] / max(calls, 1) / t_call / 1e12
+            return {"kernel": name, "bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
+                    "frac": achieved / alu_peak, "traffic": None,
+                    "peak_source": "derived: 152 SMs x 128 lanes x 2 flops x max SM clock",
+                    "hbm_view": {"algorithmic_bytes": algo_bytes[name],
+                                 "achieved_gbs": algo_bytes[name] / max(calls, 1) / t_call / 1e9,
+                                 "peak_gbs": hbm_peak},
+                    "ms_per_step": per_step[name]}
         b = algo_bytes.get(name)
         if b is None:
             return None
@@ -292,6 +308,9 @@ def main():
 
     roofline = roof(dominant)
     kernels = {k: {"ms_per_step": round(v, 3), "calls_per_step": prof[k][1] / K} for k, v in per_step.items()}
+    for name in ("apply_rot", "transform_ov", "transform_ss", "density", "xc_h"):
+        if name in prof and name != dominant:
+            kernels[name]["roofline"] = roof(name)
 
     cpu = None
     if not args.no_cpu_baseline:

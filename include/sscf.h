@@ -80,6 +80,8 @@ typedef struct {
     int64_t nnz_c;           /* stored values of C: tiles x 96 (6 AO rows x 16 MOs)       */
     int64_t nnz_occ;         /* stored values of the occupied tiles                      */
     int64_t launches;        /* kernels launched by the step                              */
+    int64_t upd_rot;         /* 2x2 row updates applied by the rotation sweep (pairs x rows) */
+    int64_t upd_combo;       /* 2x2 row updates applied by the orthonormalisation pass    */
     int iteration;
 } sscf_step_info;
 

@@ -60,7 +60,8 @@ class StepInfo(ctypes.Structure):
     _fields_ = [("energy", ctypes.c_double), ("dq_max", ctypes.c_double), ("dE", ctypes.c_double),
                 ("max_fov", ctypes.c_double), ("eta", ctypes.c_double), ("n_rot", ctypes.c_int64),
                 ("n_combo", ctypes.c_int64), ("nnz_c", ctypes.c_int64), ("nnz_occ", ctypes.c_int64),
-                ("launches", ctypes.c_int64), ("iteration", ctypes.c_int)]
+                ("launches", ctypes.c_int64), ("upd_rot", ctypes.c_int64), ("upd_combo", ctypes.c_int64),
+                ("iteration", ctypes.c_int)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -833,6 +833,8 @@ int sscf_step(sscf_ctx* h, sscf_step_info* info) {
         info->nnz_c = (int64_t)c.h_sc->tiles[0] * kTileVals;
         info->nnz_occ = (int64_t)c.h_sc->tiles[1] * kTileVals;
         info->launches = (int64_t)(c.n_launch - l0);
+        info->upd_rot = (int64_t)c.h_sc->upd[0];
+        info->upd_combo = (int64_t)c.h_sc->upd[1];
         info->iteration = c.iteration;
     }
     if (!std::isfinite(c.h_sc->energy)) return SSCF_ERR_NONFINITE;

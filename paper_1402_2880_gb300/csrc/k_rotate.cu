@@ -387,6 +387,7 @@ struct SweepArgs {
     const uint16_t* pr_ij;
     const void* pr_cs;
     const double* dsc;       // combinations: divide the pass's MOs by d_i first
+    unsigned long long* upd; // counter of 2x2 row updates
     const int* cci_ptr;
     const int* cci_row;
     const int* cci_slot;
@@ -607,6 +608,7 @@ __global__ void __launch_bounds__(apply_threads<T>()) k_apply_colour(SweepArgs a
         return;
     }
     const int nk = min(CH, n_rows - k0);
+    if (threadIdx.x == 0) atomicAdd(a.upd, (unsigned long long)np * (unsigned long long)(nk * 6));
     // a combination block inside one group: both sides are the same tiles, held once
     const bool same = MODE == 1 && A == B;
     const int pav = sa.run1 >= 0 ? a.cci_ptr[sa.run1] : 0;
@@ -897,6 +899,7 @@ static void fill_args(Ctx* c, SweepArgs& a, int mode, int which) {
     a.pr_ij = c->d_pr_ij;
     a.pr_cs = c->d_pr_cs;
     a.dsc = c->d_scale;
+    a.upd = &c->d_sc->upd[mode == 0 ? 0 : 1];
     a.cci_ptr = c->d_cci_ptr;
     a.cci_row = c->d_cci_row;
     a.cci_slot = c->d_cci_slot;

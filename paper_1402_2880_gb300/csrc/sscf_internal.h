@@ -60,6 +60,7 @@ struct DeviceScalars {
     double dq_max;
     double energy;
     unsigned long long tiles[2];  // stored tiles of C, occupied tiles among them
+    unsigned long long upd[2];    // 2x2 row updates of the sweep: rotations, combinations
     unsigned long long hist[256];
 };
 

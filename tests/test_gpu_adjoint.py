@@ -40,3 +40,32 @@ def test_gradients_match_oracle(n, prec, tol):
     assert np.abs(gp - rgp).max() <= tol * np.abs(rgp).max()
     # net force vanishes (translation invariance of the energy)
     assert np.abs(g.sum(axis=0)).max() < 1e-6 * np.abs(g).max() + (1e-4 if prec else 1e-8)
+
+
+def test_autograd_function_backward():
+    import torch
+
+    from gpu_common import library
+    library()
+    from paper_1402_2880_gb300.autograd import scc_energy
+    s = water(8, seed=3, sigma=0.1)
+    xyz = torch.tensor(s.xyz, dtype=torch.float64, requires_grad=True)
+    V0 = torch.tensor(P["V0"], dtype=torch.float64, requires_grad=True)
+    S0 = torch.tensor(P["S0"], dtype=torch.float64, requires_grad=True)
+    E = scc_energy(s, xyz, V0, S0, P)
+    (2.0 * E).backward()
+    ctx = context(s)
+    ctx.run(allow_not_converged=True)
+    g, gp = ctx.gradients()
+    assert np.allclose(xyz.grad.numpy(), 2.0 * g, rtol=0, atol=1e-9 * np.abs(g).max())
+    assert np.allclose(V0.grad.numpy(), 2.0 * gp[:4], rtol=1e-9, atol=0)
+    assert np.allclose(S0.grad.numpy(), 2.0 * gp[4:], rtol=1e-9, atol=0)
+    # one finite-difference check through the function itself (FP64 path)
+    h = 1e-4
+    k = int(np.argmax(np.abs(g[:, 0])))
+    xp = xyz.detach().clone()
+    xm = xyz.detach().clone()
+    xp[k, 0] += h
+    xm[k, 0] -= h
+    fd = (scc_energy(s, xp, V0.detach(), S0.detach(), P) - scc_energy(s, xm, V0.detach(), S0.detach(), P)) / (2 * h)
+    assert abs(float(fd) - g[k, 0]) < 1e-4 * np.abs(g).max()
