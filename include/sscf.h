@@ -39,12 +39,18 @@ enum { SSCF_ORTHO_ALL = 0, SSCF_ORTHO_OCC = 1 };
 
 typedef struct sscf_ctx sscf_ctx;
 
-/* Geometry and partition (host arrays, copied at sscf_create). */
+/* Geometry and partition (host arrays, copied at sscf_create). One context
+ * may hold several independent clusters (batch mode): molecules of a cluster
+ * are consecutive, clusters are numbered 0, 1, ... in order, groups never
+ * span two clusters and are numbered cluster by cluster. Nothing couples two
+ * clusters: no Hamiltonian or overlap element, no group neighbour, no gamma
+ * term; every kernel launch serves all clusters at once. */
 typedef struct {
     int n_atoms;              /* 3 * n_mol                                              */
     const int* species;       /* n_atoms: 0 = O, 1 = H; molecule-major O, H, H          */
     const double* xyz;        /* 3 * n_atoms, bohr                                       */
-    const int* group_of_mol;  /* n_atoms / 3: MO-group index of every molecule          */
+    const int* group_of_mol;  /* n_atoms / 3: MO-group index of every molecule (<= 8 per group) */
+    const int* cluster_of_mol; /* n_atoms / 3: cluster index, or NULL for one cluster    */
 } sscf_system;
 
 /* Model and SCF parameters (Section "Specific implementation for DFTB",
@@ -161,7 +167,7 @@ int sscf_reset_charges(sscf_ctx* ctx, double* E_out);
 int sscf_step(sscf_ctx* ctx, sscf_step_info* info);
 
 /* Loose stage (eps 1e-3, dq 1e-1), full orthonormalisation, user stage until
- * dq_max <= dq_tol and |dE| <= e_tol, final occupied orthonormalisation to
+ * dq_max <= dq_tol and |dE| <= e_tol in every cluster, final occupied orthonormalisation to
  * eps / 100 and final charges and energy. Returns NOT_CONVERGED with the
  * state kept if max_scc is reached. */
 int sscf_run(sscf_ctx* ctx, sscf_step_info* info);
@@ -176,6 +182,12 @@ int sscf_run(sscf_ctx* ctx, sscf_step_info* info);
  * dE_dparams: host, 8: dE/dV0[0..3], dE/dS0[0..3], or NULL.
  * The charges of the current MOs become the SCC input (as sscf_reset_charges). */
 int sscf_gradients(sscf_ctx* ctx, double* dE_dxyz, double* dE_dparams);
+
+/* Batch mode: per-cluster results of the last charge update (sscf_step,
+ * sscf_density, sscf_reset_charges, sscf_run): energies and max |q - q_prev|.
+ * Outputs are host arrays of n_clusters entries (n_clusters_out, if not NULL,
+ * receives the count; any array may be NULL). */
+int sscf_get_cluster_results(sscf_ctx* ctx, double* energy, double* dq_max, int* n_clusters_out);
 
 /* Tracing --------------------------------------------------------------- */
 

@@ -32,7 +32,7 @@ EXPORTED = [
     "sscf_density", "sscf_reset_charges", "sscf_step", "sscf_run", "sscf_get_C_dense",
     "sscf_set_C_dense", "sscf_get_H_dense", "sscf_get_F_dense", "sscf_get_charges",
     "sscf_set_charges", "sscf_get_colouring", "sscf_get_pairs", "sscf_profile", "sscf_profile_read",
-    "sscf_select_pairs_noalloc", "sscf_gradients",
+    "sscf_select_pairs_noalloc", "sscf_gradients", "sscf_get_cluster_results",
 ]
 
 
@@ -44,7 +44,8 @@ class SscfError(RuntimeError):
 
 class System(ctypes.Structure):
     _fields_ = [("n_atoms", ctypes.c_int), ("species", ctypes.POINTER(ctypes.c_int)),
-                ("xyz", ctypes.POINTER(ctypes.c_double)), ("group_of_mol", ctypes.POINTER(ctypes.c_int))]
+                ("xyz", ctypes.POINTER(ctypes.c_double)), ("group_of_mol", ctypes.POINTER(ctypes.c_int)),
+                ("cluster_of_mol", ctypes.POINTER(ctypes.c_int))]
 
 
 class Params(ctypes.Structure):
@@ -111,6 +112,7 @@ def load() -> ctypes.CDLL:
         "sscf_profile_read": (c_int, [c_vp, c_int, ctypes.c_char_p, P(c_double), P(c_i64), P(c_int)]),
         "sscf_select_pairs_noalloc": (c_int, [c_vp, c_i64, c_double, c_i64, c_vp, P(c_i64), c_vp]),
         "sscf_gradients": (c_int, [c_vp, P(c_double), P(c_double)]),
+        "sscf_get_cluster_results": (c_int, [c_vp, P(c_double), P(c_double), P(c_int)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -164,13 +166,15 @@ class Context:
     """One cluster on the GPU (wraps an ``sscf_ctx``)."""
 
     def __init__(self, species, xyz, group_of_mol, params: dict, precision: int = SSCF_FP64,
-                 stream: int | None = None, ortho_every: int = 1, cap_tiles: int = 0):
+                 stream: int | None = None, ortho_every: int = 1, cap_tiles: int = 0, cluster_of_mol=None):
         self.lib = load()
         self._species = np.ascontiguousarray(species, dtype=np.int32)
         self._xyz = np.ascontiguousarray(xyz, dtype=np.float64).reshape(-1)
         self._groups = np.ascontiguousarray(group_of_mol, dtype=np.int32)
+        self._clusters = None if cluster_of_mol is None else np.ascontiguousarray(cluster_of_mol, dtype=np.int32)
         sysc = System(n_atoms=int(self._species.size), species=_ptr(self._species, ctypes.c_int),
-                      xyz=_ptr(self._xyz), group_of_mol=_ptr(self._groups, ctypes.c_int))
+                      xyz=_ptr(self._xyz), group_of_mol=_ptr(self._groups, ctypes.c_int),
+                      cluster_of_mol=_ptr(self._clusters, ctypes.c_int))
         self.params = make_params(params, precision, ortho_every, cap_tiles)
         h = ctypes.c_void_p()
         _check(self.lib.sscf_create(ctypes.byref(sysc), ctypes.byref(self.params),
@@ -183,7 +187,19 @@ class Context:
 
     @classmethod
     def from_system(cls, sysm, params: dict, **kw):
+        clusters = getattr(sysm, "cluster_of_mol", None)
+        if clusters is not None and "cluster_of_mol" not in kw:
+            kw["cluster_of_mol"] = clusters
         return cls(sysm.species, sysm.xyz, sysm.group_of_mol, params, **kw)
+
+    def cluster_results(self):
+        """(energy, max |q - q_prev|) of every cluster after the last charge update."""
+        n = ctypes.c_int()
+        _check(self.lib.sscf_get_cluster_results(self.h, None, None, ctypes.byref(n)), "sscf_get_cluster_results")
+        e = np.empty(n.value)
+        d = np.empty(n.value)
+        _check(self.lib.sscf_get_cluster_results(self.h, _ptr(e), _ptr(d), None), "sscf_get_cluster_results")
+        return e, d
 
     def close(self):
         if getattr(self, "h", None):

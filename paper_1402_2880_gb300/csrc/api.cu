@@ -99,6 +99,7 @@ int build_structure(Ctx& c, const sscf_system* sys) {
                     int x = cx + dx, y = cy + dy, z = cz + dz;
                     if (x < 0 || y < 0 || z < 0 || x >= grid.n[0] || y >= grid.n[1] || z >= grid.n[2]) continue;
                     for (int n = grid.head[x + grid.n[0] * (y + grid.n[1] * z)]; n >= 0; n = grid.next[n]) {
+                        if (c.h_mol_cluster[n] != c.h_mol_cluster[m]) continue;
                         bool hit = (n == m);
                         for (int a = 0; a < 3 && !hit; ++a)
                             for (int b = 0; b < 3 && !hit; ++b)
@@ -129,6 +130,9 @@ int build_structure(Ctx& c, const sscf_system* sys) {
     int o = 0, v = c.n_occ, ot = 0;
     for (int g = 0; g < G; ++g) {
         if (mols[g].empty() || mols[g].size() > 8) return SSCF_ERR_INVALID_ARG;
+        for (int m : mols[g])
+            if (c.h_mol_cluster[m] != c.h_mol_cluster[mols[g][0]]) return SSCF_ERR_INVALID_ARG;
+        if (g > 0 && c.h_mol_cluster[mols[g][0]] < c.h_mol_cluster[mols[g - 1][0]]) return SSCF_ERR_INVALID_ARG;
         for (size_t k = 0; k < mols[g].size(); ++k) c.h_mol_local[mols[g][k]] = (int)k;
         int nm = (int)mols[g].size();
         c.h_group_nmol[g] = nm;
@@ -197,6 +201,7 @@ int build_structure(Ctx& c, const sscf_system* sys) {
                     int x = cx + dx, y = cy + dy, z = cz + dz;
                     if (x < 0 || y < 0 || z < 0 || x >= gg.n[0] || y >= gg.n[1] || z >= gg.n[2]) continue;
                     for (int B = gg.head[x + gg.n[0] * (y + gg.n[1] * z)]; B >= 0; B = gg.next[B]) {
+                        if (c.h_mol_cluster[mols[B][0]] != c.h_mol_cluster[mols[A][0]]) continue;
                         bool hit = (A == B);
                         for (size_t i = 0; i < gatoms[A].size() && !hit; ++i)
                             for (size_t j = 0; j < gatoms[B].size() && !hit; ++j)
@@ -505,6 +510,24 @@ int sscf_create(const sscf_system* sys, const sscf_params* prm, void* cuda_strea
     c.h_species.assign(sys->species, sys->species + c.n_atoms);
     c.h_xyz.assign(sys->xyz, sys->xyz + 3 * c.n_atoms);
     c.h_mol_group.assign(sys->group_of_mol, sys->group_of_mol + c.n_mol);
+    c.h_mol_cluster.assign(c.n_mol, 0);
+    if (sys->cluster_of_mol) c.h_mol_cluster.assign(sys->cluster_of_mol, sys->cluster_of_mol + c.n_mol);
+    c.n_clusters = 0;
+    for (int m = 0; m < c.n_mol; ++m) {
+        const int cl = c.h_mol_cluster[m];
+        const int prev = m ? c.h_mol_cluster[m - 1] : -1;
+        if (cl != prev && cl != prev + 1) {   // clusters consecutive and numbered in order
+            delete h;
+            return SSCF_ERR_INVALID_ARG;
+        }
+        c.n_clusters = cl + 1;
+    }
+    c.h_cl_mol0.assign(c.n_clusters, 0);
+    c.h_cl_nmol.assign(c.n_clusters, 0);
+    for (int m = c.n_mol - 1; m >= 0; --m) {
+        c.h_cl_mol0[c.h_mol_cluster[m]] = m;
+        c.h_cl_nmol[c.h_mol_cluster[m]]++;
+    }
     int G = 0;
     for (int m = 0; m < c.n_mol; ++m) {
         if (c.h_mol_group[m] < 0) {
@@ -525,13 +548,27 @@ int sscf_create(const sscf_system* sys, const sscf_params* prm, void* cuda_strea
         delete h;
         return s;
     };
-    c.cap = prm->cap_tiles > 0 ? std::min(prm->cap_tiles, c.n_tiles) : c.n_tiles;
+    // per-cluster sizes: a row of C only holds tiles of its own cluster, a
+    // column of Y only rows of its own cluster
+    {
+        std::vector<int> cl_tiles(c.n_clusters, 0), cl_otiles(c.n_clusters, 0);
+        std::vector<int> g_cl(c.n_groups, 0);
+        for (int m = 0; m < c.n_mol; ++m) g_cl[c.h_mol_group[m]] = c.h_mol_cluster[m];
+        for (int t = 0; t < c.n_tiles; ++t) {
+            cl_tiles[g_cl[c.h_tile_group[t]]]++;
+            if (c.h_tile_kind[t] == 0) cl_otiles[g_cl[c.h_tile_group[t]]]++;
+        }
+        c.max_cl_tiles = *std::max_element(cl_tiles.begin(), cl_tiles.end());
+        c.max_cl_otiles = *std::max_element(cl_otiles.begin(), cl_otiles.end());
+        c.max_cl_mol = *std::max_element(c.h_cl_nmol.begin(), c.h_cl_nmol.end());
+    }
+    c.cap = prm->cap_tiles > 0 ? std::min(prm->cap_tiles, c.max_cl_tiles) : c.max_cl_tiles;
     c.cap = std::max(c.cap, 2);
     if (c.n_tiles > 32768) {   // tile ids and slots are packed into 16 bits in the sweep kernel
         delete h;
         return SSCF_ERR_INVALID_ARG;
     }
-    c.capY = c.n_mol;
+    c.capY = c.max_cl_mol;
     // uploads
 #define UP(d, v)                        \
     do {                                \
@@ -562,6 +599,38 @@ int sscf_create(const sscf_system* sys, const sscf_params* prm, void* cuda_strea
         if (c.h_gnb_row[e] == c.h_gnb_col[e]) c.h_self_blk[c.h_gnb_row[e]] = e;
     UP(c.d_self_blk, c.h_self_blk);
     UP(c.d_tile_group, c.h_tile_group);
+    {
+        std::vector<int> g_row0(c.n_groups, 0), tile_row0(c.n_tiles), mol_row0(c.n_mol), mol_ot0(c.n_mol);
+        std::vector<int> cl_ot0(c.n_clusters, 1 << 30), lo(c.n_atoms), hi(c.n_atoms);
+        for (int m = c.n_mol - 1; m >= 0; --m) g_row0[c.h_mol_group[m]] = c.h_cl_mol0[c.h_mol_cluster[m]];
+        for (int t = 0; t < c.n_tiles; ++t) tile_row0[t] = g_row0[c.h_tile_group[t]];
+        for (int m = 0; m < c.n_mol; ++m) {
+            mol_row0[m] = c.h_cl_mol0[c.h_mol_cluster[m]];
+            const int cl = c.h_mol_cluster[m];
+            cl_ot0[cl] = std::min(cl_ot0[cl], c.h_group_ot0[c.h_mol_group[m]]);
+        }
+        for (int m = 0; m < c.n_mol; ++m) mol_ot0[m] = cl_ot0[c.h_mol_cluster[m]];
+        for (int a2 = 0; a2 < c.n_atoms; ++a2) {
+            const int cl = c.h_mol_cluster[a2 / 3];
+            lo[a2] = 3 * c.h_cl_mol0[cl];
+            hi[a2] = 3 * (c.h_cl_mol0[cl] + c.h_cl_nmol[cl]);
+        }
+        std::vector<int> group_cl(c.n_groups, 0);
+        for (int m = 0; m < c.n_mol; ++m) group_cl[c.h_mol_group[m]] = c.h_mol_cluster[m];
+        UP(c.d_group_cl, group_cl);
+        c.h_cl_sel_init.assign((size_t)c.n_clusters * 6, 0ull);
+        for (int cl = 0; cl < c.n_clusters; ++cl)
+            c.h_cl_sel_init[(size_t)cl * 6 + 5] =
+                (unsigned long long)(c.prm.rot_cap_factor * (double)(4 * c.h_cl_nmol[cl]));
+        UP(c.d_tile_row0, tile_row0);
+        UP(c.d_mol_row0, mol_row0);
+        UP(c.d_mol_ot0, mol_ot0);
+        UP(c.d_mol_cluster, c.h_mol_cluster);
+        UP(c.d_atom_lo, lo);
+        UP(c.d_atom_hi, hi);
+        UP(c.d_cl_mol0, c.h_cl_mol0);
+        UP(c.d_cl_nmol, c.h_cl_nmol);
+    }
     UP(c.d_tile_kind, c.h_tile_kind);
     UP(c.d_tile_loc0, c.h_tile_loc0);
     UP(c.d_tile_nmo, c.h_tile_nmo);
@@ -636,6 +705,11 @@ int sscf_create(const sscf_system* sys, const sscf_params* prm, void* cuda_strea
     AL(c.d_Q, (size_t)c.n_atoms * 8);
     AL(c.d_e_mol, (size_t)c.n_mol * 8);
     AL(c.d_red, (size_t)(c.n_mol + 4096) * 8);
+    AL(c.d_cl_E, (size_t)c.n_clusters * 8);
+    AL(c.d_cl_sel, (size_t)c.n_clusters * 6 * 8);
+    AL(c.d_cl_hist, (size_t)c.n_clusters * 256 * 8);
+    AL(c.d_cl_eta, (size_t)c.n_clusters * 8);
+    AL(c.d_cl_dq, (size_t)c.n_clusters * 8);
     AL(c.d_grad, (size_t)c.n_atoms * 3 * 8);
     AL(c.d_par, 8 * 8);
     AL(c.d_gmol, (size_t)c.n_mol * 9 * 8);
@@ -648,6 +722,8 @@ int sscf_create(const sscf_system* sys, const sscf_params* prm, void* cuda_strea
         return fail(SSCF_ERR_OOM);
     }
     if (cudaMemsetAsync(c.d_sc, 0, sizeof(DeviceScalars), c.stream) != cudaSuccess) return fail(SSCF_ERR_CUDA);
+    if (cudaMemsetAsync(c.d_cl_hist, 0, (size_t)c.n_clusters * 256 * 8, c.stream) != cudaSuccess)
+        return fail(SSCF_ERR_CUDA);
     for (double* p : {c.d_q, c.d_q_prev, c.d_dq_in, c.d_Q_in, c.d_dq, c.d_Q})
         if (cudaMemsetAsync(p, 0, (size_t)c.n_atoms * 8, c.stream) != cudaSuccess) return fail(SSCF_ERR_CUDA);
     for (int b = 0; b < 2; ++b)
@@ -864,6 +940,16 @@ int sscf_gradients(sscf_ctx* h, double* dE_dxyz, double* dE_dparams) {
     return SSCF_OK;
 }
 
+int sscf_get_cluster_results(sscf_ctx* h, double* energy, double* dq_max, int* n_clusters_out) {
+    if (!h) return SSCF_ERR_INVALID_ARG;
+    Ctx& c = h->c;
+    CK(cudaStreamSynchronize(c.stream));
+    if (energy) CK(cudaMemcpy(energy, c.d_cl_E, (size_t)c.n_clusters * 8, cudaMemcpyDeviceToHost));
+    if (dq_max) CK(cudaMemcpy(dq_max, c.d_cl_dq, (size_t)c.n_clusters * 8, cudaMemcpyDeviceToHost));
+    if (n_clusters_out) *n_clusters_out = c.n_clusters;
+    return SSCF_OK;
+}
+
 int sscf_profile(sscf_ctx* h, int enable) {
     if (!h) return SSCF_ERR_INVALID_ARG;
     Ctx& c = h->c;
@@ -908,9 +994,18 @@ int sscf_run(sscf_ctx* h, sscf_step_info* info) {
         CKS(sscf_orthonormalise(h, SSCF_ORTHO_ALL, 200, nullptr, nullptr));
         if (s == 0) CKS(sscf_reset_charges(h, nullptr));
         converged = false;
+        std::vector<double> e_prev(c.n_clusters), e_now(c.n_clusters), dq_now(c.n_clusters);
+        CKS(sscf_get_cluster_results(h, e_prev.data(), nullptr, nullptr));
         for (int it = 0; it < c.prm.max_scc; ++it) {
             CKS(sscf_step(h, &last));
-            if (last.dq_max <= stages[s].dq && std::fabs(last.dE) <= stages[s].e) {
+            CKS(sscf_get_cluster_results(h, e_now.data(), dq_now.data(), nullptr));
+            double de = 0.0, dq = 0.0;
+            for (int k = 0; k < c.n_clusters; ++k) {
+                de = std::max(de, std::fabs(e_now[k] - e_prev[k]));
+                dq = std::max(dq, dq_now[k]);
+            }
+            e_prev = e_now;
+            if (dq <= stages[s].dq && de <= stages[s].e) {
                 converged = true;
                 break;
             }

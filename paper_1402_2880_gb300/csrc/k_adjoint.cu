@@ -266,20 +266,22 @@ __device__ void pair_terms(const SKd& P, const double* xa, const double* xb, int
 constexpr int kGradWarps = 8;
 template <typename T>
 __global__ void __launch_bounds__(kGradWarps * 32)
-k_grad_blocks(int n_occ_tiles, int cap, const int* __restrict__ c_nt, const int* __restrict__ c_tile,
+k_grad_blocks(int n_occ_tiles, int map_n, const int* __restrict__ mol_ot0, int cap, const int* __restrict__ c_nt,
+              const int* __restrict__ c_tile,
               const T* __restrict__ c_val, const int* __restrict__ z_nt, const int* __restrict__ z_tile,
               const T* __restrict__ z_val, const int* __restrict__ mp_ptr, const int* __restrict__ mp_col,
               const double* __restrict__ xyz, const double* __restrict__ Q, SKd P, double* __restrict__ gmol,
               double* __restrict__ pmol) {
-    extern __shared__ int smap[];   // n_occ_tiles: slot of tile in C row m or -1
+    extern __shared__ int smap[];   // map_n: slot in C row m of each occupied tile of m's cluster, or -1
     __shared__ double part[kGradWarps][17];
     const int m = blockIdx.x;
-    for (int i = threadIdx.x; i < n_occ_tiles; i += blockDim.x) smap[i] = -1;
+    const int t0 = mol_ot0[m];
+    for (int i = threadIdx.x; i < map_n; i += blockDim.x) smap[i] = -1;
     __syncthreads();
     const int ntm = c_nt[m];
     for (int s = threadIdx.x; s < ntm; s += blockDim.x) {
         const int t = c_tile[(size_t)m * cap + s];
-        if (t < n_occ_tiles) smap[t] = s;
+        if (t < n_occ_tiles) smap[t - t0] = s;
     }
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -296,7 +298,7 @@ k_grad_blocks(int n_occ_tiles, int cap, const int* __restrict__ c_nt, const int*
         for (int s = half; s < ntn; s += 2) {
             const int t = c_tile[(size_t)n * cap + s];
             if (t >= n_occ_tiles) break;
-            const int sm_ = smap[t];
+            const int sm_ = smap[t - t0];
             if (sm_ < 0) continue;
             const T* cm = c_val + ((size_t)m * cap + sm_) * kTileVals + col;
             const T* cn = c_val + ((size_t)n * cap + s) * kTileVals + col;
@@ -311,7 +313,7 @@ k_grad_blocks(int n_occ_tiles, int cap, const int* __restrict__ c_nt, const int*
         const int nzn = z_nt[n];
         for (int s = half; s < nzn; s += 2) {
             const int t = z_tile[(size_t)n * cap + s];
-            const int sm_ = smap[t];
+            const int sm_ = smap[t - t0];
             if (sm_ < 0) continue;
             const T* cm = c_val + ((size_t)m * cap + sm_) * kTileVals + col;
             const T* zn = z_val + ((size_t)n * cap + s) * kTileVals + col;
@@ -374,13 +376,15 @@ k_grad_blocks(int n_occ_tiles, int cap, const int* __restrict__ c_nt, const int*
 
 // dE/dx_a of dq^T gamma dq / 2: -dq_a sum_b dq_b gamma_ab^3 (x_a - x_b)
 __global__ void k_gamma_force(int n, const double* __restrict__ xyz, const int* __restrict__ species,
+                              const int* __restrict__ atom_lo, const int* __restrict__ atom_hi,
                               const double* __restrict__ dq, double invU0, double invU1, double* __restrict__ out) {
     const int a = blockIdx.x * blockDim.x + threadIdx.x;
     if (a >= n) return;
+    const int b_lo = atom_lo[a], b_hi = atom_hi[a];   // gamma couples atoms of one cluster only
     const double xa = xyz[3 * a], ya = xyz[3 * a + 1], za = xyz[3 * a + 2];
     const double ia = species[a] == 0 ? invU0 : invU1;
     double f[3] = {0, 0, 0};
-    for (int b = 0; b < n; ++b) {
+    for (int b = b_lo; b < b_hi; ++b) {
         if (b == a) continue;
         const double dx = xa - xyz[3 * b], dy = ya - xyz[3 * b + 1], dz = za - xyz[3 * b + 2];
         const double h = 0.5 * (ia + (species[b] == 0 ? invU0 : invU1));
@@ -424,13 +428,14 @@ static cudaError_t adjoint_t(Ctx* c, double* d_grad, double* d_par, double* d_gm
     }
     P.r_decay = c->prm.r_decay;
     P.rc2 = c->prm.r_cut * c->prm.r_cut;
-    const size_t smem_g = (size_t)c->n_occ_tiles * 4;
+    const size_t smem_g = (size_t)c->max_cl_otiles * 4;
     e = cudaFuncSetAttribute(k_grad_blocks<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_g);
     if (e != cudaSuccess) return e;
     k_grad_blocks<T><<<c->n_mol, kGradWarps * 32, smem_g, c->stream>>>(
-        c->n_occ_tiles, c->cap, c->d_c_nt[in], c->d_c_tile[in], (const T*)c->d_c_val[in], c->d_c_nt[zb],
+        c->n_occ_tiles, c->max_cl_otiles, c->d_mol_ot0, c->cap, c->d_c_nt[in], c->d_c_tile[in], (const T*)c->d_c_val[in], c->d_c_nt[zb],
         c->d_c_tile[zb], (const T*)c->d_c_val[zb], c->d_mp_ptr, c->d_mp_col, c->d_xyz, c->d_Q, P, d_gmol, d_pmol);
-    k_gamma_force<<<(c->n_atoms + 127) / 128, 128, 0, c->stream>>>(c->n_atoms, c->d_xyz, c->d_species, c->d_dq,
+    k_gamma_force<<<(c->n_atoms + 127) / 128, 128, 0, c->stream>>>(c->n_atoms, c->d_xyz, c->d_species, c->d_atom_lo,
+                                                                  c->d_atom_hi, c->d_dq,
                                                                   1.0 / c->prm.U[0], 1.0 / c->prm.U[1], d_grad);
     k_grad_finish<<<1, 1024, 0, c->stream>>>(c->n_mol, d_gmol, d_pmol, d_grad, d_par);
     c->n_launch += 4;

@@ -13,6 +13,38 @@ __global__ void k_dq(int n, const double* __restrict__ q, const int* __restrict_
     if (a < n) dq[a] = q[a] - (species[a] == 0 ? q0O : q0H);
 }
 
+// One CTA per cluster: its energy (band + Coulomb) and max |q - q_prev|,
+// fixed-order reductions.
+__global__ void k_cluster_reduce(const int* __restrict__ cl_mol0, const int* __restrict__ cl_nmol,
+                                 const double* __restrict__ e_mol, const double* __restrict__ q,
+                                 const double* __restrict__ q_prev, const double* __restrict__ dq,
+                                 const double* __restrict__ Q, double* __restrict__ cl_E, double* __restrict__ cl_dq) {
+    __shared__ double s_e[256], s_m[256];
+    const int cl = blockIdx.x;
+    const int m0 = cl_mol0[cl], nm = cl_nmol[cl];
+    double e = 0.0, mx = 0.0;
+    for (int m = threadIdx.x; m < nm; m += blockDim.x) e += e_mol[m0 + m];
+    for (int a = threadIdx.x; a < 3 * nm; a += blockDim.x) {
+        const int at = 3 * m0 + a;
+        e += 0.5 * dq[at] * Q[at];
+        mx = fmax(mx, fabs(q[at] - q_prev[at]));
+    }
+    s_e[threadIdx.x] = e;
+    s_m[threadIdx.x] = mx;
+    __syncthreads();
+    for (int off = blockDim.x / 2; off > 0; off >>= 1) {
+        if ((int)threadIdx.x < off) {
+            s_e[threadIdx.x] += s_e[threadIdx.x + off];
+            s_m[threadIdx.x] = fmax(s_m[threadIdx.x], s_m[threadIdx.x + off]);
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        cl_E[cl] = s_e[0];
+        cl_dq[cl] = s_m[0];
+    }
+}
+
 // One CTA: fixed-order reductions (deterministic) and the mixing update.
 __global__ void k_finish(int n_atoms, int n_mol, int mix, double beta, const double* __restrict__ e_mol,
                          double* __restrict__ q, double* __restrict__ q_prev, const double* __restrict__ dq,
@@ -92,6 +124,9 @@ cudaError_t launch_charges_finish(Ctx* c, bool mix) {
                                                          c->prm.q0[1], c->d_dq);
     cudaError_t e = launch_gamma(c, c->d_dq, c->d_Q);
     if (e != cudaSuccess) return e;
+    k_cluster_reduce<<<c->n_clusters, 256, 0, c->stream>>>(c->d_cl_mol0, c->d_cl_nmol, c->d_e_mol, c->d_q, c->d_q_prev,
+                                                          c->d_dq, c->d_Q, c->d_cl_E, c->d_cl_dq);
+    c->n_launch += 1;
     k_finish<<<1, 1024, 0, c->stream>>>(c->n_atoms, c->n_mol, mix ? 1 : 0, c->prm.mix_beta, c->d_e_mol, c->d_q,
                                         c->d_q_prev, c->d_dq, c->d_Q, c->d_dq_in, c->d_Q_in, c->d_sc);
     return cudaGetLastError();

@@ -97,26 +97,40 @@ __global__ void k_sk_blocks(int n_mp, const int* __restrict__ mp_row, const int*
 constexpr int kGammaTile = 256;
 template <typename P>
 __global__ void k_gamma(int n, const double* __restrict__ xyz, const int* __restrict__ species,
+                        const int* __restrict__ atom_lo, const int* __restrict__ atom_hi,
                         const double* __restrict__ dq, double invU0, double invU1, double* __restrict__ Q) {
     __shared__ P sx[kGammaTile * 3];
     __shared__ P sq[kGammaTile];
     __shared__ P si[kGammaTile];
+    __shared__ int s_lo, s_hi;
     const int a = blockIdx.x * blockDim.x + threadIdx.x;
     double xa_d[3] = {0, 0, 0}, ia_d = invU0;
+    int lo = 1 << 30, hi = -1;   // gamma couples atoms of one cluster only
     if (a < n) {
         xa_d[0] = xyz[3 * a];
         xa_d[1] = xyz[3 * a + 1];
         xa_d[2] = xyz[3 * a + 2];
         ia_d = species[a] == 0 ? invU0 : invU1;
+        lo = atom_lo[a];
+        hi = atom_hi[a];
     }
+    if (threadIdx.x == 0) {
+        s_lo = 1 << 30;
+        s_hi = -1;
+    }
+    __syncthreads();
+    atomicMin(&s_lo, lo);
+    atomicMax(&s_hi, hi);
+    __syncthreads();
     const P xa[3] = {(P)xa_d[0], (P)xa_d[1], (P)xa_d[2]};
     const P ia = (P)ia_d;
     double acc = 0.0;
-    for (int b0 = 0; b0 < n; b0 += kGammaTile) {
+    const int blo = s_lo, bhi = s_hi;
+    for (int b0 = blo; b0 < bhi; b0 += kGammaTile) {
         __syncthreads();
         for (int t = threadIdx.x; t < kGammaTile; t += blockDim.x) {
             int b = b0 + t;
-            if (b < n) {
+            if (b < bhi) {
                 sx[3 * t] = (P)xyz[3 * b];
                 sx[3 * t + 1] = (P)xyz[3 * b + 1];
                 sx[3 * t + 2] = (P)xyz[3 * b + 2];
@@ -129,9 +143,10 @@ __global__ void k_gamma(int n, const double* __restrict__ xyz, const int* __rest
             }
         }
         __syncthreads();
-        const int nb = min(kGammaTile, n - b0);
+        const int nb = min(kGammaTile, bhi - b0);
         P part = 0;
-        for (int t = 0; t < nb; ++t) {
+        const int t_lo = max(0, lo - b0), t_hi = min(nb, hi - b0);
+        for (int t = t_lo; t < t_hi; ++t) {
             const P dx = sx[3 * t] - xa[0], dy = sx[3 * t + 1] - xa[1], dz = sx[3 * t + 2] - xa[2];
             const P d2 = dx * dx + dy * dy + dz * dz;
             const P h = (P)0.5 * (ia + si[t]);
@@ -341,10 +356,12 @@ cudaError_t launch_gamma(Ctx* c, const double* dq, double* Q) {
     c->n_launch += 1;
     const int th = 256;
     if (c->prec == SSCF_FP64)
-        k_gamma<double><<<(c->n_atoms + th - 1) / th, th, 0, c->stream>>>(c->n_atoms, c->d_xyz, c->d_species, dq,
+        k_gamma<double><<<(c->n_atoms + th - 1) / th, th, 0, c->stream>>>(c->n_atoms, c->d_xyz, c->d_species,
+                                                                          c->d_atom_lo, c->d_atom_hi, dq,
                                                                           1.0 / c->prm.U[0], 1.0 / c->prm.U[1], Q);
     else
-        k_gamma<float><<<(c->n_atoms + th - 1) / th, th, 0, c->stream>>>(c->n_atoms, c->d_xyz, c->d_species, dq,
+        k_gamma<float><<<(c->n_atoms + th - 1) / th, th, 0, c->stream>>>(c->n_atoms, c->d_xyz, c->d_species,
+                                                                         c->d_atom_lo, c->d_atom_hi, dq,
                                                                          1.0 / c->prm.U[0], 1.0 / c->prm.U[1], Q);
     return cudaGetLastError();
 }

@@ -39,13 +39,19 @@ __device__ __forceinline__ void side_pos(int loc, int no, int not_, int& tpos, i
 }
 
 // --------------------------------------------------------------------------
-// rotation candidates: count |F_ij| >= tau (F_ij != 0) and the largest |F|
+// rotation candidates: count |F_ij| >= tau (F_ij != 0) per cluster and the
+// largest |F|. The cap of rot_cap_factor * N_occ is a per-cluster rule: every
+// cluster of a batch selects exactly as it would alone.
 // --------------------------------------------------------------------------
+struct ClSel {
+    unsigned long long cand, prefix, mask, rank, thr, kmax;
+};
+
 template <typename T>
 __global__ void k_rot_stats(int n_gnb, const int* __restrict__ gnb_row, const int* __restrict__ gnb_col,
                             const int* __restrict__ group_nmol, const int* __restrict__ group_nvt,
-                            const int* __restrict__ blk_tp0, const T* __restrict__ F, double tau,
-                            DeviceScalars* sc) {
+                            const int* __restrict__ group_cl, const int* __restrict__ blk_tp0,
+                            const T* __restrict__ F, double tau, DeviceScalars* sc, ClSel* cl) {
     const int e = blockIdx.x;
     const int A = gnb_row[e], B = gnb_col[e];
     const int no = 4 * group_nmol[A], nv = 2 * group_nmol[B], nvt = group_nvt[B];
@@ -63,24 +69,24 @@ __global__ void k_rot_stats(int n_gnb, const int* __restrict__ gnb_row, const in
         mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, off));
     }
     if ((threadIdx.x & 31) == 0) {
-        if (cnt) atomicAdd(&sc->cand, (unsigned long long)cnt);
+        if (cnt) atomicAdd(&cl[group_cl[A]].cand, (unsigned long long)cnt);
         atomic_max_pos(&sc->max_fov, mx);
     }
 }
 
-// one radix-select pass over the candidate keys (8 bits, most significant first)
+// one radix-select pass over the candidate keys (8 bits, most significant
+// first) of every cluster whose candidates exceed its cap
 template <typename T>
-__global__ void k_rot_hist(int shift, unsigned long long kmax, int n_gnb, const int* __restrict__ gnb_row,
-                           const int* __restrict__ gnb_col, const int* __restrict__ group_nmol,
-                           const int* __restrict__ group_nvt, const int* __restrict__ blk_tp0,
-                           const T* __restrict__ F, double tau, DeviceScalars* sc) {
-    if (sc->cand <= kmax) return;
-    __shared__ unsigned h[256];
-    for (int i = threadIdx.x; i < 256; i += blockDim.x) h[i] = 0;
-    __syncthreads();
-    const unsigned long long prefix = sc->sel_prefix, mask = sc->sel_mask;
+__global__ void k_rot_hist(int shift, int n_gnb, const int* __restrict__ gnb_row, const int* __restrict__ gnb_col,
+                           const int* __restrict__ group_nmol, const int* __restrict__ group_nvt,
+                           const int* __restrict__ group_cl, const int* __restrict__ blk_tp0,
+                           const T* __restrict__ F, double tau, const ClSel* __restrict__ cl,
+                           unsigned long long* __restrict__ hist) {
     for (int e = blockIdx.x; e < n_gnb; e += gridDim.x) {
         const int A = gnb_row[e], B = gnb_col[e];
+        const int c = group_cl[A];
+        const ClSel s = cl[c];
+        if (s.cand <= s.kmax) continue;
         const int no = 4 * group_nmol[A], nv = 2 * group_nmol[B], nvt = group_nvt[B];
         for (int p = threadIdx.x; p < no * nv; p += blockDim.x) {
             const int i = p / nv, j = p % nv;
@@ -88,34 +94,33 @@ __global__ void k_rot_hist(int shift, unsigned long long kmax, int n_gnb, const 
             const double f = fabs((double)F[(size_t)tp * 256 + (i & 15) * 16 + (j & 15)]);
             if (!(f >= tau && f > 0.0)) continue;
             const unsigned long long k = dkey(f);
-            if ((k & mask) != prefix) continue;
-            atomicAdd(&h[(k >> shift) & 255ull], 1u);
+            if ((k & s.mask) != s.prefix) continue;
+            atomicAdd(&hist[(size_t)c * 256 + ((k >> shift) & 255ull)], 1ull);
         }
     }
-    __syncthreads();
-    for (int i = threadIdx.x; i < 256; i += blockDim.x)
-        if (h[i]) atomicAdd(&sc->hist[i], (unsigned long long)h[i]);
 }
 
-__global__ void k_rot_pick(int shift, unsigned long long kmax, DeviceScalars* sc) {
-    if (sc->cand <= kmax) return;
-    if (shift == 56) {
-        sc->sel_k = kmax;
+// one thread per cluster: pick the bin holding the kmax-th largest key
+__global__ void k_rot_pick(int shift, int n_clusters, ClSel* cl, unsigned long long* hist) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= n_clusters) return;
+    ClSel s = cl[c];
+    unsigned long long* h = hist + (size_t)c * 256;
+    if (s.cand > s.kmax) {
+        if (shift == 56) s.rank = s.kmax;
+        unsigned long long cum = 0;
+        int b = 255;
+        for (; b > 0; --b) {
+            if (cum + h[b] >= s.rank) break;
+            cum += h[b];
+        }
+        s.prefix |= (unsigned long long)b << shift;
+        s.mask |= 255ull << shift;
+        s.rank -= cum;
+        for (int i = 0; i < 256; ++i) h[i] = 0ull;
     }
-    unsigned long long k = sc->sel_k, cum = 0;
-    int b = 255;
-    for (; b > 0; --b) {
-        if (cum + sc->hist[b] >= k) break;
-        cum += sc->hist[b];
-    }
-    sc->sel_prefix |= (unsigned long long)b << shift;
-    sc->sel_mask |= 255ull << shift;
-    sc->sel_k = k - cum;
-    for (int i = 0; i < 256; ++i) sc->hist[i] = 0;
-}
-
-__global__ void k_rot_threshold(unsigned long long kmax, double tau, DeviceScalars* sc) {
-    sc->thr_key = sc->cand > kmax ? sc->sel_prefix : 0ull;
+    if (shift == 0) s.thr = s.cand > s.kmax ? s.prefix : 0ull;
+    cl[c] = s;
 }
 
 // per block: kept pairs sorted by (in-block colour, i_loc) with Jacobi angles
@@ -125,8 +130,9 @@ template <typename T>
 __global__ void k_rot_lists(int n_gnb, const int* __restrict__ gnb_row, const int* __restrict__ gnb_col,
                             const int* __restrict__ group_nmol, const int* __restrict__ group_nvt,
                             const int* __restrict__ group_occ0_mo, const int* __restrict__ group_virt0_mo,
-                            const int* __restrict__ blk_tp0, const T* __restrict__ F,
-                            const double* __restrict__ Fd, double tau, DeviceScalars* sc, int* __restrict__ pr_n,
+                            const int* __restrict__ group_cl, const int* __restrict__ blk_tp0,
+                            const T* __restrict__ F, const double* __restrict__ Fd, double tau, DeviceScalars* sc,
+                            const ClSel* __restrict__ cl, int* __restrict__ pr_n,
                             int* __restrict__ pr_lvl, uint16_t* __restrict__ pr_ij, T* __restrict__ pr_cs,
                             int* __restrict__ pr_touch) {
     __shared__ unsigned char keep[32 * 16];
@@ -135,7 +141,7 @@ __global__ void k_rot_lists(int n_gnb, const int* __restrict__ gnb_row, const in
     const int A = gnb_row[e], B = gnb_col[e];
     const int no = 4 * group_nmol[A], nv = 2 * group_nmol[B], nvt = group_nvt[B];
     const int nsub = max(no, nv);
-    const unsigned long long thr = sc->thr_key;
+    const unsigned long long thr = cl[group_cl[A]].thr;
     for (int p = threadIdx.x; p < 32 * 16; p += blockDim.x) {
         int i = p >> 4, j = p & 15;
         unsigned char kp = 0;
@@ -248,7 +254,8 @@ __global__ void k_ortho_eta(int w, const int* __restrict__ oblk, int n_oblk, con
                             const int* __restrict__ gnb_col, const int* __restrict__ group_nmol,
                             const int* __restrict__ group_not, const int* __restrict__ occ0,
                             const int* __restrict__ virt0, const int* __restrict__ blk_tp,
-                            const T* __restrict__ sig, const double* __restrict__ dsc, DeviceScalars* sc) {
+                            const T* __restrict__ sig, const double* __restrict__ dsc, DeviceScalars* sc,
+                            const int* __restrict__ group_cl, double* __restrict__ cl_eta) {
     const int e = oblk[blockIdx.x];
     const int A = gnb_row[e], B = gnb_col[e];
     const int noA = 4 * group_nmol[A], noB = 4 * group_nmol[B];
@@ -265,7 +272,10 @@ __global__ void k_ortho_eta(int w, const int* __restrict__ oblk, int n_oblk, con
         mx = fmax(mx, fabs(sig_hat(sig, blk_tp, e, same, ia, ib, ci, cj, di, dj)));
     }
     for (int off = 16; off > 0; off >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, off));
-    if ((threadIdx.x & 31) == 0) atomic_max_pos(&sc->eta, mx);
+    if ((threadIdx.x & 31) == 0) {
+        atomic_max_pos(&sc->eta, mx);
+        atomic_max_pos(&cl_eta[group_cl[A]], mx);
+    }
 }
 
 template <typename T>
@@ -274,6 +284,7 @@ __global__ void k_ortho_lists(int w, double tol, const int* __restrict__ oblk, c
                               const int* __restrict__ group_not, const int* __restrict__ occ0,
                               const int* __restrict__ virt0, const int* __restrict__ blk_tp,
                               const T* __restrict__ sig, const double* __restrict__ dsc, DeviceScalars* sc,
+                              const int* __restrict__ group_cl, const double* __restrict__ cl_eta,
                               int* __restrict__ pr_n, int* __restrict__ pr_lvl, uint16_t* __restrict__ pr_ij,
                               T* __restrict__ pr_cs, int* __restrict__ pr_touch) {
     __shared__ unsigned char keep[48 * 48];
@@ -284,7 +295,7 @@ __global__ void k_ortho_lists(int w, double tol, const int* __restrict__ oblk, c
     const int nA = w == 1 ? noA : 6 * group_nmol[A], nB = w == 1 ? noB : 6 * group_nmol[B];
     const bool same = A == B;
     const int nsub = max(nA, nB);
-    const double eta = sc->eta;
+    const double eta = cl_eta[group_cl[A]];   // threshold of the block's own cluster
     const bool active = !(eta < tol);
     const double cut = 1e-3 * eta;
     for (int p = threadIdx.x; p < 48 * 48; p += blockDim.x) {
@@ -538,7 +549,7 @@ __device__ __forceinline__ Side side_of(const SweepArgs& a, int g, bool virt_onl
     return s;
 }
 
-constexpr int kUnroll = 8;                 // pairs of one level in flight per thread
+constexpr int kUnroll = 1;                 // pairs of one level in flight per thread (measured best)
 constexpr int kSegUnroll = 4;              // panel segments in flight per thread
 
 template <typename T> struct Vec;
@@ -825,25 +836,30 @@ __global__ void k_compact(int cap, const int* __restrict__ in_nt, const int* __r
 template <typename T>
 static cudaError_t select_rot_t(Ctx* c) {
     const double tau = c->prm.eps;
-    const unsigned long long kmax = (unsigned long long)(c->prm.rot_cap_factor * (double)c->n_occ);
+    ClSel* cl = (ClSel*)c->d_cl_sel;
+    // per-cluster state: counts and prefixes zero, kmax = rot_cap_factor * N_occ(cluster)
+    cudaError_t e = cudaMemcpyAsync(c->d_cl_sel, c->h_cl_sel_init.data(), c->h_cl_sel_init.size() * 8,
+                                    cudaMemcpyHostToDevice, c->stream);
+    if (e != cudaSuccess) return e;
     k_rot_stats<T><<<c->n_gnb, 256, 0, c->stream>>>(c->n_gnb, c->d_gnb_row, c->d_gnb_col, c->d_group_nmol,
-                                                    c->d_group_nvt, c->d_rot_blk_tp0, (const T*)c->d_F, tau, c->d_sc);
+                                                    c->d_group_nvt, c->d_group_cl, c->d_rot_blk_tp0, (const T*)c->d_F,
+                                                    tau, c->d_sc, cl);
     const int hb = std::min(c->n_gnb, 1024);
     for (int shift = 56; shift >= 0; shift -= 8) {
-        k_rot_hist<T><<<hb, 256, 0, c->stream>>>(shift, kmax, c->n_gnb, c->d_gnb_row, c->d_gnb_col, c->d_group_nmol,
-                                                 c->d_group_nvt, c->d_rot_blk_tp0, (const T*)c->d_F, tau, c->d_sc);
-        k_rot_pick<<<1, 1, 0, c->stream>>>(shift, kmax, c->d_sc);
+        k_rot_hist<T><<<hb, 256, 0, c->stream>>>(shift, c->n_gnb, c->d_gnb_row, c->d_gnb_col, c->d_group_nmol,
+                                                 c->d_group_nvt, c->d_group_cl, c->d_rot_blk_tp0, (const T*)c->d_F,
+                                                 tau, cl, c->d_cl_hist);
+        k_rot_pick<<<(c->n_clusters + 127) / 128, 128, 0, c->stream>>>(shift, c->n_clusters, cl, c->d_cl_hist);
     }
-    k_rot_threshold<<<1, 1, 0, c->stream>>>(kmax, tau, c->d_sc);
     k_rot_lists<T><<<c->n_gnb, 128, 0, c->stream>>>(
         c->n_gnb, c->d_gnb_row, c->d_gnb_col, c->d_group_nmol, c->d_group_nvt, c->d_group_occ0_mo,
-        c->d_group_virt0_mo, c->d_rot_blk_tp0, (const T*)c->d_F, c->d_Fd, tau, c->d_sc, c->d_pr_n, c->d_pr_lvl,
-        c->d_pr_ij, (T*)c->d_pr_cs, c->d_pr_touch);
+        c->d_group_virt0_mo, c->d_group_cl, c->d_rot_blk_tp0, (const T*)c->d_F, c->d_Fd, tau, c->d_sc, cl, c->d_pr_n,
+        c->d_pr_lvl, c->d_pr_ij, (T*)c->d_pr_cs, c->d_pr_touch);
     return cudaGetLastError();
 }
 
 cudaError_t launch_select_rot(Ctx* c) {
-    c->n_launch += 19;
+    c->n_launch += 18;
     return c->prec == SSCF_FP64 ? select_rot_t<double>(c) : select_rot_t<float>(c);
 }
 
@@ -854,14 +870,17 @@ static cudaError_t ortho_prepare_t(Ctx* c, int w, double tol) {
         w, 0, t_hi, c->d_tile_group, c->d_tile_kind, c->d_tile_nmo, c->d_tile_mo0, c->d_group_ot0, c->d_group_not,
         c->d_group_vt0, c->d_self_blk, c->d_ort_blk_tp[w], (const T*)c->d_sig, c->d_scale, &c->d_sc->err);
     const int nob = (int)c->h_ocolour_blk.size();
+    cudaError_t e = cudaMemsetAsync(c->d_cl_eta, 0, (size_t)c->n_clusters * 8, c->stream);
+    if (e != cudaSuccess) return e;
     k_ortho_eta<T><<<nob, 256, 0, c->stream>>>(w, c->d_ocolour_blk, nob, c->d_gnb_row, c->d_gnb_col,
                                               c->d_group_nmol, c->d_group_not, c->d_group_occ0_mo,
                                               c->d_group_virt0_mo, c->d_ort_blk_tp[w], (const T*)c->d_sig,
-                                              c->d_scale, c->d_sc);
+                                              c->d_scale, c->d_sc, c->d_group_cl, c->d_cl_eta);
     k_ortho_lists<T><<<nob, 128, 0, c->stream>>>(w, tol, c->d_ocolour_blk, c->d_gnb_row, c->d_gnb_col,
                                                 c->d_group_nmol, c->d_group_not, c->d_group_occ0_mo,
                                                 c->d_group_virt0_mo, c->d_ort_blk_tp[w], (const T*)c->d_sig,
-                                                c->d_scale, c->d_sc, c->d_pr_n, c->d_pr_lvl, c->d_pr_ij,
+                                                c->d_scale, c->d_sc, c->d_group_cl, c->d_cl_eta, c->d_pr_n,
+                                                c->d_pr_lvl, c->d_pr_ij,
                                                 (T*)c->d_pr_cs, c->d_pr_touch);
     return cudaGetLastError();
 }

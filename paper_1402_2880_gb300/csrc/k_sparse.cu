@@ -109,27 +109,29 @@ __global__ void k_ci_sort(const int* __restrict__ ptr, int* __restrict__ row, in
 // X[r, n] (6x6) C[n, t] (6x16) over the pattern neighbours n holding t.
 // ---------------------------------------------------------------------------
 template <typename T>
-__global__ void k_xc(int tile_lo, int n_mol, int cap, int capY, const int* __restrict__ cci_ptr,
-                     const int* __restrict__ cci_row, const int* __restrict__ cci_slot,
-                     const T* __restrict__ c_val, const int* __restrict__ mp_ptr, const int* __restrict__ mp_col,
-                     const T* __restrict__ Xb, int* __restrict__ y_n, int* __restrict__ y_row,
-                     T* __restrict__ y_val, unsigned* __restrict__ err) {
+__global__ void k_xc(int tile_lo, int n_rows, int cap, int capY, const int* __restrict__ tile_row0,
+                     const int* __restrict__ cci_ptr, const int* __restrict__ cci_row,
+                     const int* __restrict__ cci_slot, const T* __restrict__ c_val, const int* __restrict__ mp_ptr,
+                     const int* __restrict__ mp_col, const T* __restrict__ Xb, int* __restrict__ y_n,
+                     int* __restrict__ y_row, T* __restrict__ y_val, unsigned* __restrict__ err) {
+    // row maps are local to the tile's cluster: row r -> r - r0, n_rows = largest cluster
     extern __shared__ int sm[];
-    int* rowpos = sm;                            // n_mol: index into the tile's column list or -1
-    unsigned* bits = (unsigned*)(sm + n_mol);    // n_mol bits
-    int* wpre = (int*)(bits + (n_mol + 31) / 32);  // prefix of popcounts per word
+    int* rowpos = sm;                             // n_rows: index into the tile's column list or -1
+    unsigned* bits = (unsigned*)(sm + n_rows);    // n_rows bits
+    int* wpre = (int*)(bits + (n_rows + 31) / 32);  // prefix of popcounts per word
     __shared__ int s_total;
     const int t = tile_lo + blockIdx.x;
+    const int r0 = tile_row0[t];
     const int lo = cci_ptr[t], nc = cci_ptr[t + 1] - lo;
-    const int nw = (n_mol + 31) / 32;
-    for (int i = threadIdx.x; i < n_mol; i += blockDim.x) rowpos[i] = -1;
+    const int nw = (n_rows + 31) / 32;
+    for (int i = threadIdx.x; i < n_rows; i += blockDim.x) rowpos[i] = -1;
     for (int i = threadIdx.x; i < nw; i += blockDim.x) bits[i] = 0u;
     __syncthreads();
-    for (int k = threadIdx.x; k < nc; k += blockDim.x) rowpos[cci_row[lo + k]] = k;
+    for (int k = threadIdx.x; k < nc; k += blockDim.x) rowpos[cci_row[lo + k] - r0] = k;
     for (int k = threadIdx.x; k < nc; k += blockDim.x) {
         int r = cci_row[lo + k];
         for (int e = mp_ptr[r]; e < mp_ptr[r + 1]; ++e) {
-            int n = mp_col[e];
+            int n = mp_col[e] - r0;
             atomicOr(&bits[n >> 5], 1u << (n & 31));
         }
     }
@@ -159,19 +161,19 @@ __global__ void k_xc(int tile_lo, int n_mol, int cap, int capY, const int* __res
         while (b) {
             int i = __ffs(b) - 1;
             b &= b - 1;
-            y_row[(size_t)t * capY + p++] = w * 32 + i;
+            y_row[(size_t)t * capY + p++] = r0 + w * 32 + i;
         }
     }
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-    const int col = lane & 15, r0 = lane >> 4;   // rows r0, r0+2, r0+4
+    const int col = lane & 15, q0 = lane >> 4;   // AO rows q0, q0+2, q0+4
     using A = typename Acc<T>::type;
     for (int k = warp; k < ny; k += nwarps) {
         const int r = y_row[(size_t)t * capY + k];
         A acc0 = 0, acc1 = 0, acc2 = 0;
         for (int e = mp_ptr[r]; e < mp_ptr[r + 1]; ++e) {
             const int n = mp_col[e];
-            const int j = rowpos[n];
+            const int j = rowpos[n - r0];
             if (j < 0) continue;
             const T* cv = c_val + ((size_t)n * cap + cci_slot[lo + j]) * kTileVals + col;
             const T* xb = Xb + (size_t)e * 36;
@@ -180,15 +182,15 @@ __global__ void k_xc(int tile_lo, int n_mol, int cap, int capY, const int* __res
             for (int q = 0; q < 6; ++q) c6[q] = (A)cv[q * kTileW];
 #pragma unroll
             for (int q = 0; q < 6; ++q) {
-                acc0 += (A)xb[(r0)*6 + q] * c6[q];
-                acc1 += (A)xb[(r0 + 2) * 6 + q] * c6[q];
-                acc2 += (A)xb[(r0 + 4) * 6 + q] * c6[q];
+                acc0 += (A)xb[(q0)*6 + q] * c6[q];
+                acc1 += (A)xb[(q0 + 2) * 6 + q] * c6[q];
+                acc2 += (A)xb[(q0 + 4) * 6 + q] * c6[q];
             }
         }
         T* yv = y_val + ((size_t)t * capY + k) * kTileVals;
-        yv[(r0)*kTileW + col] = (T)acc0;
-        yv[(r0 + 2) * kTileW + col] = (T)acc1;
-        yv[(r0 + 4) * kTileW + col] = (T)acc2;
+        yv[(q0)*kTileW + col] = (T)acc0;
+        yv[(q0 + 2) * kTileW + col] = (T)acc1;
+        yv[(q0 + 4) * kTileW + col] = (T)acc2;
     }
 }
 
@@ -211,20 +213,22 @@ template <> struct V4<double> { using type = double2; };
 
 template <typename T>
 __global__ void __launch_bounds__(kTfWarps * 32)
-k_transform(int n_mol, int cap, int capY, const int* __restrict__ tp_ptr, const int* __restrict__ tp_b,
+k_transform(int n_rows, const int* __restrict__ tile_row0, int cap, int capY, const int* __restrict__ tp_ptr,
+            const int* __restrict__ tp_b,
             const int* __restrict__ tp_out, const int* __restrict__ cci_ptr, const int* __restrict__ cci_row,
             const int* __restrict__ cci_slot, const T* __restrict__ c_val, const int* __restrict__ y_n,
             const int* __restrict__ y_row, const T* __restrict__ y_val, T* __restrict__ out) {
     extern __shared__ __align__(16) unsigned char sraw[];
     T* stage = (T*)sraw;                                        // [warps][kStage][2][96]
-    int* slot_of = (int*)(stage + (size_t)kTfWarps * kStage * 2 * kTileVals);   // n_mol
+    int* slot_of = (int*)(stage + (size_t)kTfWarps * kStage * 2 * kTileVals);   // n_rows (cluster-local)
     const int a = blockIdx.x;
     const int p0 = tp_ptr[a], p1 = tp_ptr[a + 1];
     if (p0 == p1) return;
+    const int r0 = tile_row0[a];
     const int lo = cci_ptr[a], nc = cci_ptr[a + 1] - lo;
-    for (int i = threadIdx.x; i < n_mol; i += blockDim.x) slot_of[i] = -1;
+    for (int i = threadIdx.x; i < n_rows; i += blockDim.x) slot_of[i] = -1;
     __syncthreads();
-    for (int k = threadIdx.x; k < nc; k += blockDim.x) slot_of[cci_row[lo + k]] = cci_slot[lo + k];
+    for (int k = threadIdx.x; k < nc; k += blockDim.x) slot_of[cci_row[lo + k] - r0] = cci_slot[lo + k];
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     T* buf = stage + (size_t)warp * kStage * 2 * kTileVals;
@@ -246,7 +250,7 @@ k_transform(int n_mol, int cap, int capY, const int* __restrict__ tp_ptr, const 
         }
         for (int k0 = 0; k0 < nb; k0 += 32) {
             const int k = k0 + lane;
-            const int s = k < nb ? slot_of[yr[k]] : -1;
+            const int s = k < nb ? slot_of[yr[k] - r0] : -1;
             unsigned m = __ballot_sync(0xffffffffu, s >= 0);
             while (m) {
                 // stage up to kStage matched row blocks
@@ -333,19 +337,21 @@ constexpr int kDensWarps = 8;
 constexpr int kDensFlush = 8;   // tiles per lane between FP64 flushes
 template <typename T>
 __global__ void __launch_bounds__(kDensWarps * 32)
-k_density(int n_occ_tiles, int cap, const int* __restrict__ c_nt, const int* __restrict__ c_tile,
-          const T* __restrict__ c_val, const int* __restrict__ mp_ptr, const int* __restrict__ mp_col,
-          const double* __restrict__ H0b, const double* __restrict__ Sb, double* __restrict__ q,
-          double* __restrict__ e_mol) {
-    extern __shared__ int smap[];   // n_occ_tiles: slot of tile in row m or -1
+k_density(int n_occ_tiles, int map_n, const int* __restrict__ mol_ot0, int cap, const int* __restrict__ c_nt,
+          const int* __restrict__ c_tile, const T* __restrict__ c_val, const int* __restrict__ mp_ptr,
+          const int* __restrict__ mp_col, const double* __restrict__ H0b, const double* __restrict__ Sb,
+          double* __restrict__ q, double* __restrict__ e_mol) {
+    // slot of every occupied tile of m's cluster in row m, or -1 (map_n = largest cluster)
+    extern __shared__ int smap[];
     __shared__ double part[kDensWarps][4];
     const int m = blockIdx.x;
-    for (int i = threadIdx.x; i < n_occ_tiles; i += blockDim.x) smap[i] = -1;
+    const int t0 = mol_ot0[m];
+    for (int i = threadIdx.x; i < map_n; i += blockDim.x) smap[i] = -1;
     __syncthreads();
     const int ntm = c_nt[m];
     for (int s = threadIdx.x; s < ntm; s += blockDim.x) {
         int t = c_tile[(size_t)m * cap + s];
-        if (t < n_occ_tiles) smap[t] = s;
+        if (t < n_occ_tiles) smap[t - t0] = s;
     }
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -368,7 +374,7 @@ k_density(int n_occ_tiles, int cap, const int* __restrict__ c_nt, const int* __r
         for (int s = half; s < ntn; s += 2) {
             const int t = c_tile[(size_t)n * cap + s];
             if (t >= n_occ_tiles) break;   // tiles are sorted: occupied tiles first
-            const int sm_ = smap[t];
+            const int sm_ = smap[t - t0];
             if (sm_ < 0) continue;
             const T* cm = c_val + ((size_t)m * cap + sm_) * kTileVals + col;
             const T* cn = c_val + ((size_t)n * cap + s) * kTileVals + col;
@@ -480,15 +486,16 @@ cudaError_t launch_xc(Ctx* c, bool use_h, int tile_lo, int tile_hi) {
     const int b = c->cur;
     const int n = tile_hi - tile_lo;
     if (n <= 0) return cudaSuccess;
-    const size_t smem = (size_t)c->n_mol * 4 + (size_t)((c->n_mol + 31) / 32) * 8 + 64;
+    const int nr = c->max_cl_mol;
+    const size_t smem = (size_t)nr * 4 + (size_t)((nr + 31) / 32) * 8 + 64;
     if (smem > 200 * 1024) return cudaErrorInvalidValue;
     if (c->prec == SSCF_FP64)
-        k_xc<double><<<n, 256, smem, c->stream>>>(tile_lo, c->n_mol, c->cap, c->capY, c->d_cci_ptr, c->d_cci_row,
+        k_xc<double><<<n, 256, smem, c->stream>>>(tile_lo, nr, c->cap, c->capY, c->d_tile_row0, c->d_cci_ptr, c->d_cci_row,
                                                   c->d_cci_slot, (const double*)c->d_c_val[b], c->d_mp_ptr,
                                                   c->d_mp_col, (const double*)(use_h ? c->d_Hb : c->d_Sbt),
                                                   c->d_y_n, c->d_y_row, (double*)c->d_y_val, &c->d_sc->err);
     else
-        k_xc<float><<<n, 256, smem, c->stream>>>(tile_lo, c->n_mol, c->cap, c->capY, c->d_cci_ptr, c->d_cci_row,
+        k_xc<float><<<n, 256, smem, c->stream>>>(tile_lo, nr, c->cap, c->capY, c->d_tile_row0, c->d_cci_ptr, c->d_cci_row,
                                                  c->d_cci_slot, (const float*)c->d_c_val[b], c->d_mp_ptr,
                                                  c->d_mp_col, (const float*)(use_h ? c->d_Hb : c->d_Sbt),
                                                  c->d_y_n, c->d_y_row, (float*)c->d_y_val, &c->d_sc->err);
@@ -497,8 +504,8 @@ cudaError_t launch_xc(Ctx* c, bool use_h, int tile_lo, int tile_hi) {
 
 template <typename T>
 static cudaError_t transform_t(Ctx* c, const int* ptr, const int* bl, const int* outl, void* out) {
-    const size_t smem = (size_t)kTfWarps * kStage * 2 * kTileVals * sizeof(T) + (size_t)c->n_mol * 4;
-    k_transform<T><<<c->n_tiles, kTfWarps * 32, smem, c->stream>>>(c->n_mol, c->cap, c->capY, ptr, bl, outl, c->d_cci_ptr,
+    const size_t smem = (size_t)kTfWarps * kStage * 2 * kTileVals * sizeof(T) + (size_t)c->max_cl_mol * 4;
+    k_transform<T><<<c->n_tiles, kTfWarps * 32, smem, c->stream>>>(c->max_cl_mol, c->d_tile_row0, c->cap, c->capY, ptr, bl, outl, c->d_cci_ptr,
                                                          c->d_cci_row, c->d_cci_slot, (const T*)c->d_c_val[c->cur],
                                                          c->d_y_n, c->d_y_row, (const T*)c->d_y_val, (T*)out);
     return cudaGetLastError();
@@ -508,7 +515,7 @@ cudaError_t launch_transform_rot(Ctx* c) {
     c->n_launch += 3;
     cudaError_t e = ensure_attrs();
     if (e != cudaSuccess) return e;
-    if ((size_t)kTfWarps * kStage * 2 * kTileVals * 8 + (size_t)c->n_mol * 4 > 200 * 1024) return cudaErrorInvalidValue;
+    if ((size_t)kTfWarps * kStage * 2 * kTileVals * 8 + (size_t)c->max_cl_mol * 4 > 200 * 1024) return cudaErrorInvalidValue;
     if (c->prec == SSCF_FP64) {
         e = transform_t<double>(c, c->d_rot_tp_ptr, c->d_rot_tp_b, c->d_rot_tp_out, c->d_F);
         if (e == cudaSuccess)
@@ -541,15 +548,15 @@ cudaError_t launch_density(Ctx* c) {
     c->n_launch += 1;
     cudaError_t e = ensure_attrs();
     if (e != cudaSuccess) return e;
-    const size_t smem = (size_t)c->n_occ_tiles * 4;
+    const size_t smem = (size_t)c->max_cl_otiles * 4;
     if (smem > 160 * 1024) return cudaErrorInvalidValue;
     const int b = c->cur;
     if (c->prec == SSCF_FP64)
-        k_density<double><<<c->n_mol, kDensWarps * 32, smem, c->stream>>>(c->n_occ_tiles, c->cap, c->d_c_nt[b], c->d_c_tile[b],
+        k_density<double><<<c->n_mol, kDensWarps * 32, smem, c->stream>>>(c->n_occ_tiles, c->max_cl_otiles, c->d_mol_ot0, c->cap, c->d_c_nt[b], c->d_c_tile[b],
                                                               (const double*)c->d_c_val[b], c->d_mp_ptr,
                                                               c->d_mp_col, c->d_H0b, c->d_Sb, c->d_q, c->d_e_mol);
     else
-        k_density<float><<<c->n_mol, kDensWarps * 32, smem, c->stream>>>(c->n_occ_tiles, c->cap, c->d_c_nt[b], c->d_c_tile[b],
+        k_density<float><<<c->n_mol, kDensWarps * 32, smem, c->stream>>>(c->n_occ_tiles, c->max_cl_otiles, c->d_mol_ot0, c->cap, c->d_c_nt[b], c->d_c_tile[b],
                                                              (const float*)c->d_c_val[b], c->d_mp_ptr, c->d_mp_col,
                                                              c->d_H0b, c->d_Sb, c->d_q, c->d_e_mol);
     return cudaGetLastError();

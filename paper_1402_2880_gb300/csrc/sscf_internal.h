@@ -74,6 +74,10 @@ struct Ctx {
     int n_atoms = 0, n_mol = 0, n_ao = 0, n_occ = 0, n_mo = 0;
     int n_groups = 0, n_tiles = 0, n_occ_tiles = 0, n_colours = 0;
     int n_mp = 0;        // molecule-pair blocks, including (m, m)
+    int n_clusters = 1;
+    int max_cl_mol = 0;       // molecules of the largest cluster
+    int max_cl_otiles = 0;    // occupied tiles of the largest cluster
+    int max_cl_tiles = 0;     // tiles of the largest cluster
     int n_gnb = 0;       // group-graph entries (directed, including (A, A))
     int cap = 0;         // tiles per row block of C
     int capY = 0;        // row blocks per tile of Y
@@ -88,7 +92,8 @@ struct Ctx {
     // host copies of the structure
     std::vector<int> h_species;
     std::vector<double> h_xyz;
-    std::vector<int> h_mol_group, h_mol_local;
+    std::vector<int> h_mol_group, h_mol_local, h_mol_cluster;
+    std::vector<int> h_cl_mol0, h_cl_nmol;    // molecule range of every cluster
     std::vector<int> h_mp_ptr, h_mp_col;
     std::vector<int> h_group_nmol, h_group_occ0, h_group_virt0;
     std::vector<int> h_group_ot0, h_group_not, h_group_vt0, h_group_nvt;
@@ -126,6 +131,21 @@ struct Ctx {
     int* d_self_blk = nullptr;        // group-graph entry of (g, g)
     std::vector<int> h_self_blk;
     int* d_tile_group = nullptr;
+    int* d_tile_row0 = nullptr;       // first molecule of the tile's cluster
+    int* d_mol_cluster = nullptr;
+    int* d_mol_row0 = nullptr;        // first molecule of the molecule's cluster
+    int* d_mol_ot0 = nullptr;         // first occupied tile of the molecule's cluster
+    int* d_atom_lo = nullptr;         // atom range of the atom's cluster
+    int* d_atom_hi = nullptr;
+    int* d_cl_mol0 = nullptr;
+    int* d_cl_nmol = nullptr;
+    int* d_group_cl = nullptr;        // cluster of every group
+    void* d_cl_sel = nullptr;         // per-cluster top-k state (6 words each)
+    std::vector<unsigned long long> h_cl_sel_init;
+    unsigned long long* d_cl_hist = nullptr;   // per-cluster radix histograms (256 each)
+    double* d_cl_eta = nullptr;       // per-cluster largest normalised overlap
+    double* d_cl_E = nullptr;         // per-cluster energy of the last charge update
+    double* d_cl_dq = nullptr;        // per-cluster max |q - q_prev|
     int* d_tile_kind = nullptr;
     int* d_tile_loc0 = nullptr;
     int* d_tile_nmo = nullptr;

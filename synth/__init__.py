@@ -9,4 +9,5 @@ from .water import (  # noqa: F401
     default_params,
     lattice_water,
     cluster_sizes,
+    concat_clusters,
 )

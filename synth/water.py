@@ -45,6 +45,7 @@ class WaterSystem:
     group_of_mol: np.ndarray   # (n_mol,) int32 MO-group index
     n_groups: int
     lattice_edge: int
+    cluster_of_mol: np.ndarray | None = None   # batch of independent clusters, else None
 
     @property
     def n_atoms(self) -> int:
@@ -155,3 +156,26 @@ def lattice_water(n_mol: int, seed: int = 0, spacing_A: float = 3.1,
 def cluster_sizes(n_clusters: int = 256, lo: int = 200, hi: int = 3000, seed: int = 7) -> np.ndarray:
     """Molecule counts of the batched workload: uniform integers in [lo, hi]."""
     return np.random.default_rng(seed).integers(lo, hi + 1, n_clusters)
+
+
+def concat_clusters(systems) -> WaterSystem:
+    """Independent clusters in one system: molecules, atoms and groups of
+    cluster k follow those of cluster k-1, ``cluster_of_mol`` marks them.
+    Coordinates are kept as drawn (clusters may overlap in space; nothing
+    couples two clusters)."""
+    species, xyz, mol_of_atom, site, groups, clusters = [], [], [], [], [], []
+    m0 = g0 = 0
+    for k, s in enumerate(systems):
+        species.append(s.species)
+        xyz.append(s.xyz)
+        mol_of_atom.append(s.mol_of_atom + m0)
+        site.append(s.site)
+        groups.append(s.group_of_mol + g0)
+        clusters.append(np.full(s.n_mol, k, dtype=np.int32))
+        m0 += s.n_mol
+        g0 += s.n_groups
+    return WaterSystem(n_mol=m0, species=np.concatenate(species), xyz=np.concatenate(xyz),
+                       mol_of_atom=np.concatenate(mol_of_atom).astype(np.int32), site=np.concatenate(site),
+                       group_of_mol=np.concatenate(groups).astype(np.int32), n_groups=g0,
+                       lattice_edge=max(s.lattice_edge for s in systems),
+                       cluster_of_mol=np.concatenate(clusters))
