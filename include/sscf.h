@@ -166,6 +166,14 @@ int sscf_reset_charges(sscf_ctx* ctx, double* E_out);
  * (ortho_every = 1), density and mixing. */
 int sscf_step(sscf_ctx* ctx, sscf_step_info* info);
 
+/* CUDA graphs: when enabled, sscf_step captures its device work (all kernel
+ * launches of one SCC iteration) into a graph at the first call and replays
+ * it afterwards: one launch per iteration. The graph is rebuilt when eps
+ * changes or the C buffers swapped parity (sscf_set_C_dense, sscf_guess).
+ * Needs a non-NULL stream (SSCF_ERR_INVALID_ARG otherwise); per-launcher
+ * profiling does not see replayed launches. */
+int sscf_enable_graph(sscf_ctx* ctx, int enable);
+
 /* Loose stage (eps 1e-3, dq 1e-1), full orthonormalisation, user stage until
  * dq_max <= dq_tol and |dE| <= e_tol in every cluster, final occupied orthonormalisation to
  * eps / 100 and final charges and energy. Returns NOT_CONVERGED with the

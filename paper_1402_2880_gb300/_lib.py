@@ -33,6 +33,7 @@ EXPORTED = [
     "sscf_set_C_dense", "sscf_get_H_dense", "sscf_get_F_dense", "sscf_get_charges",
     "sscf_set_charges", "sscf_get_colouring", "sscf_get_pairs", "sscf_profile", "sscf_profile_read",
     "sscf_select_pairs_noalloc", "sscf_gradients", "sscf_get_cluster_results",
+    "sscf_enable_graph",
 ]
 
 
@@ -113,6 +114,7 @@ def load() -> ctypes.CDLL:
         "sscf_select_pairs_noalloc": (c_int, [c_vp, c_i64, c_double, c_i64, c_vp, P(c_i64), c_vp]),
         "sscf_gradients": (c_int, [c_vp, P(c_double), P(c_double)]),
         "sscf_get_cluster_results": (c_int, [c_vp, P(c_double), P(c_double), P(c_int)]),
+        "sscf_enable_graph": (c_int, [c_vp, c_int]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -243,6 +245,9 @@ class Context:
         E = ctypes.c_double()
         _check(self.lib.sscf_reset_charges(self.h, ctypes.byref(E)), "sscf_reset_charges")
         return E.value
+
+    def enable_graph(self, enable: bool = True):
+        _check(self.lib.sscf_enable_graph(self.h, 1 if enable else 0), "sscf_enable_graph")
 
     def step(self) -> dict:
         info = StepInfo()

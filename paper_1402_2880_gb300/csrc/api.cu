@@ -409,6 +409,14 @@ int prof_collect(Ctx& c) {
         CK(call);                 \
     } while (0)
 
+void drop_graph(Ctx& c) {
+    if (c.graph_exec) cudaGraphExecDestroy(c.graph_exec);
+    if (c.graph) cudaGraphDestroy(c.graph);
+    c.graph_exec = nullptr;
+    c.graph = nullptr;
+    c.graph_valid = false;
+}
+
 int sync_scalars(Ctx& c) {
     CK(cudaMemcpyAsync(c.h_sc, c.d_sc, sizeof(DeviceScalars), cudaMemcpyDeviceToHost, c.stream));
     CK(cudaStreamSynchronize(c.stream));
@@ -622,6 +630,7 @@ int sscf_create(const sscf_system* sys, const sscf_params* prm, void* cuda_strea
         for (int cl = 0; cl < c.n_clusters; ++cl)
             c.h_cl_sel_init[(size_t)cl * 6 + 5] =
                 (unsigned long long)(c.prm.rot_cap_factor * (double)(4 * c.h_cl_nmol[cl]));
+        UP(c.d_cl_sel_init, c.h_cl_sel_init);
         UP(c.d_tile_row0, tile_row0);
         UP(c.d_mol_row0, mol_row0);
         UP(c.d_mol_ot0, mol_ot0);
@@ -739,6 +748,7 @@ void sscf_destroy(sscf_ctx* h) {
     if (!h) return;
     cudaStreamSynchronize(h->c.stream);
     prof_collect(h->c);
+    drop_graph(h->c);
     dev_free_all(&h->c);
     if (h->c.h_sc) cudaFreeHost(h->c.h_sc);
     delete h;
@@ -746,6 +756,7 @@ void sscf_destroy(sscf_ctx* h) {
 
 int sscf_set_thresholds(sscf_ctx* h, double eps, double dq_tol, double e_tol) {
     if (!h || !(eps >= 0) || !(dq_tol >= 0) || !(e_tol >= 0)) return SSCF_ERR_INVALID_ARG;
+    if (h->c.prm.eps != eps) drop_graph(h->c);
     h->c.prm.eps = eps;
     h->c.prm.dq_tol = dq_tol;
     h->c.prm.e_tol = e_tol;
@@ -885,17 +896,66 @@ int sscf_reset_charges(sscf_ctx* h, double* E_out) {
     return SSCF_OK;
 }
 
-int sscf_step(sscf_ctx* h, sscf_step_info* info) {
-    if (!h) return SSCF_ERR_INVALID_ARG;
-    Ctx& c = h->c;
-    if (!c.have_guess) return SSCF_ERR_STATE;
-    const long long l0 = c.n_launch;
+// Device part of one SCC iteration (no host synchronisation: capturable).
+static int step_device(Ctx& c) {
     CK(cudaMemsetAsync(c.d_sc, 0, offsetof(DeviceScalars, hist), c.stream));
     PK("build_fock", launch_build_h(&c, c.prm.eps));
     CKS(rotate_sweep_async(c));
     if (c.prm.ortho_every) CKS(ortho_pass_async(c, SSCF_ORTHO_OCC, c.prm.eps / 100.0));
     CKS(density_async(c, true));
     CK(launch_count_tiles(&c, c.d_sc->tiles));
+    return SSCF_OK;
+}
+
+// Captures step_device into a CUDA graph (once per threshold set and buffer
+// parity) and replays it: one launch per SCC iteration.
+static int step_graph(Ctx& c) {
+    if (c.graph_valid && c.graph_cur != c.cur) drop_graph(c);
+    if (!c.graph_valid) {
+        const bool prof = c.prof;
+        c.prof = false;
+        const long long l0 = c.n_launch;
+        const int cur0 = c.cur;
+        CK(cudaStreamBeginCapture(c.stream, cudaStreamCaptureModeThreadLocal));
+        const int st = step_device(c);
+        cudaGraph_t g = nullptr;
+        const cudaError_t ce = cudaStreamEndCapture(c.stream, &g);
+        c.prof = prof;
+        if (st != SSCF_OK || ce != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            cudaGetLastError();
+            return st != SSCF_OK ? st : SSCF_ERR_CUDA;
+        }
+        c.graph = g;
+        CK(cudaGraphInstantiate(&c.graph_exec, c.graph, 0));
+        c.graph_launches = c.n_launch - l0;
+        c.n_launch = l0;
+        c.graph_cur = cur0;
+        c.graph_valid = true;
+    }
+    CK(cudaGraphLaunch(c.graph_exec, c.stream));
+    c.n_launch += c.graph_launches;
+    return SSCF_OK;
+}
+
+int sscf_enable_graph(sscf_ctx* h, int enable) {
+    if (!h) return SSCF_ERR_INVALID_ARG;
+    Ctx& c = h->c;
+    if (enable && c.stream == nullptr) return SSCF_ERR_INVALID_ARG;   // the legacy stream cannot be captured
+    drop_graph(c);
+    c.use_graph = enable != 0;
+    return SSCF_OK;
+}
+
+int sscf_step(sscf_ctx* h, sscf_step_info* info) {
+    if (!h) return SSCF_ERR_INVALID_ARG;
+    Ctx& c = h->c;
+    if (!c.have_guess) return SSCF_ERR_STATE;
+    const long long l0 = c.n_launch;
+    if (c.use_graph)
+        CKS(step_graph(c));
+    else
+        CKS(step_device(c));
     CKS(sync_scalars(c));
     c.iteration++;
     if (info) {
@@ -990,6 +1050,7 @@ int sscf_run(sscf_ctx* h, sscf_step_info* info) {
     sscf_step_info last{};
     bool converged = false;
     for (int s = 0; s < 2; ++s) {
+        if (c.prm.eps != stages[s].eps) drop_graph(c);
         c.prm.eps = stages[s].eps;
         CKS(sscf_orthonormalise(h, SSCF_ORTHO_ALL, 200, nullptr, nullptr));
         if (s == 0) CKS(sscf_reset_charges(h, nullptr));
@@ -1011,6 +1072,7 @@ int sscf_run(sscf_ctx* h, sscf_step_info* info) {
             }
         }
     }
+    if (c.prm.eps != eps_u) drop_graph(c);
     c.prm.eps = eps_u;
     c.prm.dq_tol = dq_u;
     c.prm.e_tol = e_u;

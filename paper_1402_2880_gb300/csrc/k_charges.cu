@@ -76,6 +76,8 @@ __global__ void k_finish(int n_atoms, int n_mol, int mix, double beta, const dou
         sc->dq_max = s_max[0];
         if (!isfinite(sc->energy)) atomicOr(&sc->err, kErrNonFinite);
     }
+    // after a capacity error the step's MOs are the previous ones: keep the charges
+    if (sc->err & (kErrCapacity | kErrSortSize)) return;
     for (int a = threadIdx.x; a < n_atoms; a += blockDim.x) {
         q_prev[a] = q[a];
         if (mix) {

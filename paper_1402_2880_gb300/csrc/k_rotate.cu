@@ -787,12 +787,15 @@ __global__ void __launch_bounds__(apply_threads<T>()) k_apply_colour(SweepArgs a
 }
 
 // drop tiles whose 6x16 values are all zero; in -> out
+// (skipped entirely when an earlier kernel of the pass set the error word:
+// `out` is then the pass's untouched input and stays as it was)
 template <typename T>
 __global__ void k_compact(int cap, const int* __restrict__ in_nt, const int* __restrict__ in_tile,
                           const T* __restrict__ in_val, int* __restrict__ out_nt, int* __restrict__ out_tile,
-                          T* __restrict__ out_val) {
+                          T* __restrict__ out_val, const unsigned* __restrict__ err) {
     __shared__ int wcnt[32];
     __shared__ int s_base;
+    if (*err & (kErrCapacity | kErrSortSize)) return;
     const int r = blockIdx.x;
     const int n = in_nt[r];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
@@ -838,8 +841,8 @@ static cudaError_t select_rot_t(Ctx* c) {
     const double tau = c->prm.eps;
     ClSel* cl = (ClSel*)c->d_cl_sel;
     // per-cluster state: counts and prefixes zero, kmax = rot_cap_factor * N_occ(cluster)
-    cudaError_t e = cudaMemcpyAsync(c->d_cl_sel, c->h_cl_sel_init.data(), c->h_cl_sel_init.size() * 8,
-                                    cudaMemcpyHostToDevice, c->stream);
+    cudaError_t e = cudaMemcpyAsync(c->d_cl_sel, c->d_cl_sel_init, c->h_cl_sel_init.size() * 8,
+                                    cudaMemcpyDeviceToDevice, c->stream);
     if (e != cudaSuccess) return e;
     k_rot_stats<T><<<c->n_gnb, 256, 0, c->stream>>>(c->n_gnb, c->d_gnb_row, c->d_gnb_col, c->d_group_nmol,
                                                     c->d_group_nvt, c->d_group_cl, c->d_rot_blk_tp0, (const T*)c->d_F,
@@ -994,11 +997,11 @@ cudaError_t launch_compact(Ctx* c) {
     if (c->prec == SSCF_FP64)
         k_compact<double><<<c->n_mol, 256, 0, c->stream>>>(c->cap, c->d_c_nt[in], c->d_c_tile[in],
                                                            (const double*)c->d_c_val[in], c->d_c_nt[out],
-                                                           c->d_c_tile[out], (double*)c->d_c_val[out]);
+                                                           c->d_c_tile[out], (double*)c->d_c_val[out], &c->d_sc->err);
     else
         k_compact<float><<<c->n_mol, 256, 0, c->stream>>>(c->cap, c->d_c_nt[in], c->d_c_tile[in],
                                                           (const float*)c->d_c_val[in], c->d_c_nt[out],
-                                                          c->d_c_tile[out], (float*)c->d_c_val[out]);
+                                                          c->d_c_tile[out], (float*)c->d_c_val[out], &c->d_sc->err);
     c->cur = out;
     return cudaGetLastError();
 }

@@ -142,6 +142,7 @@ struct Ctx {
     int* d_group_cl = nullptr;        // cluster of every group
     void* d_cl_sel = nullptr;         // per-cluster top-k state (6 words each)
     std::vector<unsigned long long> h_cl_sel_init;
+    unsigned long long* d_cl_sel_init = nullptr;   // initial per-cluster top-k state (device copy)
     unsigned long long* d_cl_hist = nullptr;   // per-cluster radix histograms (256 each)
     double* d_cl_eta = nullptr;       // per-cluster largest normalised overlap
     double* d_cl_E = nullptr;         // per-cluster energy of the last charge update
@@ -219,6 +220,14 @@ struct Ctx {
     DeviceScalars* h_sc = nullptr;   // pinned mirror
 
     std::vector<void*> allocations;
+
+    // CUDA graph of one SCC step (sscf_enable_graph)
+    bool use_graph = false;
+    bool graph_valid = false;
+    int graph_cur = 0;
+    long long graph_launches = 0;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t graph_exec = nullptr;
 
     // per-launcher CUDA-event timing (off by default)
     bool prof = false;
