@@ -213,6 +213,19 @@ int sscf_profile_read(sscf_ctx* ctx, int max_entries, char* names, double* ms, i
 /* Dense copies for small systems: C is n_ao x n_mo, row-major (C[mu*n_mo+i]). */
 int sscf_get_C_dense(sscf_ctx* ctx, double* C);
 int sscf_set_C_dense(sscf_ctx* ctx, const double* C);
+/* Rows of C for large systems: the AO rows `rows` (n of them), dense over
+ * all MOs, into out (host, n x n_mo, row-major). */
+int sscf_get_C_rows(sscf_ctx* ctx, int n, const int* rows, double* out);
+/* Columns of C for large systems: the MOs `cols` (n of them), dense over all
+ * AOs, into out (host, n_ao x n, row-major). */
+int sscf_get_C_cols(sscf_ctx* ctx, int n, const int* cols, double* out);
+/* Entries F_ov(i, j) of the last transform for occupied i and virtual j
+ * (global MO indices), 0 outside the kept blocks. */
+int sscf_get_F_entries(sscf_ctx* ctx, int n, const int* i_mo, const int* j_mo, double* out);
+/* Molecule-pair blocks: pairs (m, n) into mn (2 * n_mp) and the 6x6 blocks
+ * (row-major) of the current H, of H0 and of S into n_mp * 36 doubles each.
+ * Any array may be NULL; n_mp_out receives the number of blocks. */
+int sscf_get_blocks(sscf_ctx* ctx, int* mn, double* H, double* H0, double* S, int64_t* n_mp_out);
 /* Dense n_ao x n_ao copies of the current H, of H0 and of S. */
 int sscf_get_H_dense(sscf_ctx* ctx, double* H, double* H0, double* S);
 /* Dense F_ov (n_occ x (n_mo - n_occ), zero off the kept blocks) and diag(F)

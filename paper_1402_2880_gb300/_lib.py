@@ -33,7 +33,8 @@ EXPORTED = [
     "sscf_set_C_dense", "sscf_get_H_dense", "sscf_get_F_dense", "sscf_get_charges",
     "sscf_set_charges", "sscf_get_colouring", "sscf_get_pairs", "sscf_profile", "sscf_profile_read",
     "sscf_select_pairs_noalloc", "sscf_gradients", "sscf_get_cluster_results",
-    "sscf_enable_graph",
+    "sscf_enable_graph", "sscf_get_C_rows", "sscf_get_blocks",
+    "sscf_get_C_cols", "sscf_get_F_entries",
 ]
 
 
@@ -115,6 +116,10 @@ def load() -> ctypes.CDLL:
         "sscf_gradients": (c_int, [c_vp, P(c_double), P(c_double)]),
         "sscf_get_cluster_results": (c_int, [c_vp, P(c_double), P(c_double), P(c_int)]),
         "sscf_enable_graph": (c_int, [c_vp, c_int]),
+        "sscf_get_C_rows": (c_int, [c_vp, c_int, P(c_int), P(c_double)]),
+        "sscf_get_C_cols": (c_int, [c_vp, c_int, P(c_int), P(c_double)]),
+        "sscf_get_F_entries": (c_int, [c_vp, c_int, P(c_int), P(c_int), P(c_double)]),
+        "sscf_get_blocks": (c_int, [c_vp, P(c_int), P(c_double), P(c_double), P(c_double), P(c_i64)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -280,6 +285,38 @@ class Context:
         C = np.ascontiguousarray(C, dtype=np.float64)
         assert C.shape == (self.n_ao, self.n_mo)
         _check(self.lib.sscf_set_C_dense(self.h, _ptr(C)), "sscf_set_C_dense")
+
+    def get_C_rows(self, rows) -> np.ndarray:
+        rows = np.ascontiguousarray(rows, dtype=np.int32)
+        out = np.empty((rows.size, self.n_mo))
+        _check(self.lib.sscf_get_C_rows(self.h, int(rows.size), _ptr(rows, ctypes.c_int), _ptr(out)),
+               "sscf_get_C_rows")
+        return out
+
+    def get_C_cols(self, cols) -> np.ndarray:
+        cols = np.ascontiguousarray(cols, dtype=np.int32)
+        out = np.empty((self.n_ao, cols.size))
+        _check(self.lib.sscf_get_C_cols(self.h, int(cols.size), _ptr(cols, ctypes.c_int), _ptr(out)),
+               "sscf_get_C_cols")
+        return out
+
+    def get_F_entries(self, i, j) -> np.ndarray:
+        i = np.ascontiguousarray(i, dtype=np.int32)
+        j = np.ascontiguousarray(j, dtype=np.int32)
+        out = np.empty(i.size)
+        _check(self.lib.sscf_get_F_entries(self.h, int(i.size), _ptr(i, ctypes.c_int), _ptr(j, ctypes.c_int),
+                                           _ptr(out)), "sscf_get_F_entries")
+        return out
+
+    def get_blocks(self):
+        """(pairs (n_mp, 2), H, H0, S as (n_mp, 6, 6)) on the molecule-pair pattern."""
+        n = ctypes.c_int64()
+        _check(self.lib.sscf_get_blocks(self.h, None, None, None, None, ctypes.byref(n)), "sscf_get_blocks")
+        mn = np.empty((n.value, 2), dtype=np.int32)
+        H, H0, S = (np.empty((n.value, 6, 6)) for _ in range(3))
+        _check(self.lib.sscf_get_blocks(self.h, _ptr(mn, ctypes.c_int), _ptr(H), _ptr(H0), _ptr(S), None),
+               "sscf_get_blocks")
+        return mn, H, H0, S
 
     def get_H(self):
         H, H0, S = (np.empty((self.n_ao, self.n_ao)) for _ in range(3))

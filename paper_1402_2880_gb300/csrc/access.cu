@@ -105,6 +105,139 @@ int sscf_set_C_dense(sscf_ctx* h, const double* C) {
     return SSCF_OK;
 }
 
+// Rows (AO indices) of C, dense over all MOs: out is n x n_mo, row-major.
+int sscf_get_C_rows(sscf_ctx* h, int n, const int* rows, double* out) {
+    if (!h || n < 0 || (n > 0 && (!rows || !out))) return SSCF_ERR_INVALID_ARG;
+    Ctx& c = h->c;
+    const int b = c.cur;
+    CKA(cudaStreamSynchronize(c.stream));
+    std::memset(out, 0, sizeof(double) * (size_t)n * c.n_mo);
+    std::vector<int> tiles(c.cap);
+    std::vector<unsigned char> raw((size_t)c.cap * kTileVals * c.tsize);
+    for (int i = 0; i < n; ++i) {
+        const int mu = rows[i];
+        if (mu < 0 || mu >= c.n_ao) return SSCF_ERR_INVALID_ARG;
+        const int r = mu / 6, k = mu % 6;
+        int nt = 0;
+        CKA(cudaMemcpy(&nt, c.d_c_nt[b] + r, 4, cudaMemcpyDeviceToHost));
+        if (nt < 0 || nt > c.cap) return SSCF_ERR_STATE;
+        CKA(cudaMemcpy(tiles.data(), c.d_c_tile[b] + (size_t)r * c.cap, (size_t)nt * 4, cudaMemcpyDeviceToHost));
+        CKA(cudaMemcpy(raw.data(), (const unsigned char*)c.d_c_val[b] + (size_t)r * c.cap * kTileVals * c.tsize,
+                       (size_t)nt * kTileVals * c.tsize, cudaMemcpyDeviceToHost));
+        for (int s = 0; s < nt; ++s) {
+            const int t = tiles[s];
+            for (int col = 0; col < c.h_tile_nmo[t]; ++col) {
+                const size_t e = (size_t)s * kTileVals + k * 16 + col;
+                const double v = c.prec == SSCF_FP64 ? ((const double*)raw.data())[e] : (double)((const float*)raw.data())[e];
+                out[(size_t)i * c.n_mo + c.h_tile_mo0[t] + col] = v;
+            }
+        }
+    }
+    return SSCF_OK;
+}
+
+// Columns (MO indices) of C, dense over all AOs: out is n_ao x n, row-major.
+// Each stored tile a column needs is copied once per row block.
+int sscf_get_C_cols(sscf_ctx* h, int n, const int* cols, double* out) {
+    if (!h || n < 0 || (n > 0 && (!cols || !out))) return SSCF_ERR_INVALID_ARG;
+    Ctx& c = h->c;
+    const int b = c.cur;
+    std::vector<int> mo_tile(c.n_mo);
+    for (int t = 0; t < c.n_tiles; ++t)
+        for (int k = 0; k < c.h_tile_nmo[t]; ++k) mo_tile[c.h_tile_mo0[t] + k] = t;
+    std::vector<int> want;   // distinct tiles, sorted
+    for (int i = 0; i < n; ++i) {
+        if (cols[i] < 0 || cols[i] >= c.n_mo) return SSCF_ERR_INVALID_ARG;
+        want.push_back(mo_tile[cols[i]]);
+    }
+    std::sort(want.begin(), want.end());
+    want.erase(std::unique(want.begin(), want.end()), want.end());
+    std::vector<int> nt(c.n_mol), tiles((size_t)c.n_mol * c.cap);
+    CKA(cudaStreamSynchronize(c.stream));
+    CKA(cudaMemcpy(nt.data(), c.d_c_nt[b], nt.size() * 4, cudaMemcpyDeviceToHost));
+    CKA(cudaMemcpy(tiles.data(), c.d_c_tile[b], tiles.size() * 4, cudaMemcpyDeviceToHost));
+    std::memset(out, 0, sizeof(double) * (size_t)c.n_ao * n);
+    std::vector<unsigned char> raw(kTileVals * c.tsize);
+    for (int r = 0; r < c.n_mol; ++r) {
+        if (nt[r] < 0 || nt[r] > c.cap) return SSCF_ERR_STATE;
+        const int* tr = tiles.data() + (size_t)r * c.cap;
+        for (int t : want) {
+            const int* p = std::lower_bound(tr, tr + nt[r], t);
+            if (p == tr + nt[r] || *p != t) continue;
+            const size_t s = p - tr;
+            CKA(cudaMemcpy(raw.data(), (const unsigned char*)c.d_c_val[b] + ((size_t)r * c.cap + s) * kTileVals * c.tsize,
+                           raw.size(), cudaMemcpyDeviceToHost));
+            for (int i = 0; i < n; ++i) {
+                if (mo_tile[cols[i]] != t) continue;
+                const int col = cols[i] - c.h_tile_mo0[t];
+                for (int k = 0; k < 6; ++k) {
+                    const size_t e = (size_t)k * 16 + col;
+                    out[(size_t)(6 * r + k) * n + i] =
+                        c.prec == SSCF_FP64 ? ((const double*)raw.data())[e] : (double)((const float*)raw.data())[e];
+                }
+            }
+        }
+    }
+    return SSCF_OK;
+}
+
+// Entries F_ov(i, j) of the last transform (0 outside the kept blocks), i
+// occupied, j virtual (global MO indices).
+int sscf_get_F_entries(sscf_ctx* h, int n, const int* i_mo, const int* j_mo, double* out) {
+    if (!h || n < 0 || (n > 0 && (!i_mo || !j_mo || !out))) return SSCF_ERR_INVALID_ARG;
+    Ctx& c = h->c;
+    std::vector<int> g_of_occ(c.n_occ), g_of_virt(c.n_mo - c.n_occ);
+    for (int g = 0; g < c.n_groups; ++g) {
+        for (int k = 0; k < 4 * c.h_group_nmol[g]; ++k) g_of_occ[c.h_group_occ0[g] + k] = g;
+        for (int k = 0; k < 2 * c.h_group_nmol[g]; ++k) g_of_virt[c.h_group_virt0[g] - c.n_occ + k] = g;
+    }
+    CKA(cudaStreamSynchronize(c.stream));
+    std::vector<unsigned char> raw(c.tsize);
+    for (int q = 0; q < n; ++q) {
+        const int i = i_mo[q], j = j_mo[q];
+        if (i < 0 || i >= c.n_occ || j < c.n_occ || j >= c.n_mo) return SSCF_ERR_INVALID_ARG;
+        const int A = g_of_occ[i], B = g_of_virt[j - c.n_occ];
+        const int* lo = c.h_gnb_col.data() + c.h_gnb_ptr[A];
+        const int* hi = c.h_gnb_col.data() + c.h_gnb_ptr[A + 1];
+        const int* p = std::lower_bound(lo, hi, B);
+        out[q] = 0.0;
+        if (p == hi || *p != B) continue;
+        const int e = c.h_gnb_ptr[A] + (int)(p - lo);
+        const int il = i - c.h_group_occ0[A], jl = j - c.h_group_virt0[B];
+        const int tp = c.h_rot_blk_tp0[e] + (il / 16) * c.h_group_nvt[B] + jl / 16;
+        const size_t off = ((size_t)tp * 256 + (il % 16) * 16 + jl % 16) * c.tsize;
+        CKA(cudaMemcpy(raw.data(), (const unsigned char*)c.d_F + off, c.tsize, cudaMemcpyDeviceToHost));
+        out[q] = c.prec == SSCF_FP64 ? *(const double*)raw.data() : (double)*(const float*)raw.data();
+    }
+    return SSCF_OK;
+}
+
+// The molecule-pair blocks of H (current), H0 and S: pairs (m, n) into
+// mn (2 * n_mp ints) and 36 values per block into each non-NULL array
+// (n_mp * 36 doubles, row-major 6 x 6). n_mp_out receives the count; call
+// with NULL arrays first to size them.
+int sscf_get_blocks(sscf_ctx* h, int* mn, double* H, double* H0, double* S, int64_t* n_mp_out) {
+    if (!h) return SSCF_ERR_INVALID_ARG;
+    Ctx& c = h->c;
+    if (n_mp_out) *n_mp_out = c.n_mp;
+    if (mn)
+        for (int m = 0; m < c.n_mol; ++m)
+            for (int e = c.h_mp_ptr[m]; e < c.h_mp_ptr[m + 1]; ++e) {
+                mn[2 * e] = m;
+                mn[2 * e + 1] = c.h_mp_col[e];
+            }
+    if (H) {
+        std::vector<double> v;
+        int s = fetch_values(c, c.d_Hb, (size_t)c.n_mp * 36, v);
+        if (s != SSCF_OK) return s;
+        std::memcpy(H, v.data(), v.size() * 8);
+    }
+    CKA(cudaStreamSynchronize(c.stream));
+    if (H0) CKA(cudaMemcpy(H0, c.d_H0b, (size_t)c.n_mp * 36 * 8, cudaMemcpyDeviceToHost));
+    if (S) CKA(cudaMemcpy(S, c.d_Sb, (size_t)c.n_mp * 36 * 8, cudaMemcpyDeviceToHost));
+    return SSCF_OK;
+}
+
 int sscf_get_H_dense(sscf_ctx* h, double* H, double* H0, double* S) {
     if (!h) return SSCF_ERR_INVALID_ARG;
     Ctx& c = h->c;

@@ -1,0 +1,208 @@
+"""Parity at the benchmark's full size: 4096 water molecules, mixed precision.
+
+The state is prepared as the benchmark prepares it (guess, full
+orthonormalisation at eps = 1e-3, then eps = 1e-5). Dense 24576 x 24576
+matrices do not fit the oracle, so this file checks the full-size state
+through exact invariants and through sampled outputs that the oracle computes
+one by one:
+
+* H0 and S on every molecule-pair block against the oracle's sparse build;
+* the SCC Hamiltonian on sampled molecule-pair blocks (Eq. H_dftb2 with the
+  eps truncation of Section "Sparse matrices");
+* Q = gamma dq for every atom against the oracle's chunked gamma product;
+* sum_a q_a = 8 N_mol and dq = q - q0 (normalised, doubly occupied MOs);
+* Mulliken charges of sampled atoms from C rows and S (Eq. pop);
+* sampled overlaps c_i^T S c_j after the orthonormalisation (Section
+  "Orthonormalisation"): below its tolerance eps / 100;
+* sampled F_ij = c_i^T H c_j of the occupied-virtual transform (Step V).
+
+Mixed-precision bounds are stated where they are used: C, H, S and Y are
+stored in FP32 and products are summed in FP32 over at most 32 rows before an
+FP64 flush, so a contraction differs from the FP64 one on the same stored
+values by at most about 64 * 2^-24 times the sum of the absolute terms; the
+tests allow 256 * 2^-24 of that sum.
+"""
+import functools
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+from gpu_common import P, context, water
+from oracle import model, sparse
+
+pytestmark = pytest.mark.gpu
+
+N_MOL = 4096
+U32 = 2.0 ** -24
+K_ACC = 256 * U32
+
+
+@functools.lru_cache(maxsize=None)
+def prepared():
+    """Context in the benchmark's starting state plus the oracle's sparse model."""
+    s = water(N_MOL)
+    ctx = context(s, precision=1)
+    ctx.set_thresholds(1e-3, 1e-2, 1e-8)
+    ctx.guess()
+    passes, eta = ctx.orthonormalise(0, max_pass=60)
+    ctx.set_thresholds(1e-5, 1e-4, 1e-6)
+    ctx.reset_charges()
+    H0, S = model.build_h0_s(s, P, dense=False)
+    st = sparse.build_structure(s, P)
+    return s, ctx, passes, eta, H0.tocsr(), S.tocsr(), st
+
+
+def blocks_as_csr(mn, B, n_ao):
+    m, n = mn[:, 0], mn[:, 1]
+    r = (6 * m)[:, None, None] + np.arange(6)[None, :, None]
+    c = (6 * n)[:, None, None] + np.arange(6)[None, None, :]
+    r, c = np.broadcast_to(r, B.shape).ravel(), np.broadcast_to(c, B.shape).ravel()
+    return sp.csr_matrix((B.ravel(), (r, c)), shape=(n_ao, n_ao))
+
+
+def test_model_blocks_match_oracle_everywhere():
+    s, ctx, _, _, H0, S, _ = prepared()
+    mn, _, gH0, gS = ctx.get_blocks()
+    for g, ref in ((gH0, H0), (gS, S)):
+        G = blocks_as_csr(mn, g, s.n_ao)
+        assert abs(G - ref).max() < 1e-14
+        assert (G != 0).nnz == (ref != 0).nnz
+
+
+def test_fock_blocks_sampled():
+    s, ctx, _, _, H0, S, _ = prepared()
+    ctx.build_fock()
+    _, _, Q = ctx.get_charges()
+    mn, gH, _, _ = ctx.get_blocks()
+    atom_in_mol = np.array([0, 0, 0, 0, 1, 2])
+    rng = np.random.default_rng(11)
+    for e in rng.choice(mn.shape[0], 400, replace=False):
+        m, n = (int(x) for x in mn[e])
+        mols = [m] if m == n else [m, n]
+        ao = np.concatenate([np.arange(6 * x, 6 * x + 6) for x in mols])
+        atoms = np.concatenate([np.arange(3 * x, 3 * x + 3) for x in mols])
+        loc = np.concatenate([3 * j + atom_in_mol for j in range(len(mols))])
+        ref = sparse.fock(H0[ao][:, ao].toarray(), S[ao][:, ao].toarray(), Q[atoms], loc, 1e-5)
+        blk = ref[:6, 6:] if m != n else ref
+        # FP32 storage of H: one rounding of the FP64 value; entries within a
+        # few FP64 ulps of eps may be kept on one side and dropped on the other
+        near = np.abs(np.abs(blk) - 1e-5) <= 1e-19
+        diff = np.abs(gH[e] - blk)
+        assert np.all((diff <= 1.01 * U32 * np.abs(blk) + 1e-300) | near)
+
+
+def test_gamma_charges_everywhere():
+    s, ctx, *_ = prepared()
+    q, dq, Q = ctx.get_charges()
+    q0 = model.reference_population(s, P)
+    assert np.abs(dq - (q - q0)).max() < 1e-12
+    ref = model.gamma_times(s, P, dq, chunk=256)
+    scale = model.gamma_times(s, P, np.abs(dq), chunk=256)
+    # FP32 coordinates (|x| < 128 bohr: 2e-5 bohr on a distance) move
+    # 1/sqrt(r^2 + a^2), a >= 2 bohr, by at most 5e-6 relative; FP32 sums over
+    # 256-atom tiles add 256 * 2^-24 relative to the absolute sum.
+    assert np.all(np.abs(Q - ref) <= 3e-5 * scale + 1e-12)
+
+
+def test_electron_count():
+    s, ctx, *_ = prepared()
+    q, dq, _ = ctx.get_charges()
+    assert abs(q.sum() - 8 * N_MOL) < 1e-5 * 8 * N_MOL
+    assert abs(dq.sum()) < 1e-5 * 8 * N_MOL
+
+
+def sampled_mulliken(ctx, S, mol):
+    """Eq. (pop) for the three atoms of ``mol`` from the rows of C (oracle routine on the row slice)."""
+    rows = np.arange(6 * mol, 6 * mol + 6)
+    Sm = S[rows]
+    cols = np.unique(Sm.indices)
+    n_occ = 4 * N_MOL
+    Cr = ctx.get_C_rows(rows)[:, :n_occ]
+    Cc = ctx.get_C_rows(cols)[:, :n_occ]
+    Pm = np.zeros((6, S.shape[1]))
+    Pm[:, cols] = 2.0 * Cr @ Cc.T
+    Pabs = np.zeros_like(Pm)
+    Pabs[:, cols] = 2.0 * np.abs(Cr) @ np.abs(Cc).T
+    aoa = np.array([0, 0, 0, 0, 1, 2])
+    q = model.mulliken(Pm, Sm, aoa, 3)
+    bound = model.mulliken(Pabs, abs(Sm), aoa, 3)
+    return q, bound
+
+
+def check_sampled_mulliken(s, ctx, S):
+    q, _, _ = ctx.get_charges()
+    L = s.lattice_edge
+    for mol in (0, N_MOL - 1, N_MOL // 2 + L // 2, L * L + L + 1):
+        ref, bound = sampled_mulliken(ctx, S, mol)
+        assert np.all(np.abs(q[3 * mol:3 * mol + 3] - ref) <= K_ACC * bound + 1e-12)
+    assert abs(q.sum() - 8 * N_MOL) < 1e-5 * 8 * N_MOL
+
+
+def test_mulliken_sampled_prepared():
+    s, ctx, _, _, _, S, _ = prepared()
+    check_sampled_mulliken(s, ctx, S)
+
+
+def apply_blocks(mn, B, X):
+    """Y = A X for the block-sparse A given by molecule pairs mn and 6x6 blocks B."""
+    return blocks_as_csr(mn, B, X.shape[0]) @ X
+
+
+def _sample_group_pairs(st, rng, k):
+    A = rng.choice(st.n_groups, k, replace=False)
+    out = []
+    for a in A:
+        nb = np.flatnonzero(st.group_nb[a])
+        out.append((int(a), int(rng.choice(nb))))
+    return out
+
+
+def test_overlaps_sampled_after_orthonormalisation():
+    s, ctx, passes, eta, _, S, st = prepared()
+    tol = 1e-3 / 100.0
+    assert eta < tol, (passes, eta)
+    rng = np.random.default_rng(5)
+    pairs = _sample_group_pairs(st, rng, 6)
+    mos = np.unique(np.concatenate([np.concatenate([st.occ_of_group[a][:16], st.occ_of_group[b][:16],
+                                                    st.virt_of_group[b][:16]]) for a, b in pairs]))
+    C = ctx.get_C_cols(mos)
+    mn, _, _, Sb = ctx.get_blocks()
+    SC = apply_blocks(mn, Sb, C)
+    sigma = C.T @ SC
+    go = st.mo_group[mos]
+    mask = st.group_nb[go[:, None], go[None, :]]
+    off = sigma - np.eye(mos.size)
+    # eta is measured before the last pass's combos, which only lower |sigma_ij|;
+    # FP32 storage of C adds about 1e-6 at most to an overlap of unit vectors.
+    assert np.abs(off[mask]).max() < tol + 1e-6
+    assert np.abs(np.diag(sigma) - 1.0).max() < tol
+
+
+def test_transform_entries_sampled():
+    s, ctx, _, _, _, _, st = prepared()
+    ctx.build_fock()
+    rng = np.random.default_rng(9)
+    pairs = _sample_group_pairs(st, rng, 6)
+    occ = np.unique(np.concatenate([st.occ_of_group[a][:16] for a, _ in pairs]))
+    vir = np.unique(np.concatenate([st.virt_of_group[b][:16] for _, b in pairs]))
+    Co, Cv = ctx.get_C_cols(occ), ctx.get_C_cols(vir)
+    mn, Hb, _, _ = ctx.get_blocks()
+    ref = Co.T @ apply_blocks(mn, Hb, Cv)
+    bound = np.abs(Co).T @ apply_blocks(mn, np.abs(Hb), np.abs(Cv))
+    n_rot, max_fov = ctx.rotate_sweep()
+    ii, jj = np.meshgrid(occ, vir, indexing="ij")
+    F = ctx.get_F_entries(ii.ravel(), jj.ravel()).reshape(ii.shape)
+    mask = st.group_nb[st.mo_group[occ][:, None], st.mo_group[vir][None, :]]
+    want = np.where(mask, ref, 0.0)
+    assert np.all(np.abs(F - want) <= K_ACC * bound + 1e-12)
+    assert mask.sum() > 1000
+    assert max_fov >= np.abs(F).max() and n_rot > 0
+
+
+def test_mulliken_sampled_after_full_step():
+    """Runs last: one whole SCC iteration (Fock, sweep, occupied pass, charges)."""
+    s, ctx, _, _, _, S, _ = prepared()
+    info = ctx.step()
+    assert info["n_rot"] > 0 and np.isfinite(info["energy"])
+    check_sampled_mulliken(s, ctx, S)
