@@ -73,6 +73,9 @@ typedef struct {
     int precision;           /* SSCF_FP64 or SSCF_MIXED                                   */
     int ortho_every;         /* 1: one occupied orthonormalisation pass per SCC step     */
     int cap_tiles;           /* per-row tile capacity of C; 0 picks the dense size       */
+    int cap_y;               /* row blocks per tile of Y = X C; 0 picks the largest cluster */
+    int apply_variant;       /* 0: specialised sweep kernels where a block allows them,
+                                1: the generic kernel for every block (same results)     */
 } sscf_params;
 
 typedef struct {

@@ -129,7 +129,7 @@ int build_structure(Ctx& c, const sscf_system* sys) {
     c.h_group_nvt.assign(G, 0);
     int o = 0, v = c.n_occ, ot = 0;
     for (int g = 0; g < G; ++g) {
-        if (mols[g].empty() || mols[g].size() > 8) return SSCF_ERR_INVALID_ARG;
+        if (mols[g].empty() || mols[g].size() > (size_t)kMaxMolPerGroup) return SSCF_ERR_INVALID_ARG;
         for (int m : mols[g])
             if (c.h_mol_cluster[m] != c.h_mol_cluster[mols[g][0]]) return SSCF_ERR_INVALID_ARG;
         if (g > 0 && c.h_mol_cluster[mols[g][0]] < c.h_mol_cluster[mols[g - 1][0]]) return SSCF_ERR_INVALID_ARG;
@@ -275,6 +275,18 @@ int build_structure(Ctx& c, const sscf_system* sys) {
             int col = c.h_gnb_colour[e];
             c.h_colour_blk[f1[col]++] = e;
             if (c.h_gnb_row[e] <= c.h_gnb_col[e]) c.h_ocolour_blk[f2[col]++] = e;
+        }
+        // within each colour, blocks between two different full groups (8
+        // molecules: 32 occupied MOs on each side) first; the occupied pass
+        // runs them through the register-resident kernel
+        c.h_ocolour_nfull.assign(n_col, 0);
+        for (int k = 0; k < n_col; ++k) {
+            auto b = c.h_ocolour_blk.begin() + c.h_ocolour_ptr[k], en = c.h_ocolour_blk.begin() + c.h_ocolour_ptr[k + 1];
+            auto mid = std::stable_partition(b, en, [&](int e) {
+                const int A = c.h_gnb_row[e], B = c.h_gnb_col[e];
+                return A != B && c.h_group_nmol[A] == kMaxMolPerGroup && c.h_group_nmol[B] == kMaxMolPerGroup;
+            });
+            c.h_ocolour_nfull[k] = (int)(mid - b);
         }
     }
 
@@ -494,6 +506,8 @@ int sscf_create(const sscf_system* sys, const sscf_params* prm, void* cuda_strea
     *out = nullptr;
     if (sys->n_atoms <= 0 || sys->n_atoms % 3 != 0) return SSCF_ERR_INVALID_ARG;
     if (prm->precision != SSCF_FP64 && prm->precision != SSCF_MIXED) return SSCF_ERR_INVALID_ARG;
+    if (prm->apply_variant != 0 && prm->apply_variant != 1) return SSCF_ERR_INVALID_ARG;
+    if (prm->cap_tiles < 0 || prm->cap_y < 0) return SSCF_ERR_INVALID_ARG;
     if (!(prm->r_cut > 0) || !(prm->r_decay > 0) || !(prm->group_cut > 0) || !(prm->eps >= 0) ||
         !(prm->U[0] > 0) || !(prm->U[1] > 0) || !(prm->rot_cap_factor > 0))
         return SSCF_ERR_INVALID_ARG;
@@ -576,7 +590,8 @@ int sscf_create(const sscf_system* sys, const sscf_params* prm, void* cuda_strea
         delete h;
         return SSCF_ERR_INVALID_ARG;
     }
-    c.capY = c.max_cl_mol;
+    c.capY = prm->cap_y > 0 ? std::min(prm->cap_y, c.max_cl_mol) : c.max_cl_mol;
+    c.apply_variant = prm->apply_variant;
     // uploads
 #define UP(d, v)                        \
     do {                                \

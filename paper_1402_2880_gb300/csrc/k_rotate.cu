@@ -15,6 +15,8 @@
 
 #include "sscf_internal.h"
 
+#include <type_traits>
+
 namespace sscf {
 
 namespace {
@@ -786,6 +788,124 @@ __global__ void __launch_bounds__(apply_threads<T>()) k_apply_colour(SweepArgs a
     }
 }
 
+// Occupied pass, blocks between two different full groups (32 occupied MOs
+// on each side, in-block colour (i + j) mod 32), FP32 storage. Same updates,
+// order and truncation as k_apply_colour, laid out for fewer shared-memory
+// round trips: each thread owns two adjacent AO rows; the 32 A-side values
+// of those rows stay in registers (the index i is static once the slot loop
+// is unrolled), the 32 B-side values sit in a thread-private shared-memory
+// panel indexed by j = (level - i) mod 32. The block's combinations are
+// expanded into a dense [level][i] coefficient table with a selection mask
+// per level. No barrier is needed after the table is built: a thread reads
+// back only the rows it wrote.
+constexpr int kFullCH = 32;                       // row blocks per CTA
+constexpr int kFullNR = kFullCH * kAoPerMol;      // AO rows per CTA (panel stride, floats)
+constexpr int kFullThreads = kFullNR / 2;
+__host__ __device__ constexpr size_t full_apply_smem() { return (size_t)32 * kFullNR * 4 + (size_t)32 * 32 * 8; }
+
+__global__ void __launch_bounds__(kFullThreads) k_apply_occ_full(SweepArgs a, int p0) {
+    extern __shared__ unsigned char smraw[];
+    float* panel = (float*)smraw;                           // [32 B columns][kFullNR rows]
+    float2* coef = (float2*)(panel + 32 * kFullNR);         // [32 levels][32 i]: (-c, -c)
+    __shared__ unsigned s_mask[32];
+    const int e = a.blk[p0 + blockIdx.y];
+    const int np = a.pr_n[e];
+    if (np == 0) return;
+    const int A = a.gnb_row[e], B = a.gnb_col[e];
+    const int ta0 = a.group_ot0[A], tb0 = a.group_ot0[B];
+    const int pa = a.cci_ptr[ta0], n_rows = a.cci_ptr[ta0 + 1] - pa;
+    const int pb = a.cci_ptr[tb0];
+    const int k0 = blockIdx.x * kFullCH;
+    if (k0 >= n_rows) return;
+    if (a.cci_ptr[tb0 + 1] - pb != n_rows) {
+        if (threadIdx.x == 0) atomicOr(a.err, kErrCapacity);
+        return;
+    }
+    const int nk = min(kFullCH, n_rows - k0);
+    if (threadIdx.x == 0) atomicAdd(a.upd, (unsigned long long)np * (unsigned long long)(nk * 6));
+    for (int i = threadIdx.x; i < 32 * 32; i += blockDim.x) coef[i] = make_float2(0.f, 0.f);
+    if (threadIdx.x < 32) s_mask[threadIdx.x] = 0u;
+    __syncthreads();
+    const float* cs = (const float*)a.pr_cs + (size_t)e * kOrthoCap * 2;
+    const uint16_t* ij = a.pr_ij + (size_t)e * kOrthoCap;
+    for (int q = threadIdx.x; q < np; q += blockDim.x) {
+        const unsigned w = ij[q];
+        const int il = w & 255, jl = w >> 8, lv = (il + jl) & 31;
+        const float c = cs[2 * q];
+        coef[lv * 32 + il] = make_float2(-c, -c);
+        atomicOr(&s_mask[lv], 1u << il);
+    }
+    __syncthreads();
+    const int rb = threadIdx.x / 3, k2 = 2 * (threadIdx.x - 3 * rb);
+    if (rb >= nk) return;
+    float* val = (float*)a.out_val;   // in place
+    const int row = a.cci_row[pa + k0 + rb];
+    const size_t baseA = ((size_t)row * a.cap + a.cci_slot[pa + k0 + rb]) * kTileVals + k2 * kTileW;
+    const size_t baseB = ((size_t)row * a.cap + a.cci_slot[pb + k0 + rb]) * kTileVals + k2 * kTileW;
+    float* pr = panel + 2 * threadIdx.x;   // = 6 rb + k2: this thread's two rows
+    float2 x[32];
+#pragma unroll
+    for (int t = 0; t < 2; ++t) {
+        const float4* s0 = (const float4*)(val + baseA + (size_t)t * kTileVals);
+        const float4* s1 = (const float4*)(val + baseB + (size_t)t * kTileVals);
+        float4 u0[4], u1[4], v0[4], v1[4];
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            u0[v] = s0[v];
+            u1[v] = s0[4 + v];   // next AO row: 16 floats on
+            v0[v] = s1[v];
+            v1[v] = s1[4 + v];
+        }
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            x[t * 16 + 4 * v + 0] = make_float2(u0[v].x, u1[v].x);
+            x[t * 16 + 4 * v + 1] = make_float2(u0[v].y, u1[v].y);
+            x[t * 16 + 4 * v + 2] = make_float2(u0[v].z, u1[v].z);
+            x[t * 16 + 4 * v + 3] = make_float2(u0[v].w, u1[v].w);
+            *(float2*)(pr + (t * 16 + 4 * v + 0) * kFullNR) = make_float2(v0[v].x, v1[v].x);
+            *(float2*)(pr + (t * 16 + 4 * v + 1) * kFullNR) = make_float2(v0[v].y, v1[v].y);
+            *(float2*)(pr + (t * 16 + 4 * v + 2) * kFullNR) = make_float2(v0[v].z, v1[v].z);
+            *(float2*)(pr + (t * 16 + 4 * v + 3) * kFullNR) = make_float2(v0[v].w, v1[v].w);
+        }
+    }
+    const float tf = a.trunc_f;
+    for (int lv = 0; lv < 32; ++lv) {
+        const unsigned m = s_mask[lv];
+        if (m == 0u) continue;
+        const float2* cl = coef + lv * 32;
+#pragma unroll
+        for (int i = 0; i < 32; ++i) {
+            if (m & (1u << i)) {
+                float2* py = (float2*)(pr + ((lv - i) & 31) * kFullNR);
+                const float2 c2 = cl[i];
+                const float2 y = *py;
+                const float2 xn = __ffma2_rn(c2, y, x[i]);
+                const float2 yn = __ffma2_rn(c2, x[i], y);
+                x[i] = trunc2(xn, tf);
+                *py = trunc2(yn, tf);
+            }
+        }
+    }
+#pragma unroll
+    for (int t = 0; t < 2; ++t) {
+        float4* d0 = (float4*)(val + baseA + (size_t)t * kTileVals);
+        float4* d1 = (float4*)(val + baseB + (size_t)t * kTileVals);
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            const float2 a0 = x[t * 16 + 4 * v], a1 = x[t * 16 + 4 * v + 1];
+            const float2 a2 = x[t * 16 + 4 * v + 2], a3 = x[t * 16 + 4 * v + 3];
+            d0[v] = make_float4(a0.x, a1.x, a2.x, a3.x);
+            d0[4 + v] = make_float4(a0.y, a1.y, a2.y, a3.y);
+            const float2 b0 = *(const float2*)(pr + (t * 16 + 4 * v + 0) * kFullNR);
+            const float2 b1 = *(const float2*)(pr + (t * 16 + 4 * v + 1) * kFullNR);
+            const float2 b2 = *(const float2*)(pr + (t * 16 + 4 * v + 2) * kFullNR);
+            const float2 b3 = *(const float2*)(pr + (t * 16 + 4 * v + 3) * kFullNR);
+            d1[v] = make_float4(b0.x, b1.x, b2.x, b3.x);
+            d1[4 + v] = make_float4(b0.y, b1.y, b2.y, b3.y);
+        }
+    }
+}
+
 // drop tiles whose 6x16 values are all zero; in -> out
 // (skipped entirely when an earlier kernel of the pass set the error word:
 // `out` is then the pass's untouched input and stays as it was)
@@ -962,11 +1082,24 @@ static cudaError_t apply_mode_t(Ctx* c, int which) {
     const std::vector<int>& ptr = MODE == 0 ? c->h_colour_ptr : c->h_ocolour_ptr;
     constexpr int CH = ApplyShape<T>::chunk;
     const int gx = (c->n_mol + CH - 1) / CH;
+    // occupied passes in FP32: blocks between two full groups take the register-resident kernel
+    const bool full = std::is_same<T, float>::value && MODE == 1 && which == 1 && c->apply_variant == 0;
+    if (full) {
+        e = cudaFuncSetAttribute(k_apply_occ_full, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)full_apply_smem());
+        if (e != cudaSuccess) return e;
+    }
+    const int gxf = (c->n_mol + kFullCH - 1) / kFullCH;
     for (int col = 0; col < c->n_colours; ++col) {
-        const int nb = ptr[col + 1] - ptr[col];
+        const int nf = full ? c->h_ocolour_nfull[col] : 0;
+        if (nf > 0) {
+            k_apply_occ_full<<<dim3(gxf, nf), kFullThreads, full_apply_smem(), c->stream>>>(a, ptr[col]);
+            c->n_launch += 1;
+        }
+        const int nb = ptr[col + 1] - ptr[col] - nf;
         if (nb == 0) continue;
         dim3 grid(gx, nb);
-        k_apply_colour<T, MODE, NT, PCAP><<<grid, apply_threads<T>(), smem, c->stream>>>(a, ptr[col]);
+        k_apply_colour<T, MODE, NT, PCAP><<<grid, apply_threads<T>(), smem, c->stream>>>(a, ptr[col] + nf);
         c->n_launch += 1;
     }
     return cudaGetLastError();

@@ -32,6 +32,7 @@ namespace sscf {
 constexpr int kAoPerMol = 6;
 constexpr int kTileW = 16;
 constexpr int kTileVals = kAoPerMol * kTileW;  // 96
+constexpr int kMaxMolPerGroup = 8;
 constexpr int kMaxSub = 48;                    // in-block colours (<= MOs per group side)
 constexpr int kRotCap = 32 * 16;               // pairs of one occupied-virtual block
 constexpr int kOrthoCap = 48 * 48;             // pairs of one orthonormalisation block
@@ -81,6 +82,7 @@ struct Ctx {
     int n_gnb = 0;       // group-graph entries (directed, including (A, A))
     int cap = 0;         // tiles per row block of C
     int capY = 0;        // row blocks per tile of Y
+    int apply_variant = 0;   // 0 specialised sweep kernels where they apply, 1 generic only
     bool have_guess = false;
     int iteration = 0;
     long long n_launch = 0;   // kernels launched by this context
@@ -101,6 +103,7 @@ struct Ctx {
     std::vector<int> h_gnb_ptr, h_gnb_col, h_gnb_row, h_gnb_colour;
     std::vector<int> h_colour_ptr, h_colour_blk;        // all directed blocks by colour
     std::vector<int> h_ocolour_ptr, h_ocolour_blk;      // blocks with A <= B by colour
+    std::vector<int> h_ocolour_nfull;                   // leading blocks of each colour between two full groups
     // tile-pair lists of the transforms
     std::vector<int> h_rot_tp_ptr;   // per a-tile CSR into (b, out) for the F_ov blocks
     std::vector<int> h_rot_tp_b, h_rot_tp_out;
