@@ -276,18 +276,24 @@ int build_structure(Ctx& c, const sscf_system* sys) {
             c.h_colour_blk[f1[col]++] = e;
             if (c.h_gnb_row[e] <= c.h_gnb_col[e]) c.h_ocolour_blk[f2[col]++] = e;
         }
-        // within each colour, blocks between two different full groups (8
-        // molecules: 32 occupied MOs on each side) first; the occupied pass
-        // runs them through the register-resident kernel
-        c.h_ocolour_nfull.assign(n_col, 0);
-        for (int k = 0; k < n_col; ++k) {
-            auto b = c.h_ocolour_blk.begin() + c.h_ocolour_ptr[k], en = c.h_ocolour_blk.begin() + c.h_ocolour_ptr[k + 1];
-            auto mid = std::stable_partition(b, en, [&](int e) {
-                const int A = c.h_gnb_row[e], B = c.h_gnb_col[e];
-                return A != B && c.h_group_nmol[A] == kMaxMolPerGroup && c.h_group_nmol[B] == kMaxMolPerGroup;
-            });
-            c.h_ocolour_nfull[k] = (int)(mid - b);
-        }
+        // within each colour, blocks between full groups (8 molecules: 32
+        // occupied and 16 virtual MOs) first; FP32 sweeps run them through the
+        // register-resident kernel (occupied passes: A != B only)
+        auto full_first = [&](std::vector<int>& blk, const std::vector<int>& ptr, std::vector<int>& nfull,
+                              bool distinct) {
+            nfull.assign(n_col, 0);
+            for (int k = 0; k < n_col; ++k) {
+                auto b = blk.begin() + ptr[k], en = blk.begin() + ptr[k + 1];
+                auto mid = std::stable_partition(b, en, [&](int e) {
+                    const int A = c.h_gnb_row[e], B = c.h_gnb_col[e];
+                    return (!distinct || A != B) && c.h_group_nmol[A] == kMaxMolPerGroup &&
+                           c.h_group_nmol[B] == kMaxMolPerGroup;
+                });
+                nfull[k] = (int)(mid - b);
+            }
+        };
+        full_first(c.h_colour_blk, c.h_colour_ptr, c.h_colour_nfull, false);
+        full_first(c.h_ocolour_blk, c.h_ocolour_ptr, c.h_ocolour_nfull, true);
     }
 
     // ---- tile pairs of the occupied-virtual transform ----

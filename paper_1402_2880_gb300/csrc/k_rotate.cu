@@ -788,31 +788,55 @@ __global__ void __launch_bounds__(apply_threads<T>()) k_apply_colour(SweepArgs a
     }
 }
 
-// Occupied pass, blocks between two different full groups (32 occupied MOs
-// on each side, in-block colour (i + j) mod 32), FP32 storage. Same updates,
-// order and truncation as k_apply_colour, laid out for fewer shared-memory
-// round trips: each thread owns two adjacent AO rows; the 32 A-side values
-// of those rows stay in registers (the index i is static once the slot loop
-// is unrolled), the 32 B-side values sit in a thread-private shared-memory
-// panel indexed by j = (level - i) mod 32. The block's combinations are
-// expanded into a dense [level][i] coefficient table with a selection mask
-// per level. No barrier is needed after the table is built: a thread reads
-// back only the rows it wrote.
+// Blocks between full groups (8 molecules: 32 occupied and 16 virtual MOs per
+// group) in FP32 storage: rotations (MODE 0, A occupied x B virtual) and
+// occupied-pass combinations (MODE 1, A occupied x B occupied, A != B). The
+// in-block colour of such a block is (i + j) mod 32. Same updates, order and
+// truncation as k_apply_colour, laid out for fewer shared-memory round trips:
+// each thread owns two adjacent AO rows; the 32 A-side values of those rows
+// stay in registers (the index i is static once the slot loop is unrolled),
+// the NB B-side values sit in a thread-private shared-memory panel indexed by
+// j = (level - i) mod 32. The block's pairs are expanded into a dense
+// [level][i] coefficient table with a selection mask per level. No barrier is
+// needed after the table is built: a thread reads back only the rows it wrote.
 constexpr int kFullCH = 32;                       // row blocks per CTA
 constexpr int kFullNR = kFullCH * kAoPerMol;      // AO rows per CTA (panel stride, floats)
 constexpr int kFullThreads = kFullNR / 2;
-__host__ __device__ constexpr size_t full_apply_smem() { return (size_t)32 * kFullNR * 4 + (size_t)32 * 32 * 8; }
+template <int MODE> struct FullShape;
+template <> struct FullShape<0> {   // rotations: B = one virtual tile, coefficients (c, c, s, s)
+    static constexpr int nb = 16;
+    using Coef = float4;
+};
+template <> struct FullShape<1> {   // combinations: B = two occupied tiles, coefficients (-c, -c)
+    static constexpr int nb = 32;
+    using Coef = float2;
+};
+template <int MODE> __host__ __device__ constexpr size_t full_apply_smem() {
+    return (size_t)FullShape<MODE>::nb * kFullNR * 4 + (size_t)32 * 32 * sizeof(typename FullShape<MODE>::Coef);
+}
 
-__global__ void __launch_bounds__(kFullThreads) k_apply_occ_full(SweepArgs a, int p0) {
+__device__ __forceinline__ void load_pair_rows(const float* src, float4 (&r0)[4], float4 (&r1)[4]) {
+    const float4* s = (const float4*)src;
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+        r0[v] = s[v];
+        r1[v] = s[4 + v];   // next AO row: 16 floats on
+    }
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(kFullThreads) k_apply_full(SweepArgs a, int p0) {
+    constexpr int NB = FullShape<MODE>::nb;
+    using Coef = typename FullShape<MODE>::Coef;
     extern __shared__ unsigned char smraw[];
-    float* panel = (float*)smraw;                           // [32 B columns][kFullNR rows]
-    float2* coef = (float2*)(panel + 32 * kFullNR);         // [32 levels][32 i]: (-c, -c)
+    float* panel = (float*)smraw;                           // [NB B columns][kFullNR rows]
+    Coef* coef = (Coef*)(panel + NB * kFullNR);             // [32 levels][32 i]
     __shared__ unsigned s_mask[32];
     const int e = a.blk[p0 + blockIdx.y];
     const int np = a.pr_n[e];
     if (np == 0) return;
     const int A = a.gnb_row[e], B = a.gnb_col[e];
-    const int ta0 = a.group_ot0[A], tb0 = a.group_ot0[B];
+    const int ta0 = a.group_ot0[A], tb0 = MODE == 0 ? a.group_vt0[B] : a.group_ot0[B];
     const int pa = a.cci_ptr[ta0], n_rows = a.cci_ptr[ta0 + 1] - pa;
     const int pb = a.cci_ptr[tb0];
     const int k0 = blockIdx.x * kFullCH;
@@ -823,7 +847,10 @@ __global__ void __launch_bounds__(kFullThreads) k_apply_occ_full(SweepArgs a, in
     }
     const int nk = min(kFullCH, n_rows - k0);
     if (threadIdx.x == 0) atomicAdd(a.upd, (unsigned long long)np * (unsigned long long)(nk * 6));
-    for (int i = threadIdx.x; i < 32 * 32; i += blockDim.x) coef[i] = make_float2(0.f, 0.f);
+    for (int i = threadIdx.x; i < 32 * 32; i += blockDim.x) {
+        if constexpr (MODE == 0) coef[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+        else coef[i] = make_float2(0.f, 0.f);
+    }
     if (threadIdx.x < 32) s_mask[threadIdx.x] = 0u;
     __syncthreads();
     const float* cs = (const float*)a.pr_cs + (size_t)e * kOrthoCap * 2;
@@ -832,7 +859,12 @@ __global__ void __launch_bounds__(kFullThreads) k_apply_occ_full(SweepArgs a, in
         const unsigned w = ij[q];
         const int il = w & 255, jl = w >> 8, lv = (il + jl) & 31;
         const float c = cs[2 * q];
-        coef[lv * 32 + il] = make_float2(-c, -c);
+        if constexpr (MODE == 0) {
+            const float sn = cs[2 * q + 1];
+            coef[lv * 32 + il] = make_float4(c, c, sn, sn);
+        } else {
+            coef[lv * 32 + il] = make_float2(-c, -c);
+        }
         atomicOr(&s_mask[lv], 1u << il);
     }
     __syncthreads();
@@ -846,22 +878,22 @@ __global__ void __launch_bounds__(kFullThreads) k_apply_occ_full(SweepArgs a, in
     float2 x[32];
 #pragma unroll
     for (int t = 0; t < 2; ++t) {
-        const float4* s0 = (const float4*)(val + baseA + (size_t)t * kTileVals);
-        const float4* s1 = (const float4*)(val + baseB + (size_t)t * kTileVals);
-        float4 u0[4], u1[4], v0[4], v1[4];
-#pragma unroll
-        for (int v = 0; v < 4; ++v) {
-            u0[v] = s0[v];
-            u1[v] = s0[4 + v];   // next AO row: 16 floats on
-            v0[v] = s1[v];
-            v1[v] = s1[4 + v];
-        }
+        float4 u0[4], u1[4];
+        load_pair_rows(val + baseA + (size_t)t * kTileVals, u0, u1);
 #pragma unroll
         for (int v = 0; v < 4; ++v) {
             x[t * 16 + 4 * v + 0] = make_float2(u0[v].x, u1[v].x);
             x[t * 16 + 4 * v + 1] = make_float2(u0[v].y, u1[v].y);
             x[t * 16 + 4 * v + 2] = make_float2(u0[v].z, u1[v].z);
             x[t * 16 + 4 * v + 3] = make_float2(u0[v].w, u1[v].w);
+        }
+    }
+#pragma unroll
+    for (int t = 0; t < NB / 16; ++t) {
+        float4 v0[4], v1[4];
+        load_pair_rows(val + baseB + (size_t)t * kTileVals, v0, v1);
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
             *(float2*)(pr + (t * 16 + 4 * v + 0) * kFullNR) = make_float2(v0[v].x, v1[v].x);
             *(float2*)(pr + (t * 16 + 4 * v + 1) * kFullNR) = make_float2(v0[v].y, v1[v].y);
             *(float2*)(pr + (t * 16 + 4 * v + 2) * kFullNR) = make_float2(v0[v].z, v1[v].z);
@@ -872,15 +904,22 @@ __global__ void __launch_bounds__(kFullThreads) k_apply_occ_full(SweepArgs a, in
     for (int lv = 0; lv < 32; ++lv) {
         const unsigned m = s_mask[lv];
         if (m == 0u) continue;
-        const float2* cl = coef + lv * 32;
+        const Coef* cl = coef + lv * 32;
 #pragma unroll
         for (int i = 0; i < 32; ++i) {
             if (m & (1u << i)) {
                 float2* py = (float2*)(pr + ((lv - i) & 31) * kFullNR);
-                const float2 c2 = cl[i];
+                const Coef c4 = cl[i];
                 const float2 y = *py;
-                const float2 xn = __ffma2_rn(c2, y, x[i]);
-                const float2 yn = __ffma2_rn(c2, x[i], y);
+                float2 xn, yn;
+                if constexpr (MODE == 0) {
+                    const float2 cc = make_float2(c4.x, c4.y);
+                    xn = __ffma2_rn(cc, x[i], __fmul2_rn(make_float2(c4.z, c4.w), y));
+                    yn = __ffma2_rn(cc, y, __fmul2_rn(make_float2(-c4.z, -c4.w), x[i]));
+                } else {
+                    xn = __ffma2_rn(c4, y, x[i]);
+                    yn = __ffma2_rn(c4, x[i], y);
+                }
                 x[i] = trunc2(xn, tf);
                 *py = trunc2(yn, tf);
             }
@@ -889,13 +928,19 @@ __global__ void __launch_bounds__(kFullThreads) k_apply_occ_full(SweepArgs a, in
 #pragma unroll
     for (int t = 0; t < 2; ++t) {
         float4* d0 = (float4*)(val + baseA + (size_t)t * kTileVals);
-        float4* d1 = (float4*)(val + baseB + (size_t)t * kTileVals);
 #pragma unroll
         for (int v = 0; v < 4; ++v) {
             const float2 a0 = x[t * 16 + 4 * v], a1 = x[t * 16 + 4 * v + 1];
             const float2 a2 = x[t * 16 + 4 * v + 2], a3 = x[t * 16 + 4 * v + 3];
             d0[v] = make_float4(a0.x, a1.x, a2.x, a3.x);
             d0[4 + v] = make_float4(a0.y, a1.y, a2.y, a3.y);
+        }
+    }
+#pragma unroll
+    for (int t = 0; t < NB / 16; ++t) {
+        float4* d1 = (float4*)(val + baseB + (size_t)t * kTileVals);
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
             const float2 b0 = *(const float2*)(pr + (t * 16 + 4 * v + 0) * kFullNR);
             const float2 b1 = *(const float2*)(pr + (t * 16 + 4 * v + 1) * kFullNR);
             const float2 b2 = *(const float2*)(pr + (t * 16 + 4 * v + 2) * kFullNR);
@@ -1082,18 +1127,19 @@ static cudaError_t apply_mode_t(Ctx* c, int which) {
     const std::vector<int>& ptr = MODE == 0 ? c->h_colour_ptr : c->h_ocolour_ptr;
     constexpr int CH = ApplyShape<T>::chunk;
     const int gx = (c->n_mol + CH - 1) / CH;
-    // occupied passes in FP32: blocks between two full groups take the register-resident kernel
-    const bool full = std::is_same<T, float>::value && MODE == 1 && which == 1 && c->apply_variant == 0;
+    // FP32 rotations and occupied passes: blocks between full groups take the register-resident kernel
+    const bool full = std::is_same<T, float>::value && (MODE == 0 || which == 1) && c->apply_variant == 0;
     if (full) {
-        e = cudaFuncSetAttribute(k_apply_occ_full, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)full_apply_smem());
+        e = cudaFuncSetAttribute(k_apply_full<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)full_apply_smem<MODE>());
         if (e != cudaSuccess) return e;
     }
+    const std::vector<int>& nfull = MODE == 0 ? c->h_colour_nfull : c->h_ocolour_nfull;
     const int gxf = (c->n_mol + kFullCH - 1) / kFullCH;
     for (int col = 0; col < c->n_colours; ++col) {
-        const int nf = full ? c->h_ocolour_nfull[col] : 0;
+        const int nf = full ? nfull[col] : 0;
         if (nf > 0) {
-            k_apply_occ_full<<<dim3(gxf, nf), kFullThreads, full_apply_smem(), c->stream>>>(a, ptr[col]);
+            k_apply_full<MODE><<<dim3(gxf, nf), kFullThreads, full_apply_smem<MODE>(), c->stream>>>(a, ptr[col]);
             c->n_launch += 1;
         }
         const int nb = ptr[col + 1] - ptr[col] - nf;

@@ -103,7 +103,7 @@ struct Ctx {
     std::vector<int> h_gnb_ptr, h_gnb_col, h_gnb_row, h_gnb_colour;
     std::vector<int> h_colour_ptr, h_colour_blk;        // all directed blocks by colour
     std::vector<int> h_ocolour_ptr, h_ocolour_blk;      // blocks with A <= B by colour
-    std::vector<int> h_ocolour_nfull;                   // leading blocks of each colour between two full groups
+    std::vector<int> h_colour_nfull, h_ocolour_nfull;   // leading blocks of each colour between full groups
     // tile-pair lists of the transforms
     std::vector<int> h_rot_tp_ptr;   // per a-tile CSR into (b, out) for the F_ov blocks
     std::vector<int> h_rot_tp_b, h_rot_tp_out;
