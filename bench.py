@@ -143,6 +143,24 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------------------
+def shard(items, rank: int, world: int):
+    """Independent units (clusters) of rank `rank` out of `world`: every `world`-th, starting at `rank`."""
+    return list(items)[rank::world]
+
+
+def aggregate(local_atoms: float, local_ms: float, dist=None, device=None):
+    """Whole-job atoms (sum over ranks) and the slowest rank's time (max over ranks)."""
+    if dist is None:
+        return float(local_atoms), float(local_ms)
+    import torch
+    a = torch.tensor([float(local_atoms)], dtype=torch.float64, device=device)
+    t = torch.tensor([float(local_ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(a, op=dist.ReduceOp.SUM)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(a.item()), float(t.item())
+
+
+# ---------------------------------------------------------------------------
 def main():
     args = parse()
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -190,9 +208,12 @@ def main():
 
     p = default_params()
     if args.clusters > 0:
+        # independent clusters: each rank converges its own share, no data-path collective
         from synth import cluster_sizes, concat_clusters
-        sizes = cluster_sizes()[:args.clusters]
-        s = concat_clusters([lattice_water(int(nm), seed=k) for k, nm in enumerate(sizes)])
+        if args.clusters < world:
+            raise SystemExit(f"--clusters {args.clusters} gives some of the {world} ranks no cluster")
+        mine = shard(enumerate(cluster_sizes()[:args.clusters]), rank, world)
+        s = concat_clusters([lattice_water(int(nm), seed=k) for k, nm in mine])
     else:
         s = lattice_water(args.n_mol, seed=0)
     stream = torch.cuda.Stream(dev) if args.graph else torch.cuda.current_stream(dev)
@@ -244,12 +265,8 @@ def main():
     prof = ctx.profile_read()
     ctx.profile(False)
     ms = sum(a.elapsed_time(b_) for a, b_ in ev)
-    t_max = ms
-    if dist is not None:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_max = float(t.item())
-    value = n_gpus * s.n_atoms * K / (t_max / 1e3)
+    job_atoms, t_max = aggregate(s.n_atoms, ms, dist, dev)
+    value = job_atoms * K / (t_max / 1e3)
 
     # end to end through the C-ABI: host charges in, host charges out, every step
     pinned = [torch.empty(s.n_atoms, dtype=torch.float64, pin_memory=True).numpy() for _ in range(3)]
@@ -264,12 +281,8 @@ def main():
         ctx.get_charges(out=pinned)
     torch.cuda.synchronize(dev)
     e2e_dt = time.perf_counter() - t0
-    e2e_t = e2e_dt
-    if dist is not None:
-        t = torch.tensor([e2e_dt], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_t = float(t.item())
-    e2e_value = n_gpus * s.n_atoms * K / e2e_t
+    _, e2e_t = aggregate(s.n_atoms, e2e_dt, dist, dev)
+    e2e_value = job_atoms * K / e2e_t
 
     if rank != 0:
         if dist is not None:
@@ -355,13 +368,14 @@ def main():
                                + f"{args.precision}, eps {args.eps:g}, one SCC iteration per step"
                                + (", CUDA graph" if args.graph else ""),
                    "n_mol": s.n_mol, "eps": args.eps, "precision": args.precision, "clusters": max(args.clusters, 1),
-                   "parallelism": "replicas" if n_gpus > 1 else "single",
+                   "parallelism": ("clusters sharded over ranks" if args.clusters > 0 else "replicas")
+                                  if n_gpus > 1 else "single",
                    "l2": (f"C holds {c_bytes / 1e6:.0f} MB, " + ("L2 flushed (256 MB write) before every timed step"
                                                                    if flush is not None else
                                                                    "more than twice the 129 MB L2: no flush")),
                    "prep": {"eps": args.prep_eps, "ortho_passes": prep_passes, "eta": prep_eta}},
         "scf_iter_per_s": n_gpus * K / (t_max / 1e3),
-        "cluster_iter_per_s": n_gpus * max(args.clusters, 1) * K / (t_max / 1e3),
+        "cluster_iter_per_s": (max(args.clusters, 1) if args.clusters > 0 else n_gpus) * K / (t_max / 1e3),
         "clocks": clocks,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 3 * 8 * s.n_atoms,
                 "d2h_bytes_per_step": 3 * 8 * s.n_atoms},

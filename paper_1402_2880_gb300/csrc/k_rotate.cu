@@ -793,15 +793,16 @@ __global__ void __launch_bounds__(apply_threads<T>()) k_apply_colour(SweepArgs a
 // occupied-pass combinations (MODE 1, A occupied x B occupied, A != B). The
 // in-block colour of such a block is (i + j) mod 32. Same updates, order and
 // truncation as k_apply_colour, laid out for fewer shared-memory round trips:
-// each thread owns two adjacent AO rows; the 32 A-side values of those rows
+// each thread owns kFullRPT pairs of adjacent AO rows; the 32 A-side values of those rows
 // stay in registers (the index i is static once the slot loop is unrolled),
 // the NB B-side values sit in a thread-private shared-memory panel indexed by
 // j = (level - i) mod 32. The block's pairs are expanded into a dense
 // [level][i] coefficient table with a selection mask per level. No barrier is
 // needed after the table is built: a thread reads back only the rows it wrote.
-constexpr int kFullCH = 32;                       // row blocks per CTA
+constexpr int kFullRPT = 1;                       // adjacent AO-row pairs per thread (2 measured slower)
+constexpr int kFullCH = 32 * kFullRPT;            // row blocks per CTA
 constexpr int kFullNR = kFullCH * kAoPerMol;      // AO rows per CTA (panel stride, floats)
-constexpr int kFullThreads = kFullNR / 2;
+constexpr int kFullThreads = kFullNR / (2 * kFullRPT);
 template <int MODE> struct FullShape;
 template <> struct FullShape<0> {   // rotations: B = one virtual tile, coefficients (c, c, s, s)
     static constexpr int nb = 16;
@@ -827,6 +828,7 @@ __device__ __forceinline__ void load_pair_rows(const float* src, float4 (&r0)[4]
 template <int MODE>
 __global__ void __launch_bounds__(kFullThreads) k_apply_full(SweepArgs a, int p0) {
     constexpr int NB = FullShape<MODE>::nb;
+    constexpr int RPT = kFullRPT;
     using Coef = typename FullShape<MODE>::Coef;
     extern __shared__ unsigned char smraw[];
     float* panel = (float*)smraw;                           // [NB B columns][kFullNR rows]
@@ -868,36 +870,59 @@ __global__ void __launch_bounds__(kFullThreads) k_apply_full(SweepArgs a, int p0
         atomicOr(&s_mask[lv], 1u << il);
     }
     __syncthreads();
-    const int rb = threadIdx.x / 3, k2 = 2 * (threadIdx.x - 3 * rb);
-    if (rb >= nk) return;
+    // row pair r of this thread: pair index p = threadIdx.x + r * kFullThreads,
+    // row block p / 3, AO rows 2 (p % 3) and 2 (p % 3) + 1, panel rows 2p and 2p + 1
+    if (threadIdx.x / 3 >= nk) return;
     float* val = (float*)a.out_val;   // in place
-    const int row = a.cci_row[pa + k0 + rb];
-    const size_t baseA = ((size_t)row * a.cap + a.cci_slot[pa + k0 + rb]) * kTileVals + k2 * kTileW;
-    const size_t baseB = ((size_t)row * a.cap + a.cci_slot[pb + k0 + rb]) * kTileVals + k2 * kTileW;
-    float* pr = panel + 2 * threadIdx.x;   // = 6 rb + k2: this thread's two rows
-    float2 x[32];
+    size_t baseA[RPT], baseB[RPT];
+    bool ok[RPT];
 #pragma unroll
-    for (int t = 0; t < 2; ++t) {
-        float4 u0[4], u1[4];
-        load_pair_rows(val + baseA + (size_t)t * kTileVals, u0, u1);
-#pragma unroll
-        for (int v = 0; v < 4; ++v) {
-            x[t * 16 + 4 * v + 0] = make_float2(u0[v].x, u1[v].x);
-            x[t * 16 + 4 * v + 1] = make_float2(u0[v].y, u1[v].y);
-            x[t * 16 + 4 * v + 2] = make_float2(u0[v].z, u1[v].z);
-            x[t * 16 + 4 * v + 3] = make_float2(u0[v].w, u1[v].w);
-        }
+    for (int r = 0; r < RPT; ++r) {
+        const int pp = threadIdx.x + r * kFullThreads, rb = pp / 3, k2 = 2 * (pp - 3 * rb);
+        ok[r] = rb < nk;
+        const int rr = ok[r] ? rb : 0;
+        const int row = a.cci_row[pa + k0 + rr];
+        baseA[r] = ((size_t)row * a.cap + a.cci_slot[pa + k0 + rr]) * kTileVals + k2 * kTileW;
+        baseB[r] = ((size_t)row * a.cap + a.cci_slot[pb + k0 + rr]) * kTileVals + k2 * kTileW;
     }
+    float* pr = panel + 2 * threadIdx.x;   // row pair r at pr + 2 r kFullThreads
+    float2 x[RPT][32];
 #pragma unroll
-    for (int t = 0; t < NB / 16; ++t) {
-        float4 v0[4], v1[4];
-        load_pair_rows(val + baseB + (size_t)t * kTileVals, v0, v1);
+    for (int r = 0; r < RPT; ++r) {
 #pragma unroll
-        for (int v = 0; v < 4; ++v) {
-            *(float2*)(pr + (t * 16 + 4 * v + 0) * kFullNR) = make_float2(v0[v].x, v1[v].x);
-            *(float2*)(pr + (t * 16 + 4 * v + 1) * kFullNR) = make_float2(v0[v].y, v1[v].y);
-            *(float2*)(pr + (t * 16 + 4 * v + 2) * kFullNR) = make_float2(v0[v].z, v1[v].z);
-            *(float2*)(pr + (t * 16 + 4 * v + 3) * kFullNR) = make_float2(v0[v].w, v1[v].w);
+        for (int t = 0; t < 2; ++t) {
+            float4 u0[4], u1[4];
+            if (ok[r]) {
+                load_pair_rows(val + baseA[r] + (size_t)t * kTileVals, u0, u1);
+            } else {
+#pragma unroll
+                for (int v = 0; v < 4; ++v) u0[v] = u1[v] = make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+#pragma unroll
+            for (int v = 0; v < 4; ++v) {
+                x[r][t * 16 + 4 * v + 0] = make_float2(u0[v].x, u1[v].x);
+                x[r][t * 16 + 4 * v + 1] = make_float2(u0[v].y, u1[v].y);
+                x[r][t * 16 + 4 * v + 2] = make_float2(u0[v].z, u1[v].z);
+                x[r][t * 16 + 4 * v + 3] = make_float2(u0[v].w, u1[v].w);
+            }
+        }
+#pragma unroll
+        for (int t = 0; t < NB / 16; ++t) {
+            float4 v0[4], v1[4];
+            if (ok[r]) {
+                load_pair_rows(val + baseB[r] + (size_t)t * kTileVals, v0, v1);
+            } else {
+#pragma unroll
+                for (int v = 0; v < 4; ++v) v0[v] = v1[v] = make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+            float* prr = pr + 2 * r * kFullThreads;
+#pragma unroll
+            for (int v = 0; v < 4; ++v) {
+                *(float2*)(prr + (t * 16 + 4 * v + 0) * kFullNR) = make_float2(v0[v].x, v1[v].x);
+                *(float2*)(prr + (t * 16 + 4 * v + 1) * kFullNR) = make_float2(v0[v].y, v1[v].y);
+                *(float2*)(prr + (t * 16 + 4 * v + 2) * kFullNR) = make_float2(v0[v].z, v1[v].z);
+                *(float2*)(prr + (t * 16 + 4 * v + 3) * kFullNR) = make_float2(v0[v].w, v1[v].w);
+            }
         }
     }
     const float tf = a.trunc_f;
@@ -908,45 +933,55 @@ __global__ void __launch_bounds__(kFullThreads) k_apply_full(SweepArgs a, int p0
 #pragma unroll
         for (int i = 0; i < 32; ++i) {
             if (m & (1u << i)) {
-                float2* py = (float2*)(pr + ((lv - i) & 31) * kFullNR);
+                float* py0 = pr + ((lv - i) & 31) * kFullNR;
                 const Coef c4 = cl[i];
-                const float2 y = *py;
-                float2 xn, yn;
-                if constexpr (MODE == 0) {
-                    const float2 cc = make_float2(c4.x, c4.y);
-                    xn = __ffma2_rn(cc, x[i], __fmul2_rn(make_float2(c4.z, c4.w), y));
-                    yn = __ffma2_rn(cc, y, __fmul2_rn(make_float2(-c4.z, -c4.w), x[i]));
-                } else {
-                    xn = __ffma2_rn(c4, y, x[i]);
-                    yn = __ffma2_rn(c4, x[i], y);
+                float2 y[RPT];
+#pragma unroll
+                for (int r = 0; r < RPT; ++r) y[r] = *(const float2*)(py0 + 2 * r * kFullThreads);
+#pragma unroll
+                for (int r = 0; r < RPT; ++r) {
+                    float2 xn, yn;
+                    if constexpr (MODE == 0) {
+                        const float2 cc = make_float2(c4.x, c4.y);
+                        xn = __ffma2_rn(cc, x[r][i], __fmul2_rn(make_float2(c4.z, c4.w), y[r]));
+                        yn = __ffma2_rn(cc, y[r], __fmul2_rn(make_float2(-c4.z, -c4.w), x[r][i]));
+                    } else {
+                        xn = __ffma2_rn(c4, y[r], x[r][i]);
+                        yn = __ffma2_rn(c4, x[r][i], y[r]);
+                    }
+                    x[r][i] = trunc2(xn, tf);
+                    *(float2*)(py0 + 2 * r * kFullThreads) = trunc2(yn, tf);
                 }
-                x[i] = trunc2(xn, tf);
-                *py = trunc2(yn, tf);
             }
         }
     }
 #pragma unroll
-    for (int t = 0; t < 2; ++t) {
-        float4* d0 = (float4*)(val + baseA + (size_t)t * kTileVals);
+    for (int r = 0; r < RPT; ++r) {
+        if (!ok[r]) continue;
 #pragma unroll
-        for (int v = 0; v < 4; ++v) {
-            const float2 a0 = x[t * 16 + 4 * v], a1 = x[t * 16 + 4 * v + 1];
-            const float2 a2 = x[t * 16 + 4 * v + 2], a3 = x[t * 16 + 4 * v + 3];
-            d0[v] = make_float4(a0.x, a1.x, a2.x, a3.x);
-            d0[4 + v] = make_float4(a0.y, a1.y, a2.y, a3.y);
+        for (int t = 0; t < 2; ++t) {
+            float4* d0 = (float4*)(val + baseA[r] + (size_t)t * kTileVals);
+#pragma unroll
+            for (int v = 0; v < 4; ++v) {
+                const float2 a0 = x[r][t * 16 + 4 * v], a1 = x[r][t * 16 + 4 * v + 1];
+                const float2 a2 = x[r][t * 16 + 4 * v + 2], a3 = x[r][t * 16 + 4 * v + 3];
+                d0[v] = make_float4(a0.x, a1.x, a2.x, a3.x);
+                d0[4 + v] = make_float4(a0.y, a1.y, a2.y, a3.y);
+            }
         }
-    }
+        const float* prr = pr + 2 * r * kFullThreads;
 #pragma unroll
-    for (int t = 0; t < NB / 16; ++t) {
-        float4* d1 = (float4*)(val + baseB + (size_t)t * kTileVals);
+        for (int t = 0; t < NB / 16; ++t) {
+            float4* d1 = (float4*)(val + baseB[r] + (size_t)t * kTileVals);
 #pragma unroll
-        for (int v = 0; v < 4; ++v) {
-            const float2 b0 = *(const float2*)(pr + (t * 16 + 4 * v + 0) * kFullNR);
-            const float2 b1 = *(const float2*)(pr + (t * 16 + 4 * v + 1) * kFullNR);
-            const float2 b2 = *(const float2*)(pr + (t * 16 + 4 * v + 2) * kFullNR);
-            const float2 b3 = *(const float2*)(pr + (t * 16 + 4 * v + 3) * kFullNR);
-            d1[v] = make_float4(b0.x, b1.x, b2.x, b3.x);
-            d1[4 + v] = make_float4(b0.y, b1.y, b2.y, b3.y);
+            for (int v = 0; v < 4; ++v) {
+                const float2 b0 = *(const float2*)(prr + (t * 16 + 4 * v + 0) * kFullNR);
+                const float2 b1 = *(const float2*)(prr + (t * 16 + 4 * v + 1) * kFullNR);
+                const float2 b2 = *(const float2*)(prr + (t * 16 + 4 * v + 2) * kFullNR);
+                const float2 b3 = *(const float2*)(prr + (t * 16 + 4 * v + 3) * kFullNR);
+                d1[v] = make_float4(b0.x, b1.x, b2.x, b3.x);
+                d1[4 + v] = make_float4(b0.y, b1.y, b2.y, b3.y);
+            }
         }
     }
 }
