@@ -52,6 +52,10 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--clusters", type=int, default=0,
                     help="batched workload: the first K clusters of the seed-7 size draw U[200, 3000] in one context")
+    ap.add_argument("--wave", type=int, default=0,
+                    help="batched workload: clusters per context, contexts run one after another (0: all in one)")
+    ap.add_argument("--cap-tiles", type=int, default=0, help="tiles per row of C (0: the largest cluster's tiles)")
+    ap.add_argument("--cap-y", type=int, default=0, help="row blocks per tile of Y (0: the largest cluster)")
     ap.add_argument("--graph", action="store_true", help="replay each SCC iteration as one CUDA graph")
     return ap.parse_args()
 
@@ -213,76 +217,100 @@ def main():
         if args.clusters < world:
             raise SystemExit(f"--clusters {args.clusters} gives some of the {world} ranks no cluster")
         mine = shard(enumerate(cluster_sizes()[:args.clusters]), rank, world)
-        s = concat_clusters([lattice_water(int(nm), seed=k) for k, nm in mine])
+        w = args.wave if args.wave > 0 else len(mine)
+        systems = [concat_clusters([lattice_water(int(nm), seed=k) for k, nm in mine[i:i + w]])
+                   for i in range(0, len(mine), w)]
     else:
-        s = lattice_water(args.n_mol, seed=0)
+        systems = [lattice_water(args.n_mol, seed=0)]
     stream = torch.cuda.Stream(dev) if args.graph else torch.cuda.current_stream(dev)
     prec = SSCF_MIXED if args.precision == "mixed" else SSCF_FP64
-    ctx = Context.from_system(s, p, precision=prec, stream=stream.cuda_stream)
-    # input state
-    ctx.set_thresholds(args.prep_eps, 10 * args.prep_eps, 1e-8)
-    ctx.guess()
-    prep_passes, prep_eta = ctx.orthonormalise(SSCF_ORTHO_ALL, max_pass=args.prep_passes)
-    ctx.set_thresholds(args.eps, 10 * args.eps, 1e-6)
-    ctx.reset_charges()
-    if args.graph:
-        ctx.enable_graph(True)
-    warm = None
-    for _ in range(max(args.warmup, 0)):
-        warm = ctx.step()
-    torch.cuda.synchronize(dev)
-    # C below twice the 129 MB L2: flush L2 between timed steps (outside the events)
-    tsz = 4 if prec == SSCF_MIXED else 8
-    c_bytes = tsz * (warm["nnz_c"] if warm else s.n_ao * 16)
-    flush = torch.empty(64 << 20, dtype=torch.float32, device=dev) if c_bytes < 2 * L2_BYTES else None
-
     K = args.steps
-    ctx.profile(True)
+    flush = None
+
+    def run_one(s):
+        """Prepare one context (untimed), warm up, time K steps, then K end-to-end steps."""
+        nonlocal flush
+        ctx = Context.from_system(s, p, precision=prec, stream=stream.cuda_stream, cap_tiles=args.cap_tiles,
+                                  cap_y=args.cap_y)
+        ctx.set_thresholds(args.prep_eps, 10 * args.prep_eps, 1e-8)
+        ctx.guess()
+        prep = ctx.orthonormalise(SSCF_ORTHO_ALL, max_pass=args.prep_passes)
+        ctx.set_thresholds(args.eps, 10 * args.eps, 1e-6)
+        ctx.reset_charges()
+        if args.graph:
+            ctx.enable_graph(True)
+        warm = None
+        for _ in range(max(args.warmup, 0)):
+            warm = ctx.step()
+        torch.cuda.synchronize(dev)
+        # C below twice the 129 MB L2: flush L2 between timed steps (outside the events)
+        c_bytes = (4 if prec == SSCF_MIXED else 8) * (warm["nnz_c"] if warm else s.n_ao * 16)
+        flushing = c_bytes < 2 * L2_BYTES
+        if flushing and flush is None:
+            flush = torch.empty(64 << 20, dtype=torch.float32, device=dev)
+        ctx.profile(True)
+        infos = []
+        torch.cuda.synchronize(dev)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(K if flushing else 1)]
+        if not flushing:
+            ev[0][0].record(stream)
+        for k in range(K):
+            if flushing:
+                with torch.cuda.stream(stream):
+                    flush.zero_()
+                ev[k][0].record(stream)
+            infos.append(ctx.step())
+            if flushing:
+                ev[k][1].record(stream)
+        if not flushing:
+            ev[0][1].record(stream)
+        torch.cuda.synchronize(dev)
+        prof = ctx.profile_read()
+        ctx.profile(False)
+        ms = sum(a.elapsed_time(b_) for a, b_ in ev)
+        # end to end through the C-ABI: host charges in, host charges out, every step
+        pinned = [torch.empty(s.n_atoms, dtype=torch.float64, pin_memory=True).numpy() for _ in range(3)]
+        for a_, b_ in zip(pinned, ctx.get_charges()):
+            a_[:] = b_
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        for _ in range(K):
+            ctx.set_charges(*pinned)
+            ctx.step()
+            ctx.get_charges(out=pinned)
+        torch.cuda.synchronize(dev)
+        e2e_dt = time.perf_counter() - t0
+        n_mo = ctx.n_mo
+        ctx.close()
+        return dict(ms=ms, infos=infos, prof=prof, e2e_dt=e2e_dt, prep=prep, c_bytes=c_bytes,
+                    flushing=flushing, n_mo=n_mo)
+
     sampler = ClockSampler(local_rank)
     sampler.start()
-    infos = []
     if dist is not None:
         dist.barrier()
-    torch.cuda.synchronize(dev)
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-          for _ in range(K if flush is not None else 1)]
-    if flush is None:
-        ev[0][0].record(stream)
-    for k in range(K):
-        if flush is not None:
-            with torch.cuda.stream(stream):
-                flush.zero_()
-            ev[k][0].record(stream)
-        infos.append(ctx.step())
-        if flush is not None:
-            ev[k][1].record(stream)
-    if flush is None:
-        ev[0][1].record(stream)
-    torch.cuda.synchronize(dev)
+    runs = [run_one(s) for s in systems]
     if dist is not None:
         dist.barrier()
     clocks = sampler.stop()
-    prof = ctx.profile_read()
-    ctx.profile(False)
-    ms = sum(a.elapsed_time(b_) for a, b_ in ev)
-    job_atoms, t_max = aggregate(s.n_atoms, ms, dist, dev)
+    n_atoms_local = sum(s.n_atoms for s in systems)
+    n_mol_local = sum(s.n_mol for s in systems)
+    ms = sum(r["ms"] for r in runs)
+    job_atoms, t_max = aggregate(n_atoms_local, ms, dist, dev)
     value = job_atoms * K / (t_max / 1e3)
-
-    # end to end through the C-ABI: host charges in, host charges out, every step
-    pinned = [torch.empty(s.n_atoms, dtype=torch.float64, pin_memory=True).numpy() for _ in range(3)]
-    q, dq, Q = ctx.get_charges()
-    for a_, b_ in zip(pinned, (q, dq, Q)):
-        a_[:] = b_
-    torch.cuda.synchronize(dev)
-    t0 = time.perf_counter()
-    for _ in range(K):
-        ctx.set_charges(*pinned)
-        ctx.step()
-        ctx.get_charges(out=pinned)
-    torch.cuda.synchronize(dev)
-    e2e_dt = time.perf_counter() - t0
-    _, e2e_t = aggregate(s.n_atoms, e2e_dt, dist, dev)
+    _, e2e_t = aggregate(n_atoms_local, sum(r["e2e_dt"] for r in runs), dist, dev)
     e2e_value = job_atoms * K / e2e_t
+    infos = [inf for r in runs for inf in r["infos"]]
+    prof = {}
+    for r in runs:
+        for k_, (t_, n_) in r["prof"].items():
+            t0_, n0_ = prof.get(k_, (0.0, 0))
+            prof[k_] = (t0_ + t_, n0_ + n_)
+    prep_passes, prep_eta = runs[0]["prep"]
+    c_bytes = max(r["c_bytes"] for r in runs)
+    flushed = any(r["flushing"] for r in runs)
+    n_mo_local = sum(r["n_mo"] for r in runs)
 
     if rank != 0:
         if dist is not None:
@@ -291,7 +319,8 @@ def main():
 
     # roofline of the dominant launcher: algorithmic HBM bytes per call / mean call time
     tsz = 4 if prec == SSCF_MIXED else 8
-    mean = lambda k: float(np.mean([inf[k] for inf in infos]))  # noqa: E731
+    # per-step quantities summed over the waves
+    mean = lambda k: float(np.mean([inf[k] for inf in infos])) * len(runs)  # noqa: E731
     nnz_c, nnz_o = mean("nnz_c"), mean("nnz_occ")
     n_rot, n_combo = mean("n_rot"), mean("n_combo")
     algo_bytes = {
@@ -301,7 +330,7 @@ def main():
         "xc_s": 2 * tsz * nnz_o,
         "transform_ov": 2 * tsz * nnz_c,                      # read C and Y once
         "transform_ss": 2 * tsz * nnz_o,
-        "density": tsz * nnz_o + 8 * s.n_atoms,
+        "density": tsz * nnz_o + 8 * n_atoms_local,
         "closure": 2 * tsz * nnz_c,
         "compact": 2 * tsz * nnz_c,
     }
@@ -363,28 +392,30 @@ def main():
         "ms_per_step": t_max / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32+f64" if prec == SSCF_MIXED else "f64", "data": "synthetic",
         "config": {"workload": (f"batch of {args.clusters} independent water-lattice clusters "
-                                f"({s.n_mol} molecules, {s.n_atoms} atoms), " if args.clusters > 0 else
-                                f"water lattice {args.n_mol} molecules ({s.n_atoms} atoms, {6 * args.n_mol} AOs), ")
+                                f"({n_mol_local} molecules, {n_atoms_local} atoms"
+                                + (f", {len(runs)} waves of {args.wave}" if len(runs) > 1 else "") + "), "
+                                if args.clusters > 0 else
+                                f"water lattice {args.n_mol} molecules ({n_atoms_local} atoms, {6 * args.n_mol} AOs), ")
                                + f"{args.precision}, eps {args.eps:g}, one SCC iteration per step"
                                + (", CUDA graph" if args.graph else ""),
-                   "n_mol": s.n_mol, "eps": args.eps, "precision": args.precision, "clusters": max(args.clusters, 1),
+                   "n_mol": n_mol_local, "eps": args.eps, "precision": args.precision, "clusters": max(args.clusters, 1),
                    "parallelism": ("clusters sharded over ranks" if args.clusters > 0 else "replicas")
                                   if n_gpus > 1 else "single",
                    "l2": (f"C holds {c_bytes / 1e6:.0f} MB, " + ("L2 flushed (256 MB write) before every timed step"
-                                                                   if flush is not None else
+                                                                   if flushed else
                                                                    "more than twice the 129 MB L2: no flush")),
                    "prep": {"eps": args.prep_eps, "ortho_passes": prep_passes, "eta": prep_eta}},
         "scf_iter_per_s": n_gpus * K / (t_max / 1e3),
         "cluster_iter_per_s": (max(args.clusters, 1) if args.clusters > 0 else n_gpus) * K / (t_max / 1e3),
         "clocks": clocks,
-        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 3 * 8 * s.n_atoms,
-                "d2h_bytes_per_step": 3 * 8 * s.n_atoms},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 3 * 8 * n_atoms_local,
+                "d2h_bytes_per_step": 3 * 8 * n_atoms_local},
         "gpu_launches": launches * K,
         "roofline": roofline,
         "kernels": kernels,
         "cpu_baseline": cpu,
         "state": {"energy": infos[-1]["energy"], "dq_max": infos[-1]["dq_max"], "n_rot": n_rot,
-                  "n_combo": n_combo, "nnz_per_mo": nnz_c / ctx.n_mo},
+                  "n_combo": n_combo, "nnz_per_mo": nnz_c / n_mo_local},
     }
     print(json.dumps(line), flush=True)
     if dist is not None:

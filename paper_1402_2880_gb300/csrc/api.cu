@@ -88,26 +88,31 @@ int build_structure(Ctx& c, const sscf_system* sys) {
         rmax = std::max(rmax, rad[m]);
     }
     const double rc2 = c.prm.r_cut * c.prm.r_cut;
-    CellGrid grid;
-    grid.build(ox, nM, c.prm.r_cut + 2.0 * rmax + 1e-9);
     std::vector<std::vector<int>> nbm(nM);
-    for (int m = 0; m < nM; ++m) {
-        int cx = grid.coord(&ox[3 * m], 0), cy = grid.coord(&ox[3 * m], 1), cz = grid.coord(&ox[3 * m], 2);
-        for (int dz = -1; dz <= 1; ++dz)
-            for (int dy = -1; dy <= 1; ++dy)
-                for (int dx = -1; dx <= 1; ++dx) {
-                    int x = cx + dx, y = cy + dy, z = cz + dz;
-                    if (x < 0 || y < 0 || z < 0 || x >= grid.n[0] || y >= grid.n[1] || z >= grid.n[2]) continue;
-                    for (int n = grid.head[x + grid.n[0] * (y + grid.n[1] * z)]; n >= 0; n = grid.next[n]) {
-                        if (c.h_mol_cluster[n] != c.h_mol_cluster[m]) continue;
-                        bool hit = (n == m);
-                        for (int a = 0; a < 3 && !hit; ++a)
-                            for (int b = 0; b < 3 && !hit; ++b)
-                                if (dist2(&X[3 * (3 * m + a)], &X[3 * (3 * n + b)]) <= rc2) hit = true;
-                        if (hit) nbm[m].push_back(n);
+    // clusters never couple: one cell grid per cluster (molecules of a cluster are consecutive)
+    for (int k = 0; k < c.n_clusters; ++k) {
+        const int m0 = c.h_cl_mol0[k], nk = c.h_cl_nmol[k];
+        std::vector<double> oxk(ox.begin() + 3 * (size_t)m0, ox.begin() + 3 * (size_t)(m0 + nk));
+        CellGrid grid;
+        grid.build(oxk, nk, c.prm.r_cut + 2.0 * rmax + 1e-9);
+        for (int m = m0; m < m0 + nk; ++m) {
+            int cx = grid.coord(&ox[3 * m], 0), cy = grid.coord(&ox[3 * m], 1), cz = grid.coord(&ox[3 * m], 2);
+            for (int dz = -1; dz <= 1; ++dz)
+                for (int dy = -1; dy <= 1; ++dy)
+                    for (int dx = -1; dx <= 1; ++dx) {
+                        int x = cx + dx, y = cy + dy, z = cz + dz;
+                        if (x < 0 || y < 0 || z < 0 || x >= grid.n[0] || y >= grid.n[1] || z >= grid.n[2]) continue;
+                        for (int nl = grid.head[x + grid.n[0] * (y + grid.n[1] * z)]; nl >= 0; nl = grid.next[nl]) {
+                            const int n = m0 + nl;
+                            bool hit = (n == m);
+                            for (int a = 0; a < 3 && !hit; ++a)
+                                for (int b = 0; b < 3 && !hit; ++b)
+                                    if (dist2(&X[3 * (3 * m + a)], &X[3 * (3 * n + b)]) <= rc2) hit = true;
+                            if (hit) nbm[m].push_back(n);
+                        }
                     }
-                }
-        std::sort(nbm[m].begin(), nbm[m].end());
+            std::sort(nbm[m].begin(), nbm[m].end());
+        }
     }
     c.h_mp_ptr.assign(nM + 1, 0);
     for (int m = 0; m < nM; ++m) c.h_mp_ptr[m + 1] = c.h_mp_ptr[m] + (int)nbm[m].size();
@@ -190,26 +195,35 @@ int build_structure(Ctx& c, const sscf_system* sys) {
     }
     double gmax = *std::max_element(grad.begin(), grad.end());
     const double gc2 = c.prm.group_cut * c.prm.group_cut;
-    CellGrid gg;
-    gg.build(gc, G, c.prm.group_cut + 2.0 * gmax + 1e-9);
+    // groups of a cluster are consecutive (checked above): one cell grid per cluster
+    c.h_cl_g0.assign(c.n_clusters + 1, G);
+    for (int g = G - 1; g >= 0; --g) c.h_cl_g0[c.h_mol_cluster[mols[g][0]]] = g;
+    for (int k = c.n_clusters - 1; k >= 0; --k) c.h_cl_g0[k] = std::min(c.h_cl_g0[k], c.h_cl_g0[k + 1]);
     std::vector<std::vector<int>> gnb(G);
-    for (int A = 0; A < G; ++A) {
-        int cx = gg.coord(&gc[3 * A], 0), cy = gg.coord(&gc[3 * A], 1), cz = gg.coord(&gc[3 * A], 2);
-        for (int dz = -1; dz <= 1; ++dz)
-            for (int dy = -1; dy <= 1; ++dy)
-                for (int dx = -1; dx <= 1; ++dx) {
-                    int x = cx + dx, y = cy + dy, z = cz + dz;
-                    if (x < 0 || y < 0 || z < 0 || x >= gg.n[0] || y >= gg.n[1] || z >= gg.n[2]) continue;
-                    for (int B = gg.head[x + gg.n[0] * (y + gg.n[1] * z)]; B >= 0; B = gg.next[B]) {
-                        if (c.h_mol_cluster[mols[B][0]] != c.h_mol_cluster[mols[A][0]]) continue;
-                        bool hit = (A == B);
-                        for (size_t i = 0; i < gatoms[A].size() && !hit; ++i)
-                            for (size_t j = 0; j < gatoms[B].size() && !hit; ++j)
-                                if (dist2(&X[3 * gatoms[A][i]], &X[3 * gatoms[B][j]]) < gc2) hit = true;
-                        if (hit) gnb[A].push_back(B);
+    for (int k = 0; k < c.n_clusters; ++k) {
+        const int g0 = c.h_cl_g0[k], ng = c.h_cl_g0[k + 1] - g0;
+        if (ng <= 0) continue;
+        std::vector<double> gck(gc.begin() + 3 * (size_t)g0, gc.begin() + 3 * (size_t)(g0 + ng));
+        CellGrid gg;
+        gg.build(gck, ng, c.prm.group_cut + 2.0 * gmax + 1e-9);
+        for (int A = g0; A < g0 + ng; ++A) {
+            int cx = gg.coord(&gc[3 * A], 0), cy = gg.coord(&gc[3 * A], 1), cz = gg.coord(&gc[3 * A], 2);
+            for (int dz = -1; dz <= 1; ++dz)
+                for (int dy = -1; dy <= 1; ++dy)
+                    for (int dx = -1; dx <= 1; ++dx) {
+                        int x = cx + dx, y = cy + dy, z = cz + dz;
+                        if (x < 0 || y < 0 || z < 0 || x >= gg.n[0] || y >= gg.n[1] || z >= gg.n[2]) continue;
+                        for (int Bl = gg.head[x + gg.n[0] * (y + gg.n[1] * z)]; Bl >= 0; Bl = gg.next[Bl]) {
+                            const int B = g0 + Bl;
+                            bool hit = (A == B);
+                            for (size_t i = 0; i < gatoms[A].size() && !hit; ++i)
+                                for (size_t j = 0; j < gatoms[B].size() && !hit; ++j)
+                                    if (dist2(&X[3 * gatoms[A][i]], &X[3 * gatoms[B][j]]) < gc2) hit = true;
+                            if (hit) gnb[A].push_back(B);
+                        }
                     }
-                }
-        std::sort(gnb[A].begin(), gnb[A].end());
+            std::sort(gnb[A].begin(), gnb[A].end());
+        }
     }
     // ---- greedy first-fit edge colouring, edges {A < B} in lexicographic order ----
     std::vector<std::vector<char>> used(G);
@@ -592,7 +606,10 @@ int sscf_create(const sscf_system* sys, const sscf_params* prm, void* cuda_strea
     }
     c.cap = prm->cap_tiles > 0 ? std::min(prm->cap_tiles, c.max_cl_tiles) : c.max_cl_tiles;
     c.cap = std::max(c.cap, 2);
-    if (c.n_tiles > 32768) {   // tile ids and slots are packed into 16 bits in the sweep kernel
+    c.max_cl_groups = 0;
+    for (int k = 0; k < c.n_clusters; ++k) c.max_cl_groups = std::max(c.max_cl_groups, c.h_cl_g0[k + 1] - c.h_cl_g0[k]);
+    // the closure keeps the old slot of every tile of the row's cluster as a 16-bit value in shared memory
+    if (c.cap > 32767 || closure_smem_bytes(&c) > (size_t)kMaxDynSmem) {
         delete h;
         return SSCF_ERR_INVALID_ARG;
     }
@@ -656,6 +673,27 @@ int sscf_create(const sscf_system* sys, const sscf_params* prm, void* cuda_strea
         UP(c.d_mol_row0, mol_row0);
         UP(c.d_mol_ot0, mol_ot0);
         UP(c.d_mol_cluster, c.h_mol_cluster);
+        UP(c.d_cl_g0, c.h_cl_g0);
+        std::vector<int> cot(c.n_clusters + 1), cvt(c.n_clusters + 1);
+        for (int k = 0; k <= c.n_clusters; ++k) {
+            const int g = c.h_cl_g0[k];
+            cot[k] = g < c.n_groups ? c.h_group_ot0[g] : c.n_occ_tiles;
+            cvt[k] = g < c.n_groups ? c.h_group_vt0[g] : c.n_tiles;
+        }
+        UP(c.d_cl_ot0, cot);
+        UP(c.d_cl_vt0, cvt);
+        // blocks by cluster: gnb entries run over A, and groups over clusters, so
+        // the blocks of a cluster are consecutive in both lists
+        for (int w = 0; w < 2; ++w) {
+            std::vector<int> ptr(c.n_clusters + 1, 0), blk;
+            for (int k = 0; k < c.n_clusters; ++k) {
+                for (int e = c.h_gnb_ptr[c.h_cl_g0[k]]; e < c.h_gnb_ptr[c.h_cl_g0[k + 1]]; ++e)
+                    if (w == 0 || c.h_gnb_row[e] <= c.h_gnb_col[e]) blk.push_back(e);
+                ptr[k + 1] = (int)blk.size();
+            }
+            UP(c.d_clblk_ptr[w], ptr);
+            UP(c.d_clblk[w], blk);
+        }
         UP(c.d_atom_lo, lo);
         UP(c.d_atom_hi, hi);
         UP(c.d_cl_mol0, c.h_cl_mol0);

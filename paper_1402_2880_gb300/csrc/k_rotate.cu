@@ -380,10 +380,16 @@ __global__ void k_ortho_lists(int w, double tol, const int* __restrict__ oblk, c
 struct SweepArgs {
     int mode;        // 0 rotations (A occupied | B virtual), 1 combinations
     int which;       // combinations: 0 all MOs, 1 occupied MOs
-    int n_tiles, n_groups, cap, n_blk;
+    int n_tiles, n_occ_tiles, n_groups, cap, n_blk, max_cl_groups;
     double trunc;
     float trunc_f;   // smallest float >= trunc: |x| < trunc <=> |x| < trunc_f for every float x
-    const int* blk;          // blocks of the pass (any order for the closure)
+    const int* blk;          // blocks of the pass by colour
+    const int* mol_cluster;  // closure: cluster of every row block
+    const int* cl_g0;        // closure: first group, occupied tile and virtual tile of every cluster
+    const int* cl_ot0;
+    const int* cl_vt0;
+    const int* clblk_ptr;    // closure: blocks of the pass by cluster
+    const int* clblk;
     const int* gnb_row;
     const int* gnb_col;
     const int* group_nmol;
@@ -423,21 +429,28 @@ static_assert(sizeof(float) == 4, "");
 template <typename T>
 __global__ void __launch_bounds__(256) k_closure(SweepArgs a) {
     extern __shared__ unsigned char smraw[];
-    const int gw = (a.n_groups + 31) >> 5;
+    // everything a row block touches belongs to its own cluster: group bits and
+    // the tile map are indexed inside the cluster's ranges
+    const int r = blockIdx.x;
+    const int k = a.mol_cluster[r];
+    const int g0 = a.cl_g0[k], ng = a.cl_g0[k + 1] - g0;
+    const int ot0 = a.cl_ot0[k], not_ = a.cl_ot0[k + 1] - ot0;
+    const int vt0 = a.cl_vt0[k], nvt = a.cl_vt0[k + 1] - vt0;
+    const int gw = (a.max_cl_groups + 31) >> 5;
     unsigned* occ = (unsigned*)smraw;
     unsigned* vir = occ + gw;
-    short* map = (short*)(vir + gw);             // n_tiles: old slot or -1
+    short* map = (short*)(vir + gw);             // tiles of the cluster (occupied, then virtual): old slot or -1
+    auto lt = [&](int t) { return t < a.n_occ_tiles ? t - ot0 : not_ + (t - vt0); };
     __shared__ int part[256];
     __shared__ int s_total;
-    const int r = blockIdx.x;
     for (int i = threadIdx.x; i < gw; i += blockDim.x) occ[i] = vir[i] = 0u;
-    for (int i = threadIdx.x; i < a.n_tiles; i += blockDim.x) map[i] = -1;
+    for (int i = threadIdx.x; i < not_ + nvt; i += blockDim.x) map[i] = -1;
     __syncthreads();
     const int n0 = a.in_nt[r];
     for (int s = threadIdx.x; s < n0; s += blockDim.x) {
         const int t = a.in_tile[(size_t)r * a.cap + s];
-        map[t] = (short)s;
-        const int g = a.tile_group[t];
+        map[lt(t)] = (short)s;
+        const int g = a.tile_group[t] - g0;
         const unsigned bit = 1u << (g & 31);
         if (a.mode == 1 && a.which == 0) {
             atomicOr(&occ[g >> 5], bit);
@@ -449,12 +462,13 @@ __global__ void __launch_bounds__(256) k_closure(SweepArgs a) {
         }
     }
     __syncthreads();
+    const int jb0 = a.clblk_ptr[k], jb1 = a.clblk_ptr[k + 1];
     for (int it = 0; it < kClosureIters; ++it) {
         int changed = 0;
-        for (int j = threadIdx.x; j < a.n_blk; j += blockDim.x) {
-            const int e = a.blk[j];
+        for (int j = jb0 + threadIdx.x; j < jb1; j += blockDim.x) {
+            const int e = a.clblk[j];
             if (a.pr_n[e] == 0) continue;
-            const int A = a.gnb_row[e], B = a.gnb_col[e];
+            const int A = a.gnb_row[e] - g0, B = a.gnb_col[e] - g0;
             const unsigned ba = 1u << (A & 31), bb = 1u << (B & 31);
             const bool ha = (occ[A >> 5] & ba) != 0;
             const bool hb = a.mode == 0 ? (vir[B >> 5] & bb) != 0 : (occ[B >> 5] & bb) != 0;
@@ -474,13 +488,13 @@ __global__ void __launch_bounds__(256) k_closure(SweepArgs a) {
         if (!__syncthreads_or(changed)) break;
     }
     // new sorted tile list: occupied units by group, then virtual units
-    const int per = (2 * a.n_groups + blockDim.x - 1) / blockDim.x;
-    const int u0 = threadIdx.x * per, u1 = min(2 * a.n_groups, u0 + per);
+    const int per = (2 * ng + blockDim.x - 1) / blockDim.x;
+    const int u0 = threadIdx.x * per, u1 = min(2 * ng, u0 + per);
     int cnt = 0;
     for (int u = u0; u < u1; ++u) {
-        const int g = u < a.n_groups ? u : u - a.n_groups;
-        const bool on = u < a.n_groups ? (occ[g >> 5] >> (g & 31)) & 1 : (vir[g >> 5] >> (g & 31)) & 1;
-        if (on) cnt += u < a.n_groups ? a.group_not[g] : a.group_nvt[g];
+        const int g = u < ng ? u : u - ng;
+        const bool on = u < ng ? (occ[g >> 5] >> (g & 31)) & 1 : (vir[g >> 5] >> (g & 31)) & 1;
+        if (on) cnt += u < ng ? a.group_not[g0 + g] : a.group_nvt[g0 + g];
     }
     part[threadIdx.x] = cnt;
     __syncthreads();
@@ -501,11 +515,11 @@ __global__ void __launch_bounds__(256) k_closure(SweepArgs a) {
     }
     int pos = part[threadIdx.x];
     for (int u = u0; u < u1; ++u) {
-        const int g = u < a.n_groups ? u : u - a.n_groups;
-        const bool on = u < a.n_groups ? (occ[g >> 5] >> (g & 31)) & 1 : (vir[g >> 5] >> (g & 31)) & 1;
+        const int g = u < ng ? u : u - ng;
+        const bool on = u < ng ? (occ[g >> 5] >> (g & 31)) & 1 : (vir[g >> 5] >> (g & 31)) & 1;
         if (!on) continue;
-        const int t0 = u < a.n_groups ? a.group_ot0[g] : a.group_vt0[g];
-        const int nt = u < a.n_groups ? a.group_not[g] : a.group_nvt[g];
+        const int t0 = u < ng ? a.group_ot0[g0 + g] : a.group_vt0[g0 + g];
+        const int nt = u < ng ? a.group_not[g0 + g] : a.group_nvt[g0 + g];
         for (int i = 0; i < nt; ++i) a.out_tile[(size_t)r * a.cap + pos++] = t0 + i;
     }
     if (threadIdx.x == 0) a.out_nt[r] = n1;
@@ -515,7 +529,7 @@ __global__ void __launch_bounds__(256) k_closure(SweepArgs a) {
     for (int idx = threadIdx.x; idx < n1 * kTileVals; idx += blockDim.x) {
         const int s = idx / kTileVals, e = idx % kTileVals, col = e & 15;
         const int t = a.out_tile[(size_t)r * a.cap + s];
-        const int os = map[t];
+        const int os = map[lt(t)];
         T v = os >= 0 ? inv[((size_t)r * a.cap + os) * kTileVals + e] : (T)0;
         if (a.mode == 1 && os >= 0 && (a.which == 0 || a.tile_kind[t] == 0) && col < a.tile_nmo[t])
             v = v / (T)a.dsc[a.tile_mo0[t] + col];
@@ -523,9 +537,6 @@ __global__ void __launch_bounds__(256) k_closure(SweepArgs a) {
     }
 }
 
-size_t closure_smem_bytes(const Ctx* c) {
-    return (size_t)2 * ((c->n_groups + 31) / 32) * 4 + (size_t)((c->n_tiles + 1) & ~1) * 2 + 16;
-}
 
 // side tiles of a block: up to 3 per side, as (first tile of a run, offset)
 struct Side {
@@ -1033,6 +1044,10 @@ __global__ void k_compact(int cap, const int* __restrict__ in_nt, const int* __r
 
 }  // namespace
 
+size_t closure_smem_bytes(const Ctx* c) {
+    return (size_t)2 * ((c->max_cl_groups + 31) / 32) * 4 + (size_t)((c->max_cl_tiles + 1) & ~1) * 2 + 16;
+}
+
 // --------------------------------------------------------------------------
 // launchers
 // --------------------------------------------------------------------------
@@ -1098,7 +1113,15 @@ static void fill_args(Ctx* c, SweepArgs& a, int mode, int which) {
     a.mode = mode;
     a.which = which;
     a.n_tiles = c->n_tiles;
+    a.n_occ_tiles = c->n_occ_tiles;
     a.n_groups = c->n_groups;
+    a.max_cl_groups = c->max_cl_groups;
+    a.mol_cluster = c->d_mol_cluster;
+    a.cl_g0 = c->d_cl_g0;
+    a.cl_ot0 = c->d_cl_ot0;
+    a.cl_vt0 = c->d_cl_vt0;
+    a.clblk_ptr = c->d_clblk_ptr[mode == 0 ? 0 : 1];
+    a.clblk = c->d_clblk[mode == 0 ? 0 : 1];
     a.cap = c->cap;
     a.n_blk = mode == 0 ? c->n_gnb : (int)c->h_ocolour_blk.size();
     a.trunc = mode == 0 ? c->prm.eps : 1e-3 * c->prm.eps;
@@ -1140,7 +1163,7 @@ static cudaError_t closure_t(Ctx* c, int mode, int which) {
     a.out_tile = c->d_c_tile[out];
     a.out_val = c->d_c_val[out];
     const size_t smem = closure_smem_bytes(c);
-    if (smem > 200 * 1024) return cudaErrorInvalidValue;
+    if (smem > (size_t)kMaxDynSmem) return cudaErrorInvalidValue;
     cudaError_t e = cudaFuncSetAttribute(k_closure<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     k_closure<T><<<c->n_mol, 256, smem, c->stream>>>(a);

@@ -33,6 +33,7 @@ constexpr int kAoPerMol = 6;
 constexpr int kTileW = 16;
 constexpr int kTileVals = kAoPerMol * kTileW;  // 96
 constexpr int kMaxMolPerGroup = 8;
+constexpr int kMaxDynSmem = 227 * 1024;          // dynamic shared memory a CTA may opt into
 constexpr int kMaxSub = 48;                    // in-block colours (<= MOs per group side)
 constexpr int kRotCap = 32 * 16;               // pairs of one occupied-virtual block
 constexpr int kOrthoCap = 48 * 48;             // pairs of one orthonormalisation block
@@ -96,6 +97,8 @@ struct Ctx {
     std::vector<double> h_xyz;
     std::vector<int> h_mol_group, h_mol_local, h_mol_cluster;
     std::vector<int> h_cl_mol0, h_cl_nmol;    // molecule range of every cluster
+    std::vector<int> h_cl_g0;                 // group range of every cluster (n_clusters + 1)
+    int max_cl_groups = 0;
     std::vector<int> h_mp_ptr, h_mp_col;
     std::vector<int> h_group_nmol, h_group_occ0, h_group_virt0;
     std::vector<int> h_group_ot0, h_group_not, h_group_vt0, h_group_nvt;
@@ -141,6 +144,11 @@ struct Ctx {
     int* d_atom_lo = nullptr;         // atom range of the atom's cluster
     int* d_atom_hi = nullptr;
     int* d_cl_mol0 = nullptr;
+    int* d_cl_g0 = nullptr;           // n_clusters + 1: first group of every cluster
+    int* d_cl_ot0 = nullptr;          // n_clusters + 1: first occupied tile of every cluster
+    int* d_cl_vt0 = nullptr;          // n_clusters + 1: first virtual tile of every cluster
+    int* d_clblk_ptr[2] = {nullptr, nullptr};   // blocks of every cluster: [0] all directed, [1] A <= B
+    int* d_clblk[2] = {nullptr, nullptr};
     int* d_cl_nmol = nullptr;
     int* d_group_cl = nullptr;        // cluster of every group
     void* d_cl_sel = nullptr;         // per-cluster top-k state (6 words each)
@@ -269,6 +277,7 @@ cudaError_t launch_density(Ctx* c);
 cudaError_t launch_select_rot(Ctx* c);
 cudaError_t launch_ortho_prepare(Ctx* c, int which, double tol);
 cudaError_t launch_closure(Ctx* c, int mode, int which); // structural fill; cur <- other
+size_t closure_smem_bytes(const Ctx* c);
 cudaError_t launch_apply(Ctx* c, int mode, int which);   // mode 0 rotations, 1 combinations; in place
 cudaError_t launch_compact(Ctx* c);                      // drop all-zero tiles; cur <- other
 // charges

@@ -53,3 +53,35 @@ def test_batch_run_converges_every_cluster():
         c = context(s)
         o = c.run()
         assert abs(E[k] - o["energy"]) < 1e-6 * s.n_mol * 3
+
+
+@pytest.mark.parametrize("prec,e_tol,q_tol", [(0, 1e-10, 1e-9), (1, 1e-6, 1e-3)])
+def test_batch_of_drawn_cluster_sizes_equals_separate_clusters(prec, e_tol, q_tol):
+    """Three clusters of the batched workload's seed-7 size draw (214, 355 and 830
+    molecules): the batch reproduces each cluster alone. In FP64 the only
+    difference is the summation order of the gamma tiles (the batch starts them
+    at other atoms); in mixed precision those FP32 tile sums differ by FP32
+    rounding, which can flip a pair at the rotation cap. At these clusters' small
+    SCC gaps (~0.01 Ha) one flipped rotation moves charges by ~1e-4 e, so mixed
+    runs are compared to 1e-6 Ha/atom in energy and 1e-3 e in charge."""
+    from synth import cluster_sizes
+    sizes = cluster_sizes()
+    picks = [13, 8, 7]
+    assert [int(sizes[k]) for k in picks] == [214, 355, 830]
+    parts = [lattice_water(int(sizes[k]), seed=k) for k in picks]
+    eps = 1e-5
+    cb = context(concat_clusters(parts), precision=prec)
+    _prep(cb, eps)
+    singles = [context(s, precision=prec) for s in parts]
+    for c in singles:
+        _prep(c, eps)
+    a0 = np.cumsum([0] + [3 * s.n_mol for s in parts])
+    for step in range(2):
+        cb.step()
+        Eb, _ = cb.cluster_results()
+        qb, _, _ = cb.get_charges()
+        for k, c in enumerate(singles):
+            info = c.step()
+            assert abs(Eb[k] - info["energy"]) < e_tol * 3 * parts[k].n_mol, (step, k)
+            q, _, _ = c.get_charges()
+            assert np.abs(qb[a0[k]:a0[k + 1]] - q).max() < q_tol, (step, k)
