@@ -219,6 +219,21 @@ int sscf_set_C_dense(sscf_ctx* ctx, const double* C);
 /* Rows of C for large systems: the AO rows `rows` (n of them), dense over
  * all MOs, into out (host, n x n_mo, row-major). */
 int sscf_get_C_rows(sscf_ctx* ctx, int n, const int* rows, double* out);
+/* Checkpoint and restart of C in its stored form (Section "Sparse storage",
+ * here padded by row block): for every row block r (one molecule, 6 AO rows)
+ * nt[r] stored tiles with sorted tile ids, each tile 96 values laid out
+ * [6 AO rows][16 MOs] (MO columns past the tile's last MO are zero). Tiles of
+ * the occupied MOs of group g have ids group-major from 0, then the virtual
+ * tiles; all arrays are host memory owned by the caller, values in FP64 for
+ * both precisions (a mixed context rounds them to FP32 on restart).
+ * sscf_get_C_tiles: nt (n_mol ints), tiles (n_stored ints, row block after
+ *   row block), vals (96 * n_stored doubles); any may be NULL, n_stored (if not
+ *   NULL) receives the count, so a first call with NULL arrays sizes them.
+ * sscf_set_C_tiles: the same arrays. Errors: INVALID_ARG (unsorted or foreign
+ *   tile ids, negative counts), CAPACITY (more tiles than cap_tiles), NONFINITE;
+ *   on any error the context is left unchanged. */
+int sscf_get_C_tiles(sscf_ctx* ctx, int32_t* nt, int32_t* tiles, double* vals, int64_t* n_stored);
+int sscf_set_C_tiles(sscf_ctx* ctx, const int32_t* nt, const int32_t* tiles, const double* vals);
 /* Columns of C for large systems: the MOs `cols` (n of them), dense over all
  * AOs, into out (host, n_ao x n, row-major). */
 int sscf_get_C_cols(sscf_ctx* ctx, int n, const int* cols, double* out);

@@ -34,7 +34,7 @@ EXPORTED = [
     "sscf_set_charges", "sscf_get_colouring", "sscf_get_pairs", "sscf_profile", "sscf_profile_read",
     "sscf_select_pairs_noalloc", "sscf_gradients", "sscf_get_cluster_results",
     "sscf_enable_graph", "sscf_get_C_rows", "sscf_get_blocks",
-    "sscf_get_C_cols", "sscf_get_F_entries",
+    "sscf_get_C_cols", "sscf_get_F_entries", "sscf_get_C_tiles", "sscf_set_C_tiles",
 ]
 
 
@@ -119,6 +119,8 @@ def load() -> ctypes.CDLL:
         "sscf_enable_graph": (c_int, [c_vp, c_int]),
         "sscf_get_C_rows": (c_int, [c_vp, c_int, P(c_int), P(c_double)]),
         "sscf_get_C_cols": (c_int, [c_vp, c_int, P(c_int), P(c_double)]),
+        "sscf_get_C_tiles": (c_int, [c_vp, P(ctypes.c_int32), P(ctypes.c_int32), P(c_double), P(c_i64)]),
+        "sscf_set_C_tiles": (c_int, [c_vp, P(ctypes.c_int32), P(ctypes.c_int32), P(c_double)]),
         "sscf_get_F_entries": (c_int, [c_vp, c_int, P(c_int), P(c_int), P(c_double)]),
         "sscf_get_blocks": (c_int, [c_vp, P(c_int), P(c_double), P(c_double), P(c_double), P(c_i64)]),
     }
@@ -296,6 +298,24 @@ class Context:
         _check(self.lib.sscf_get_C_rows(self.h, int(rows.size), _ptr(rows, ctypes.c_int), _ptr(out)),
                "sscf_get_C_rows")
         return out
+
+    def get_C_tiles(self):
+        """Checkpoint of C: (nt per row block, tile ids, values as (n_stored, 6, 16))."""
+        n = ctypes.c_int64()
+        _check(self.lib.sscf_get_C_tiles(self.h, None, None, None, ctypes.byref(n)), "sscf_get_C_tiles")
+        nt = np.empty(self.n_ao // 6, dtype=np.int32)
+        tiles = np.empty(n.value, dtype=np.int32)
+        vals = np.empty((n.value, 6, 16))
+        _check(self.lib.sscf_get_C_tiles(self.h, _ptr(nt, ctypes.c_int32), _ptr(tiles, ctypes.c_int32), _ptr(vals),
+                                         ctypes.byref(n)), "sscf_get_C_tiles")
+        return nt, tiles, vals
+
+    def set_C_tiles(self, nt, tiles, vals):
+        nt = np.ascontiguousarray(nt, dtype=np.int32)
+        tiles = np.ascontiguousarray(tiles, dtype=np.int32)
+        vals = np.ascontiguousarray(vals, dtype=np.float64)
+        _check(self.lib.sscf_set_C_tiles(self.h, _ptr(nt, ctypes.c_int32), _ptr(tiles, ctypes.c_int32), _ptr(vals)),
+               "sscf_set_C_tiles")
 
     def get_C_cols(self, cols) -> np.ndarray:
         cols = np.ascontiguousarray(cols, dtype=np.int32)

@@ -105,6 +105,93 @@ int sscf_set_C_dense(sscf_ctx* h, const double* C) {
     return SSCF_OK;
 }
 
+// Checkpoint of C in its stored form: per row block the sorted tile ids and
+// their 6x16 values (FP64 on the host in both precisions).
+int sscf_get_C_tiles(sscf_ctx* h, int32_t* nt_out, int32_t* tiles_out, double* vals_out, int64_t* n_stored) {
+    if (!h) return SSCF_ERR_INVALID_ARG;
+    Ctx& c = h->c;
+    const int b = c.cur;
+    std::vector<int> nt(c.n_mol);
+    CKA(cudaStreamSynchronize(c.stream));
+    CKA(cudaMemcpy(nt.data(), c.d_c_nt[b], nt.size() * 4, cudaMemcpyDeviceToHost));
+    int64_t tot = 0;
+    for (int r = 0; r < c.n_mol; ++r) {
+        if (nt[r] < 0 || nt[r] > c.cap) return SSCF_ERR_STATE;
+        tot += nt[r];
+    }
+    if (n_stored) *n_stored = tot;
+    if (nt_out) std::copy(nt.begin(), nt.end(), nt_out);
+    if (!tiles_out && !vals_out) return SSCF_OK;
+    std::vector<unsigned char> raw((size_t)c.cap * kTileVals * c.tsize);
+    int64_t off = 0;
+    for (int r = 0; r < c.n_mol; ++r) {
+        if (nt[r] == 0) continue;
+        if (tiles_out)
+            CKA(cudaMemcpy(tiles_out + off, c.d_c_tile[b] + (size_t)r * c.cap, (size_t)nt[r] * 4,
+                           cudaMemcpyDeviceToHost));
+        if (vals_out) {
+            const size_t n = (size_t)nt[r] * kTileVals;
+            CKA(cudaMemcpy(raw.data(), (const unsigned char*)c.d_c_val[b] + (size_t)r * c.cap * kTileVals * c.tsize,
+                           n * c.tsize, cudaMemcpyDeviceToHost));
+            double* dst = vals_out + off * kTileVals;
+            if (c.prec == SSCF_FP64)
+                std::memcpy(dst, raw.data(), n * 8);
+            else
+                for (size_t i = 0; i < n; ++i) dst[i] = (double)((const float*)raw.data())[i];
+        }
+        off += nt[r];
+    }
+    return SSCF_OK;
+}
+
+int sscf_set_C_tiles(sscf_ctx* h, const int32_t* nt_in, const int32_t* tiles_in, const double* vals_in) {
+    if (!h || !nt_in) return SSCF_ERR_INVALID_ARG;
+    Ctx& c = h->c;
+    std::vector<int> group_cl(c.n_groups, 0);
+    for (int m = 0; m < c.n_mol; ++m) group_cl[c.h_mol_group[m]] = c.h_mol_cluster[m];
+    int64_t tot = 0;
+    for (int r = 0; r < c.n_mol; ++r) {
+        if (nt_in[r] < 0) return SSCF_ERR_INVALID_ARG;
+        if (nt_in[r] > c.cap) return SSCF_ERR_CAPACITY;
+        tot += nt_in[r];
+    }
+    if (tot > 0 && (!tiles_in || !vals_in)) return SSCF_ERR_INVALID_ARG;
+    int64_t off = 0;
+    for (int r = 0; r < c.n_mol; ++r) {   // validate everything before touching the device
+        for (int s = 0; s < nt_in[r]; ++s) {
+            const int t = tiles_in[off + s];
+            if (t < 0 || t >= c.n_tiles || (s > 0 && t <= tiles_in[off + s - 1])) return SSCF_ERR_INVALID_ARG;
+            if (group_cl[c.h_tile_group[t]] != c.h_mol_cluster[r]) return SSCF_ERR_INVALID_ARG;
+        }
+        off += nt_in[r];
+    }
+    for (int64_t i = 0; i < tot * kTileVals; ++i)
+        if (!std::isfinite(vals_in[i])) return SSCF_ERR_NONFINITE;
+    CKA(cudaStreamSynchronize(c.stream));
+    std::vector<int> tiles(c.cap);
+    std::vector<float> f((size_t)c.cap * kTileVals);
+    off = 0;
+    for (int r = 0; r < c.n_mol; ++r) {
+        const int n = nt_in[r];
+        if (n > 0) {
+            CKA(cudaMemcpy(c.d_c_tile[0] + (size_t)r * c.cap, tiles_in + off, (size_t)n * 4, cudaMemcpyHostToDevice));
+            void* dst = (unsigned char*)c.d_c_val[0] + (size_t)r * c.cap * kTileVals * c.tsize;
+            const double* src = vals_in + off * kTileVals;
+            if (c.prec == SSCF_FP64) {
+                CKA(cudaMemcpy(dst, src, (size_t)n * kTileVals * 8, cudaMemcpyHostToDevice));
+            } else {
+                for (size_t i = 0; i < (size_t)n * kTileVals; ++i) f[i] = (float)src[i];
+                CKA(cudaMemcpy(dst, f.data(), (size_t)n * kTileVals * 4, cudaMemcpyHostToDevice));
+            }
+        }
+        off += n;
+    }
+    CKA(cudaMemcpy(c.d_c_nt[0], nt_in, (size_t)c.n_mol * 4, cudaMemcpyHostToDevice));
+    c.cur = 0;
+    c.have_guess = true;
+    return SSCF_OK;
+}
+
 // Rows (AO indices) of C, dense over all MOs: out is n x n_mo, row-major.
 int sscf_get_C_rows(sscf_ctx* h, int n, const int* rows, double* out) {
     if (!h || n < 0 || (n > 0 && (!rows || !out))) return SSCF_ERR_INVALID_ARG;
