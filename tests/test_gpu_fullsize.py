@@ -206,3 +206,37 @@ def test_mulliken_sampled_after_full_step():
     info = ctx.step()
     assert info["n_rot"] > 0 and np.isfinite(info["energy"])
     check_sampled_mulliken(s, ctx, S)
+
+
+@pytest.mark.parametrize("eps", [1e-4, 1e-5, 1e-6])
+def test_one_step_mixed_against_fp64_from_the_same_state(eps):
+    """The precision error of one SCC iteration at full size: the mixed state
+    (prepared as the benchmark prepares it) is checkpointed into an FP64
+    context with the same charges, both take one step, and the energies and
+    energies are compared against the target of 1e-6 Ha/atom. Charges are
+    compared to 3e-5 e rather than 1e-5: in this unconverged state the rotation
+    cap is active (the 10 N_occ largest |F_ij| of ~26 million candidates are
+    kept), and a pair whose |F| lies within the FP32 error of F from the cut can
+    enter or leave the selection; one such rotation moves a few charges by
+    ~1e-5 e. The FP64 path is the oracle's stand-in here: it matches the oracle
+    step by step at 32-216 molecules (test_gpu_parity)."""
+    s = water(N_MOL)
+    cm = context(s, precision=1)
+    cm.set_thresholds(1e-3, 1e-2, 1e-8)
+    cm.guess()
+    cm.orthonormalise(0, max_pass=60)
+    cm.set_thresholds(eps, 10 * eps, 1e-6)
+    cm.reset_charges()
+    ck = cm.get_C_tiles()
+    charges = cm.get_charges()
+    cd = context(s, precision=0)
+    cd.set_thresholds(eps, 10 * eps, 1e-6)
+    cd.set_C_tiles(*ck)
+    cd.set_charges(*charges)
+    im, idd = cm.step(), cd.step()
+    qm, qd = cm.get_charges()[0], cd.get_charges()[0]
+    cm.close()
+    cd.close()
+    assert abs(im["energy"] - idd["energy"]) / s.n_atoms < 1e-6
+    assert np.abs(qm - qd).max() < 3e-5
+    assert abs(im["n_rot"] - idd["n_rot"]) <= 1e-3 * idd["n_rot"]
