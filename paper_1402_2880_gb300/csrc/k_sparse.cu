@@ -8,6 +8,8 @@
 // reduced over the row blocks the two columns share.
 #include "sscf_internal.h"
 
+#include <type_traits>
+
 namespace sscf {
 
 namespace {
@@ -335,14 +337,20 @@ __global__ void k_extract_diag(int n_tiles, const int* __restrict__ tile_mo0, co
 // ---------------------------------------------------------------------------
 constexpr int kDensWarps = 8;
 constexpr int kDensFlush = 8;   // tiles per lane between FP64 flushes
+constexpr int kDensUnroll = 1;  // shared tiles per half-warp and round (2 measured no faster)
+constexpr int kDensMinBlocks = 2;   // resident CTAs per SM the register budget aims at
 template <typename T>
-__global__ void __launch_bounds__(kDensWarps * 32)
+__global__ void __launch_bounds__(kDensWarps * 32, kDensMinBlocks)
 k_density(int n_occ_tiles, int map_n, const int* __restrict__ mol_ot0, int cap, const int* __restrict__ c_nt,
           const int* __restrict__ c_tile, const T* __restrict__ c_val, const int* __restrict__ mp_ptr,
           const int* __restrict__ mp_col, const double* __restrict__ H0b, const double* __restrict__ Sb,
           double* __restrict__ q, double* __restrict__ e_mol) {
-    // slot of every occupied tile of m's cluster in row m, or -1 (map_n = largest cluster)
+    // slot of every occupied tile of m's cluster in row m, or -1 (map_n = largest cluster);
+    // then, in mixed precision, the FP64 sums of each lane's 36 products (flushed
+    // from FP32 every kDensFlush tiles), kept in shared memory to save registers
     extern __shared__ int smap[];
+    constexpr bool kSplit = !std::is_same<typename Acc<T>::type, double>::value;
+    double* sacc = (double*)(smap + ((map_n + 1) & ~1));   // [warp][36][32]: per-lane FP64 sums
     __shared__ double part[kDensWarps][4];
     const int m = blockIdx.x;
     const int t0 = mol_ot0[m];
@@ -362,54 +370,107 @@ k_density(int n_occ_tiles, int map_n, const int* __restrict__ mol_ot0, int cap, 
     for (int w = warp; w < ne; w += kDensWarps) {
         const int e = e0 + w;
         const int n = mp_col[e];
-        double accd[36];
         A acc[36];
+        double* wacc = sacc + (size_t)warp * 36 * 32 + lane;
 #pragma unroll
         for (int u = 0; u < 36; ++u) {
-            accd[u] = 0.0;
             acc[u] = 0;
+            wacc[u * 32] = 0.0;
         }
         const int ntn = c_nt[n];
         int since = 0;
-        for (int s = half; s < ntn; s += 2) {
-            const int t = c_tile[(size_t)n * cap + s];
-            if (t >= n_occ_tiles) break;   // tiles are sorted: occupied tiles first
-            const int sm_ = smap[t - t0];
-            if (sm_ < 0) continue;
-            const T* cm = c_val + ((size_t)m * cap + sm_) * kTileVals + col;
-            const T* cn = c_val + ((size_t)n * cap + s) * kTileVals + col;
-            A a6[6], b6[6];
+        // 32 of n's tiles at a time: one coalesced load of their ids, the shared
+        // ones found with one ballot; then each half-warp takes kDensUnroll shared
+        // tiles per round, so their loads are in flight together
+        for (int base = 0; base < ntn; base += 32) {
+            const int s = base + lane;
+            const int t = s < ntn ? c_tile[(size_t)n * cap + s] : n_occ_tiles;
+            const int sm_ = t < n_occ_tiles ? smap[t - t0] : -1;
+            unsigned mm = __ballot_sync(0xffffffffu, sm_ >= 0);
+            const bool virt_seen = __any_sync(0xffffffffu, s < ntn && t >= n_occ_tiles);
+            while (mm) {
+                int src[kDensUnroll];
 #pragma unroll
-            for (int k = 0; k < 6; ++k) {
-                a6[k] = (A)cm[k * kTileW];
-                b6[k] = (A)cn[k * kTileW];
-            }
+                for (int u = 0; u < kDensUnroll; ++u) {
+                    // bits in order: half 0 takes the 1st, 3rd, ..., half 1 the 2nd, 4th, ...
+                    int b0 = -1, b1 = -1;
+                    if (mm) {
+                        b0 = __ffs(mm) - 1;
+                        mm &= mm - 1;
+                    }
+                    if (mm) {
+                        b1 = __ffs(mm) - 1;
+                        mm &= mm - 1;
+                    }
+                    src[u] = half ? b1 : b0;
+                }
+                A a6[kDensUnroll][6], b6[kDensUnroll][6];
 #pragma unroll
-            for (int k = 0; k < 6; ++k)
+                for (int u = 0; u < kDensUnroll; ++u) {
+                    const int ss = __shfl_sync(0xffffffffu, s, src[u] < 0 ? 0 : src[u]);
+                    const int sm2 = __shfl_sync(0xffffffffu, sm_, src[u] < 0 ? 0 : src[u]);
+                    if (src[u] >= 0) {
+                        const T* cm = c_val + ((size_t)m * cap + sm2) * kTileVals + col;
+                        const T* cn = c_val + ((size_t)n * cap + ss) * kTileVals + col;
 #pragma unroll
-                for (int l = 0; l < 6; ++l) acc[k * 6 + l] += a6[k] * b6[l];
-            if (++since == kDensFlush) {
-                since = 0;
+                        for (int k = 0; k < 6; ++k) {
+                            a6[u][k] = (A)cm[k * kTileW];
+                            b6[u][k] = (A)cn[k * kTileW];
+                        }
+                    }
+                }
 #pragma unroll
-                for (int u = 0; u < 36; ++u) {
-                    accd[u] += (double)acc[u];
-                    acc[u] = 0;
+                for (int u = 0; u < kDensUnroll; ++u) {
+                    if (src[u] < 0) continue;
+#pragma unroll
+                    for (int k = 0; k < 6; ++k)
+#pragma unroll
+                        for (int l = 0; l < 6; ++l) acc[k * 6 + l] += a6[u][k] * b6[u][l];
+                    if constexpr (kSplit) {
+                        if (++since == kDensFlush) {
+                            since = 0;
+#pragma unroll
+                            for (int v = 0; v < 36; ++v) {
+                                wacc[v * 32] += (double)acc[v];
+                                acc[v] = 0;
+                            }
+                        }
+                    }
                 }
             }
+            if (virt_seen) break;   // tiles are sorted: occupied tiles first
         }
-        // reduce the 36 partial products over the 32 lanes
-        double qa[3] = {0, 0, 0}, eb = 0.0;
+        // lane sums to shared memory, then lane u < 36 adds up entry u over the
+        // 32 lanes (rotated start: no bank conflicts) and weights it by S and H0
 #pragma unroll
         for (int u = 0; u < 36; ++u) {
-            double v = accd[u] + (double)acc[u];
-#pragma unroll
-            for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+            if constexpr (kSplit)
+                wacc[u * 32] += (double)acc[u];
+            else
+                wacc[u * 32] = (double)acc[u];
+        }
+        __syncwarp();
+        double qa[3] = {0, 0, 0}, eb = 0.0;
+        for (int u = lane; u < 36; u += 32) {
+            const double* row = sacc + ((size_t)warp * 36 + u) * 32;
+            double v = 0.0;
+            for (int j = 0; j < 32; ++j) v += row[(j + lane) & 31];
             const double P = 2.0 * v;
-            const int k = u / 6;
-            const int atom = k < 4 ? 0 : k - 3;
-            qa[atom] += P * Sb[(size_t)e * 36 + u];
+            const int k = u / 6;   // AO of m: O s, p, p, p, then H1 s, H2 s
+            const double pq = P * Sb[(size_t)e * 36 + u];
+            qa[0] += k < 4 ? pq : 0.0;
+            qa[1] += k == 4 ? pq : 0.0;
+            qa[2] += k == 5 ? pq : 0.0;
             eb += P * H0b[(size_t)e * 36 + u];
         }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            qa[0] += __shfl_xor_sync(0xffffffffu, qa[0], off);
+            qa[1] += __shfl_xor_sync(0xffffffffu, qa[1], off);
+            qa[2] += __shfl_xor_sync(0xffffffffu, qa[2], off);
+            eb += __shfl_xor_sync(0xffffffffu, eb, off);
+        }
+        __syncwarp();
         wq[0] += qa[0];
         wq[1] += qa[1];
         wq[2] += qa[2];
@@ -466,7 +527,7 @@ static cudaError_t set_attrs() {
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(k_transform<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(k_density<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
+    e = cudaFuncSetAttribute(k_density<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     return e;
 }
 
@@ -548,8 +609,8 @@ cudaError_t launch_density(Ctx* c) {
     c->n_launch += 1;
     cudaError_t e = ensure_attrs();
     if (e != cudaSuccess) return e;
-    const size_t smem = (size_t)c->max_cl_otiles * 4;
-    if (smem > 160 * 1024) return cudaErrorInvalidValue;
+    const size_t smem = (size_t)((c->max_cl_otiles + 1) & ~1) * 4 + (size_t)kDensWarps * 36 * 32 * 8;
+    if (smem > 200 * 1024) return cudaErrorInvalidValue;
     const int b = c->cur;
     if (c->prec == SSCF_FP64)
         k_density<double><<<c->n_mol, kDensWarps * 32, smem, c->stream>>>(c->n_occ_tiles, c->max_cl_otiles, c->d_mol_ot0, c->cap, c->d_c_nt[b], c->d_c_tile[b],
