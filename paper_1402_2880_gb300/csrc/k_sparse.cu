@@ -173,20 +173,51 @@ __global__ void k_xc(int tile_lo, int n_rows, int cap, int capY, const int* __re
     for (int k = warp; k < ny; k += nwarps) {
         const int r = y_row[(size_t)t * capY + k];
         A acc0 = 0, acc1 = 0, acc2 = 0;
-        for (int e = mp_ptr[r]; e < mp_ptr[r + 1]; ++e) {
-            const int n = mp_col[e];
-            const int j = rowpos[n - r0];
-            if (j < 0) continue;
-            const T* cv = c_val + ((size_t)n * cap + cci_slot[lo + j]) * kTileVals + col;
-            const T* xb = Xb + (size_t)e * 36;
-            A c6[6];
+        // 32 pattern neighbours at a time: their ids, positions and slots are
+        // looked up in parallel, one per lane; the matched ones are then summed
+        // in pattern order with their data broadcast from the owning lane
+        const int e_lo = mp_ptr[r], e_hi = mp_ptr[r + 1];
+        for (int eb = e_lo; eb < e_hi; eb += 32) {
+            const int e = eb + lane;
+            int sl = -1, nl = 0;
+            if (e < e_hi) {
+                nl = mp_col[e];
+                const int j = rowpos[nl - r0];
+                if (j >= 0) sl = cci_slot[lo + j];
+            }
+            unsigned mm = __ballot_sync(0xffffffffu, sl >= 0);
+            while (mm) {
+                // two matched neighbours per round: both loads in flight, sums in order
+                int src[2];
 #pragma unroll
-            for (int q = 0; q < 6; ++q) c6[q] = (A)cv[q * kTileW];
+                for (int u = 0; u < 2; ++u) {
+                    src[u] = mm ? __ffs(mm) - 1 : -1;
+                    if (mm) mm &= mm - 1;
+                }
+                A c6[2][6];
+                const T* xb[2];
 #pragma unroll
-            for (int q = 0; q < 6; ++q) {
-                acc0 += (A)xb[(q0)*6 + q] * c6[q];
-                acc1 += (A)xb[(q0 + 2) * 6 + q] * c6[q];
-                acc2 += (A)xb[(q0 + 4) * 6 + q] * c6[q];
+                for (int u = 0; u < 2; ++u) {
+                    const int sv = src[u] < 0 ? 0 : src[u];
+                    const int n = __shfl_sync(0xffffffffu, nl, sv);
+                    const int ss = __shfl_sync(0xffffffffu, sl, sv);
+                    xb[u] = Xb + (size_t)(eb + sv) * 36;
+                    if (src[u] >= 0) {
+                        const T* cv = c_val + ((size_t)n * cap + ss) * kTileVals + col;
+#pragma unroll
+                        for (int q = 0; q < 6; ++q) c6[u][q] = (A)cv[q * kTileW];
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < 2; ++u) {
+                    if (src[u] < 0) continue;
+#pragma unroll
+                    for (int q = 0; q < 6; ++q) {
+                        acc0 += (A)xb[u][(q0)*6 + q] * c6[u][q];
+                        acc1 += (A)xb[u][(q0 + 2) * 6 + q] * c6[u][q];
+                        acc2 += (A)xb[u][(q0 + 4) * 6 + q] * c6[u][q];
+                    }
+                }
             }
         }
         T* yv = y_val + ((size_t)t * capY + k) * kTileVals;
@@ -576,7 +607,8 @@ cudaError_t launch_transform_rot(Ctx* c) {
     c->n_launch += 3;
     cudaError_t e = ensure_attrs();
     if (e != cudaSuccess) return e;
-    if ((size_t)kTfWarps * kStage * 2 * kTileVals * 8 + (size_t)c->max_cl_mol * 4 > 200 * 1024) return cudaErrorInvalidValue;
+    if ((size_t)kTfWarps * kStage * 2 * kTileVals * c->tsize + (size_t)c->max_cl_mol * 4 > 200 * 1024)
+        return cudaErrorInvalidValue;
     if (c->prec == SSCF_FP64) {
         e = transform_t<double>(c, c->d_rot_tp_ptr, c->d_rot_tp_b, c->d_rot_tp_out, c->d_F);
         if (e == cudaSuccess)
