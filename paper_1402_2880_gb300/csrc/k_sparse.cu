@@ -239,6 +239,7 @@ __global__ void k_xc(int tile_lo, int n_rows, int cap, int capY, const int* __re
 // ---------------------------------------------------------------------------
 constexpr int kTfWarps = 8;
 constexpr int kStage = 8;   // row blocks staged per warp at a time
+constexpr int kTfSplit = 4; // CTAs per occupied tile, sharing its pairs (1, 2, 4 measured: 4 best)
 
 template <typename T> struct V4;
 template <> struct V4<float> { using type = float4; };
@@ -254,9 +255,10 @@ k_transform(int n_rows, const int* __restrict__ tile_row0, int cap, int capY, co
     extern __shared__ __align__(16) unsigned char sraw[];
     T* stage = (T*)sraw;                                        // [warps][kStage][2][96]
     int* slot_of = (int*)(stage + (size_t)kTfWarps * kStage * 2 * kTileVals);   // n_rows (cluster-local)
-    const int a = blockIdx.x;
+    // CTA (a, s) takes the pairs of tile a with index = s (mod kTfSplit)
+    const int a = blockIdx.x / kTfSplit, split = blockIdx.x % kTfSplit;
     const int p0 = tp_ptr[a], p1 = tp_ptr[a + 1];
-    if (p0 == p1) return;
+    if (p0 + split >= p1) return;
     const int r0 = tile_row0[a];
     const int lo = cci_ptr[a], nc = cci_ptr[a + 1] - lo;
     for (int i = threadIdx.x; i < n_rows; i += blockDim.x) slot_of[i] = -1;
@@ -270,7 +272,7 @@ k_transform(int n_rows, const int* __restrict__ tile_row0, int cap, int capY, co
     using VT = typename V4<T>::type;
     constexpr int kVec = sizeof(VT) / sizeof(T);          // values per 16-byte load
     constexpr int kPerTile = kTileVals / kVec;            // 16-byte loads per tile
-    for (int p = p0 + warp; p < p1; p += kTfWarps) {
+    for (int p = p0 + split + warp * kTfSplit; p < p1; p += kTfWarps * kTfSplit) {
         const int b = tp_b[p];
         const int nb = y_n[b];
         const int* yr = y_row + (size_t)b * capY;
@@ -597,7 +599,7 @@ cudaError_t launch_xc(Ctx* c, bool use_h, int tile_lo, int tile_hi) {
 template <typename T>
 static cudaError_t transform_t(Ctx* c, const int* ptr, const int* bl, const int* outl, void* out) {
     const size_t smem = (size_t)kTfWarps * kStage * 2 * kTileVals * sizeof(T) + (size_t)c->max_cl_mol * 4;
-    k_transform<T><<<c->n_tiles, kTfWarps * 32, smem, c->stream>>>(c->max_cl_mol, c->d_tile_row0, c->cap, c->capY, ptr, bl, outl, c->d_cci_ptr,
+    k_transform<T><<<c->n_tiles * kTfSplit, kTfWarps * 32, smem, c->stream>>>(c->max_cl_mol, c->d_tile_row0, c->cap, c->capY, ptr, bl, outl, c->d_cci_ptr,
                                                          c->d_cci_row, c->d_cci_slot, (const T*)c->d_c_val[c->cur],
                                                          c->d_y_n, c->d_y_row, (const T*)c->d_y_val, (T*)out);
     return cudaGetLastError();
