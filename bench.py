@@ -48,7 +48,8 @@ def parse():
     ap.add_argument("--eps", type=float, default=1e-5)
     ap.add_argument("--prep-eps", type=float, default=1e-3)
     ap.add_argument("--prep-passes", type=int, default=200)
-    ap.add_argument("--sample-mol", type=int, default=125)
+    ap.add_argument("--sample-mol", type=int, default=216,
+                    help="molecules of the sub-cube the oracle is timed on (CPU baseline and reference arm)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--clusters", type=int, default=0,
                     help="batched workload: the first K clusters of the seed-7 size draw U[200, 3000] in one context")
@@ -57,6 +58,7 @@ def parse():
     ap.add_argument("--cap-tiles", type=int, default=0, help="tiles per row of C (0: the largest cluster's tiles)")
     ap.add_argument("--cap-y", type=int, default=0, help="row blocks per tile of Y (0: the largest cluster)")
     ap.add_argument("--graph", action="store_true", help="replay each SCC iteration as one CUDA graph")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the default transform launch shape")
     return ap.parse_args()
 
 
@@ -237,10 +239,16 @@ def main():
         prep = ctx.orthonormalise(SSCF_ORTHO_ALL, max_pass=args.prep_passes)
         ctx.set_thresholds(args.eps, 10 * args.eps, 1e-6)
         ctx.reset_charges()
-        if args.graph:
-            ctx.enable_graph(True)
+        # warm-up: one eager step, the launch-shape autotuner, then the rest
+        # (graph-captured when asked, so that no capture falls in the timed region)
         warm = None
-        for _ in range(max(args.warmup, 0)):
+        tuned = None
+        for w in range(max(args.warmup, 0)):
+            if w == 1 or (w == 0 and args.warmup == 1):
+                if not args.no_autotune:
+                    tuned = ctx.autotune()
+                if args.graph:
+                    ctx.enable_graph(True)
             warm = ctx.step()
         torch.cuda.synchronize(dev)
         # C below twice the 129 MB L2: flush L2 between timed steps (outside the events)
@@ -284,7 +292,7 @@ def main():
         n_mo = ctx.n_mo
         ctx.close()
         return dict(ms=ms, infos=infos, prof=prof, e2e_dt=e2e_dt, prep=prep, c_bytes=c_bytes,
-                    flushing=flushing, n_mo=n_mo)
+                    flushing=flushing, n_mo=n_mo, tuned=tuned)
 
     sampler = ClockSampler(local_rank)
     sampler.start()
@@ -381,9 +389,9 @@ def main():
 
     cpu = None
     if not args.no_cpu_baseline:
-        rate, dt, n_at = oracle_iteration_rate(args.sample_mol, args.eps, 2)
+        rate, dt, n_at = oracle_iteration_rate(args.sample_mol, args.eps, 3)
         cpu = {"value": rate, "unit": UNIT, "cores": host_cores(), "kind": "oracle",
-               "sample": f"2 SCC iterations of oracle B (FP64, numpy) on a {args.sample_mol}-molecule "
+               "sample": f"3 SCC iterations of oracle B (FP64, numpy) on a {args.sample_mol}-molecule "
                          f"sub-cube ({n_at} atoms), {dt:.1f} s"}
 
     launches = int(round(mean("launches")))
@@ -404,7 +412,8 @@ def main():
                    "l2": (f"C holds {c_bytes / 1e6:.0f} MB, " + ("L2 flushed (256 MB write) before every timed step"
                                                                    if flushed else
                                                                    "more than twice the 129 MB L2: no flush")),
-                   "prep": {"eps": args.prep_eps, "ortho_passes": prep_passes, "eta": prep_eta}},
+                   "prep": {"eps": args.prep_eps, "ortho_passes": prep_passes, "eta": prep_eta},
+                   "autotune": {"transform_ctas_per_tile": sorted({r["tuned"] for r in runs if r["tuned"]})}},
         "scf_iter_per_s": n_gpus * K / (t_max / 1e3),
         "cluster_iter_per_s": (max(args.clusters, 1) if args.clusters > 0 else n_gpus) * K / (t_max / 1e3),
         "clocks": clocks,

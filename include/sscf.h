@@ -169,6 +169,15 @@ int sscf_reset_charges(sscf_ctx* ctx, double* E_out);
  * (ortho_every = 1), density and mixing. */
 int sscf_step(sscf_ctx* ctx, sscf_step_info* info);
 
+/* Launch-shape autotuner (no counterpart in the paper): on the current state
+ * it builds H and Y = H C as a step would, times the occupied-virtual transform
+ * (three launches after one warm-up, CUDA events on the context's stream) for
+ * 1, 2, 4 and 8 CTAs sharing each occupied tile's pairs, and keeps the fastest
+ * for later steps. Results of later calls do not depend on the choice (each
+ * pair is summed the same way). Drops a captured CUDA graph. tf_split_out
+ * (host, may be NULL) receives the choice. Errors: STATE before sscf_guess, CUDA. */
+int sscf_autotune(sscf_ctx* ctx, int* tf_split_out);
+
 /* CUDA graphs: when enabled, sscf_step captures its device work (all kernel
  * launches of one SCC iteration) into a graph at the first call and replays
  * it afterwards: one launch per iteration. The graph is rebuilt when eps

@@ -34,7 +34,7 @@ EXPORTED = [
     "sscf_set_charges", "sscf_get_colouring", "sscf_get_pairs", "sscf_profile", "sscf_profile_read",
     "sscf_select_pairs_noalloc", "sscf_gradients", "sscf_get_cluster_results",
     "sscf_enable_graph", "sscf_get_C_rows", "sscf_get_blocks",
-    "sscf_get_C_cols", "sscf_get_F_entries", "sscf_get_C_tiles", "sscf_set_C_tiles",
+    "sscf_get_C_cols", "sscf_get_F_entries", "sscf_get_C_tiles", "sscf_set_C_tiles", "sscf_autotune",
 ]
 
 
@@ -119,6 +119,7 @@ def load() -> ctypes.CDLL:
         "sscf_enable_graph": (c_int, [c_vp, c_int]),
         "sscf_get_C_rows": (c_int, [c_vp, c_int, P(c_int), P(c_double)]),
         "sscf_get_C_cols": (c_int, [c_vp, c_int, P(c_int), P(c_double)]),
+        "sscf_autotune": (c_int, [c_vp, P(c_int)]),
         "sscf_get_C_tiles": (c_int, [c_vp, P(ctypes.c_int32), P(ctypes.c_int32), P(c_double), P(c_i64)]),
         "sscf_set_C_tiles": (c_int, [c_vp, P(ctypes.c_int32), P(ctypes.c_int32), P(c_double)]),
         "sscf_get_F_entries": (c_int, [c_vp, c_int, P(c_int), P(c_int), P(c_double)]),
@@ -298,6 +299,12 @@ class Context:
         _check(self.lib.sscf_get_C_rows(self.h, int(rows.size), _ptr(rows, ctypes.c_int), _ptr(out)),
                "sscf_get_C_rows")
         return out
+
+    def autotune(self) -> int:
+        """Pick the transform's launch shape by timing it on the current state; returns the choice."""
+        s = ctypes.c_int()
+        _check(self.lib.sscf_autotune(self.h, ctypes.byref(s)), "sscf_autotune")
+        return s.value
 
     def get_C_tiles(self):
         """Checkpoint of C: (nt per row block, tile ids, values as (n_stored, 6, 16))."""

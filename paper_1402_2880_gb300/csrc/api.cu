@@ -879,6 +879,46 @@ int sscf_rotate_sweep(sscf_ctx* h, int64_t* n_rot_out, double* max_fov_out) {
     return SSCF_OK;
 }
 
+int sscf_autotune(sscf_ctx* h, int* tf_split_out) {
+    if (!h) return SSCF_ERR_INVALID_ARG;
+    Ctx& c = h->c;
+    if (!c.have_guess) return SSCF_ERR_STATE;
+    drop_graph(c);
+    // inputs of the occupied-virtual transform for the current state
+    CK(launch_build_h(&c, c.prm.eps));
+    CK(launch_colindex(&c));
+    CK(launch_xc(&c, true, 0, c.n_tiles));
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    const int cand[] = {1, 2, 4, 8};
+    int best = c.tf_split;
+    float best_ms = 1e30f;
+    cudaError_t err = cudaSuccess;
+    for (int s : cand) {
+        c.tf_split = s;
+        err = launch_transform_rot(&c);   // warm-up
+        if (err != cudaSuccess) break;
+        err = cudaEventRecord(e0, c.stream);
+        for (int r = 0; r < 3 && err == cudaSuccess; ++r) err = launch_transform_rot(&c);
+        if (err == cudaSuccess) err = cudaEventRecord(e1, c.stream);
+        if (err == cudaSuccess) err = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
+        if (err != cudaSuccess) break;
+        if (ms < best_ms) {
+            best_ms = ms;
+            best = s;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    c.tf_split = best;
+    if (err != cudaSuccess) return SSCF_ERR_CUDA;
+    if (tf_split_out) *tf_split_out = best;
+    return SSCF_OK;
+}
+
 static int ortho_pass_async(Ctx& c, int which, double tol) {
     const int w = which == SSCF_ORTHO_OCC ? 1 : 0;
     PK("colindex", launch_colindex(&c));

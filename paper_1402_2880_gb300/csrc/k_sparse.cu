@@ -239,7 +239,6 @@ __global__ void k_xc(int tile_lo, int n_rows, int cap, int capY, const int* __re
 // ---------------------------------------------------------------------------
 constexpr int kTfWarps = 8;
 constexpr int kStage = 8;   // row blocks staged per warp at a time
-constexpr int kTfSplit = 4; // CTAs per occupied tile, sharing its pairs (1, 2, 4 measured: 4 best)
 
 template <typename T> struct V4;
 template <> struct V4<float> { using type = float4; };
@@ -247,7 +246,7 @@ template <> struct V4<double> { using type = double2; };
 
 template <typename T>
 __global__ void __launch_bounds__(kTfWarps * 32)
-k_transform(int n_rows, const int* __restrict__ tile_row0, int cap, int capY, const int* __restrict__ tp_ptr,
+k_transform(int n_split, int n_rows, const int* __restrict__ tile_row0, int cap, int capY, const int* __restrict__ tp_ptr,
             const int* __restrict__ tp_b,
             const int* __restrict__ tp_out, const int* __restrict__ cci_ptr, const int* __restrict__ cci_row,
             const int* __restrict__ cci_slot, const T* __restrict__ c_val, const int* __restrict__ y_n,
@@ -255,8 +254,8 @@ k_transform(int n_rows, const int* __restrict__ tile_row0, int cap, int capY, co
     extern __shared__ __align__(16) unsigned char sraw[];
     T* stage = (T*)sraw;                                        // [warps][kStage][2][96]
     int* slot_of = (int*)(stage + (size_t)kTfWarps * kStage * 2 * kTileVals);   // n_rows (cluster-local)
-    // CTA (a, s) takes the pairs of tile a with index = s (mod kTfSplit)
-    const int a = blockIdx.x / kTfSplit, split = blockIdx.x % kTfSplit;
+    // CTA (a, s) takes the pairs of tile a with index = s (mod n_split)
+    const int a = blockIdx.x / n_split, split = blockIdx.x % n_split;
     const int p0 = tp_ptr[a], p1 = tp_ptr[a + 1];
     if (p0 + split >= p1) return;
     const int r0 = tile_row0[a];
@@ -272,7 +271,7 @@ k_transform(int n_rows, const int* __restrict__ tile_row0, int cap, int capY, co
     using VT = typename V4<T>::type;
     constexpr int kVec = sizeof(VT) / sizeof(T);          // values per 16-byte load
     constexpr int kPerTile = kTileVals / kVec;            // 16-byte loads per tile
-    for (int p = p0 + split + warp * kTfSplit; p < p1; p += kTfWarps * kTfSplit) {
+    for (int p = p0 + split + warp * n_split; p < p1; p += kTfWarps * n_split) {
         const int b = tp_b[p];
         const int nb = y_n[b];
         const int* yr = y_row + (size_t)b * capY;
@@ -369,7 +368,7 @@ __global__ void k_extract_diag(int n_tiles, const int* __restrict__ tile_mo0, co
 // warp per neighbour n, results combined in neighbour order.
 // ---------------------------------------------------------------------------
 constexpr int kDensWarps = 8;
-constexpr int kDensFlush = 8;   // tiles per lane between FP64 flushes
+constexpr int kDensFlush = 32;  // tiles per lane between FP64 flushes (FP32 sums of at most 32 products)
 constexpr int kDensUnroll = 1;  // shared tiles per half-warp and round (2 measured no faster)
 constexpr int kDensMinBlocks = 2;   // resident CTAs per SM the register budget aims at
 template <typename T>
@@ -405,11 +404,9 @@ k_density(int n_occ_tiles, int map_n, const int* __restrict__ mol_ot0, int cap, 
         const int n = mp_col[e];
         A acc[36];
         double* wacc = sacc + (size_t)warp * 36 * 32 + lane;
+        bool flushed = false;   // the first flush stores instead of adding
 #pragma unroll
-        for (int u = 0; u < 36; ++u) {
-            acc[u] = 0;
-            wacc[u * 32] = 0.0;
-        }
+        for (int u = 0; u < 36; ++u) acc[u] = 0;
         const int ntn = c_nt[n];
         int since = 0;
         // 32 of n's tiles at a time: one coalesced load of their ids, the shared
@@ -464,9 +461,10 @@ k_density(int n_occ_tiles, int map_n, const int* __restrict__ mol_ot0, int cap, 
                             since = 0;
 #pragma unroll
                             for (int v = 0; v < 36; ++v) {
-                                wacc[v * 32] += (double)acc[v];
+                                wacc[v * 32] = flushed ? wacc[v * 32] + (double)acc[v] : (double)acc[v];
                                 acc[v] = 0;
                             }
+                            flushed = true;
                         }
                     }
                 }
@@ -476,12 +474,7 @@ k_density(int n_occ_tiles, int map_n, const int* __restrict__ mol_ot0, int cap, 
         // lane sums to shared memory, then lane u < 36 adds up entry u over the
         // 32 lanes (rotated start: no bank conflicts) and weights it by S and H0
 #pragma unroll
-        for (int u = 0; u < 36; ++u) {
-            if constexpr (kSplit)
-                wacc[u * 32] += (double)acc[u];
-            else
-                wacc[u * 32] = (double)acc[u];
-        }
+        for (int u = 0; u < 36; ++u) wacc[u * 32] = flushed ? wacc[u * 32] + (double)acc[u] : (double)acc[u];
         __syncwarp();
         double qa[3] = {0, 0, 0}, eb = 0.0;
         for (int u = lane; u < 36; u += 32) {
@@ -599,7 +592,7 @@ cudaError_t launch_xc(Ctx* c, bool use_h, int tile_lo, int tile_hi) {
 template <typename T>
 static cudaError_t transform_t(Ctx* c, const int* ptr, const int* bl, const int* outl, void* out) {
     const size_t smem = (size_t)kTfWarps * kStage * 2 * kTileVals * sizeof(T) + (size_t)c->max_cl_mol * 4;
-    k_transform<T><<<c->n_tiles * kTfSplit, kTfWarps * 32, smem, c->stream>>>(c->max_cl_mol, c->d_tile_row0, c->cap, c->capY, ptr, bl, outl, c->d_cci_ptr,
+    k_transform<T><<<c->n_tiles * c->tf_split, kTfWarps * 32, smem, c->stream>>>(c->tf_split, c->max_cl_mol, c->d_tile_row0, c->cap, c->capY, ptr, bl, outl, c->d_cci_ptr,
                                                          c->d_cci_row, c->d_cci_slot, (const T*)c->d_c_val[c->cur],
                                                          c->d_y_n, c->d_y_row, (const T*)c->d_y_val, (T*)out);
     return cudaGetLastError();

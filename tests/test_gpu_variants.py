@@ -37,3 +37,24 @@ def test_full_block_kernel_matches_generic(n):
     for a, b in zip(i0, i1):
         for k in ("energy", "dq_max", "n_rot", "n_combo", "nnz_c", "upd_combo"):
             assert a[k] == b[k], k
+
+
+def test_autotune_keeps_results():
+    """sscf_autotune only chooses a launch shape: the steps after it equal
+    the steps of an untuned context bit for bit."""
+    s = water(216)
+    runs = []
+    for tune in (False, True):
+        ctx = context(s, precision=1)
+        ctx.set_thresholds(1e-3, 1e-2, 1e-8)
+        ctx.guess()
+        ctx.orthonormalise(0, max_pass=50)
+        ctx.set_thresholds(1e-5, 1e-4, 1e-6)
+        ctx.reset_charges()
+        ctx.step()
+        if tune:
+            assert ctx.autotune() in (1, 2, 4, 8)
+        infos = [ctx.step() for _ in range(2)]
+        runs.append((ctx.get_C(), infos))
+    assert np.array_equal(runs[0][0], runs[1][0])
+    assert [i["energy"] for i in runs[0][1]] == [i["energy"] for i in runs[1][1]]
