@@ -614,6 +614,12 @@ int sscf_create(const sscf_system* sys, const sscf_params* prm, void* cuda_strea
         return SSCF_ERR_INVALID_ARG;
     }
     c.capY = prm->cap_y > 0 ? std::min(prm->cap_y, c.max_cl_mol) : c.max_cl_mol;
+    {
+        int dev = 0, nsm = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess &&
+            cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && nsm > 0)
+            c.n_sm = nsm;
+    }
     c.apply_variant = prm->apply_variant;
     // uploads
 #define UP(d, v)                        \

@@ -810,6 +810,7 @@ __global__ void __launch_bounds__(apply_threads<T>()) k_apply_colour(SweepArgs a
 // j = (level - i) mod 32. The block's pairs are expanded into a dense
 // [level][i] coefficient table with a selection mask per level. No barrier is
 // needed after the table is built: a thread reads back only the rows it wrote.
+constexpr int kFullWaves = 16;                    // resident-CTA multiples per launch (row chunks loop beyond)
 constexpr int kFullRPT = 1;                       // adjacent AO-row pairs per thread (2 measured slower)
 constexpr int kFullCH = 32 * kFullRPT;            // row blocks per CTA
 constexpr int kFullNR = kFullCH * kAoPerMol;      // AO rows per CTA (panel stride, floats)
@@ -852,14 +853,14 @@ __global__ void __launch_bounds__(kFullThreads) k_apply_full(SweepArgs a, int p0
     const int ta0 = a.group_ot0[A], tb0 = MODE == 0 ? a.group_vt0[B] : a.group_ot0[B];
     const int pa = a.cci_ptr[ta0], n_rows = a.cci_ptr[ta0 + 1] - pa;
     const int pb = a.cci_ptr[tb0];
-    const int k0 = blockIdx.x * kFullCH;
-    if (k0 >= n_rows) return;
+    // CTA x takes row chunks x, x + gridDim.x, ... of the block, so its
+    // coefficient table serves several chunks
+    const int k_first = blockIdx.x * kFullCH;
+    if (k_first >= n_rows) return;
     if (a.cci_ptr[tb0 + 1] - pb != n_rows) {
         if (threadIdx.x == 0) atomicOr(a.err, kErrCapacity);
         return;
     }
-    const int nk = min(kFullCH, n_rows - k0);
-    if (threadIdx.x == 0) atomicAdd(a.upd, (unsigned long long)np * (unsigned long long)(nk * 6));
     for (int i = threadIdx.x; i < 32 * 32; i += blockDim.x) {
         if constexpr (MODE == 0) coef[i] = make_float4(0.f, 0.f, 0.f, 0.f);
         else coef[i] = make_float2(0.f, 0.f);
@@ -881,120 +882,124 @@ __global__ void __launch_bounds__(kFullThreads) k_apply_full(SweepArgs a, int p0
         atomicOr(&s_mask[lv], 1u << il);
     }
     __syncthreads();
-    // row pair r of this thread: pair index p = threadIdx.x + r * kFullThreads,
-    // row block p / 3, AO rows 2 (p % 3) and 2 (p % 3) + 1, panel rows 2p and 2p + 1
-    if (threadIdx.x / 3 >= nk) return;
     float* val = (float*)a.out_val;   // in place
-    size_t baseA[RPT], baseB[RPT];
-    bool ok[RPT];
-#pragma unroll
-    for (int r = 0; r < RPT; ++r) {
-        const int pp = threadIdx.x + r * kFullThreads, rb = pp / 3, k2 = 2 * (pp - 3 * rb);
-        ok[r] = rb < nk;
-        const int rr = ok[r] ? rb : 0;
-        const int row = a.cci_row[pa + k0 + rr];
-        baseA[r] = ((size_t)row * a.cap + a.cci_slot[pa + k0 + rr]) * kTileVals + k2 * kTileW;
-        baseB[r] = ((size_t)row * a.cap + a.cci_slot[pb + k0 + rr]) * kTileVals + k2 * kTileW;
-    }
     float* pr = panel + 2 * threadIdx.x;   // row pair r at pr + 2 r kFullThreads
-    float2 x[RPT][32];
+    for (int k0 = k_first; k0 < n_rows; k0 += gridDim.x * kFullCH) {
+        const int nk = min(kFullCH, n_rows - k0);
+        if (threadIdx.x == 0) atomicAdd(a.upd, (unsigned long long)np * (unsigned long long)(nk * 6));
+        // row pair r of this thread: pair index p = threadIdx.x + r * kFullThreads,
+        // row block p / 3, AO rows 2 (p % 3) and 2 (p % 3) + 1, panel rows 2p and 2p + 1
+        if (threadIdx.x / 3 >= nk) continue;
+        size_t baseA[RPT], baseB[RPT];
+        bool ok[RPT];
 #pragma unroll
-    for (int r = 0; r < RPT; ++r) {
-#pragma unroll
-        for (int t = 0; t < 2; ++t) {
-            float4 u0[4], u1[4];
-            if (ok[r]) {
-                load_pair_rows(val + baseA[r] + (size_t)t * kTileVals, u0, u1);
-            } else {
-#pragma unroll
-                for (int v = 0; v < 4; ++v) u0[v] = u1[v] = make_float4(0.f, 0.f, 0.f, 0.f);
-            }
-#pragma unroll
-            for (int v = 0; v < 4; ++v) {
-                x[r][t * 16 + 4 * v + 0] = make_float2(u0[v].x, u1[v].x);
-                x[r][t * 16 + 4 * v + 1] = make_float2(u0[v].y, u1[v].y);
-                x[r][t * 16 + 4 * v + 2] = make_float2(u0[v].z, u1[v].z);
-                x[r][t * 16 + 4 * v + 3] = make_float2(u0[v].w, u1[v].w);
-            }
+        for (int r = 0; r < RPT; ++r) {
+            const int pp = threadIdx.x + r * kFullThreads, rb = pp / 3, k2 = 2 * (pp - 3 * rb);
+            ok[r] = rb < nk;
+            const int rr = ok[r] ? rb : 0;
+            const int row = a.cci_row[pa + k0 + rr];
+            baseA[r] = ((size_t)row * a.cap + a.cci_slot[pa + k0 + rr]) * kTileVals + k2 * kTileW;
+            baseB[r] = ((size_t)row * a.cap + a.cci_slot[pb + k0 + rr]) * kTileVals + k2 * kTileW;
         }
+        float2 x[RPT][32];
 #pragma unroll
-        for (int t = 0; t < NB / 16; ++t) {
-            float4 v0[4], v1[4];
-            if (ok[r]) {
-                load_pair_rows(val + baseB[r] + (size_t)t * kTileVals, v0, v1);
-            } else {
+        for (int r = 0; r < RPT; ++r) {
 #pragma unroll
-                for (int v = 0; v < 4; ++v) v0[v] = v1[v] = make_float4(0.f, 0.f, 0.f, 0.f);
+            for (int t = 0; t < 2; ++t) {
+                float4 u0[4], u1[4];
+                if (ok[r]) {
+                    load_pair_rows(val + baseA[r] + (size_t)t * kTileVals, u0, u1);
+                } else {
+#pragma unroll
+                    for (int v = 0; v < 4; ++v) u0[v] = u1[v] = make_float4(0.f, 0.f, 0.f, 0.f);
+                }
+#pragma unroll
+                for (int v = 0; v < 4; ++v) {
+                    x[r][t * 16 + 4 * v + 0] = make_float2(u0[v].x, u1[v].x);
+                    x[r][t * 16 + 4 * v + 1] = make_float2(u0[v].y, u1[v].y);
+                    x[r][t * 16 + 4 * v + 2] = make_float2(u0[v].z, u1[v].z);
+                    x[r][t * 16 + 4 * v + 3] = make_float2(u0[v].w, u1[v].w);
+                }
             }
-            float* prr = pr + 2 * r * kFullThreads;
 #pragma unroll
-            for (int v = 0; v < 4; ++v) {
-                *(float2*)(prr + (t * 16 + 4 * v + 0) * kFullNR) = make_float2(v0[v].x, v1[v].x);
-                *(float2*)(prr + (t * 16 + 4 * v + 1) * kFullNR) = make_float2(v0[v].y, v1[v].y);
-                *(float2*)(prr + (t * 16 + 4 * v + 2) * kFullNR) = make_float2(v0[v].z, v1[v].z);
-                *(float2*)(prr + (t * 16 + 4 * v + 3) * kFullNR) = make_float2(v0[v].w, v1[v].w);
-            }
-        }
-    }
-    const float tf = a.trunc_f;
-    for (int lv = 0; lv < 32; ++lv) {
-        const unsigned m = s_mask[lv];
-        if (m == 0u) continue;
-        const Coef* cl = coef + lv * 32;
+            for (int t = 0; t < NB / 16; ++t) {
+                float4 v0[4], v1[4];
+                if (ok[r]) {
+                    load_pair_rows(val + baseB[r] + (size_t)t * kTileVals, v0, v1);
+                } else {
 #pragma unroll
-        for (int i = 0; i < 32; ++i) {
-            if (m & (1u << i)) {
-                float* py0 = pr + ((lv - i) & 31) * kFullNR;
-                const Coef c4 = cl[i];
-                float2 y[RPT];
+                    for (int v = 0; v < 4; ++v) v0[v] = v1[v] = make_float4(0.f, 0.f, 0.f, 0.f);
+                }
+                float* prr = pr + 2 * r * kFullThreads;
 #pragma unroll
-                for (int r = 0; r < RPT; ++r) y[r] = *(const float2*)(py0 + 2 * r * kFullThreads);
-#pragma unroll
-                for (int r = 0; r < RPT; ++r) {
-                    float2 xn, yn;
-                    if constexpr (MODE == 0) {
-                        const float2 cc = make_float2(c4.x, c4.y);
-                        xn = __ffma2_rn(cc, x[r][i], __fmul2_rn(make_float2(c4.z, c4.w), y[r]));
-                        yn = __ffma2_rn(cc, y[r], __fmul2_rn(make_float2(-c4.z, -c4.w), x[r][i]));
-                    } else {
-                        xn = __ffma2_rn(c4, y[r], x[r][i]);
-                        yn = __ffma2_rn(c4, x[r][i], y[r]);
-                    }
-                    x[r][i] = trunc2(xn, tf);
-                    *(float2*)(py0 + 2 * r * kFullThreads) = trunc2(yn, tf);
+                for (int v = 0; v < 4; ++v) {
+                    *(float2*)(prr + (t * 16 + 4 * v + 0) * kFullNR) = make_float2(v0[v].x, v1[v].x);
+                    *(float2*)(prr + (t * 16 + 4 * v + 1) * kFullNR) = make_float2(v0[v].y, v1[v].y);
+                    *(float2*)(prr + (t * 16 + 4 * v + 2) * kFullNR) = make_float2(v0[v].z, v1[v].z);
+                    *(float2*)(prr + (t * 16 + 4 * v + 3) * kFullNR) = make_float2(v0[v].w, v1[v].w);
                 }
             }
         }
-    }
+        const float tf = a.trunc_f;
+        for (int lv = 0; lv < 32; ++lv) {
+            const unsigned m = s_mask[lv];
+            if (m == 0u) continue;
+            const Coef* cl = coef + lv * 32;
 #pragma unroll
-    for (int r = 0; r < RPT; ++r) {
-        if (!ok[r]) continue;
+            for (int i = 0; i < 32; ++i) {
+                if (m & (1u << i)) {
+                    float* py0 = pr + ((lv - i) & 31) * kFullNR;
+                    const Coef c4 = cl[i];
+                    float2 y[RPT];
 #pragma unroll
-        for (int t = 0; t < 2; ++t) {
-            float4* d0 = (float4*)(val + baseA[r] + (size_t)t * kTileVals);
+                    for (int r = 0; r < RPT; ++r) y[r] = *(const float2*)(py0 + 2 * r * kFullThreads);
 #pragma unroll
-            for (int v = 0; v < 4; ++v) {
-                const float2 a0 = x[r][t * 16 + 4 * v], a1 = x[r][t * 16 + 4 * v + 1];
-                const float2 a2 = x[r][t * 16 + 4 * v + 2], a3 = x[r][t * 16 + 4 * v + 3];
-                d0[v] = make_float4(a0.x, a1.x, a2.x, a3.x);
-                d0[4 + v] = make_float4(a0.y, a1.y, a2.y, a3.y);
+                    for (int r = 0; r < RPT; ++r) {
+                        float2 xn, yn;
+                        if constexpr (MODE == 0) {
+                            const float2 cc = make_float2(c4.x, c4.y);
+                            xn = __ffma2_rn(cc, x[r][i], __fmul2_rn(make_float2(c4.z, c4.w), y[r]));
+                            yn = __ffma2_rn(cc, y[r], __fmul2_rn(make_float2(-c4.z, -c4.w), x[r][i]));
+                        } else {
+                            xn = __ffma2_rn(c4, y[r], x[r][i]);
+                            yn = __ffma2_rn(c4, x[r][i], y[r]);
+                        }
+                        x[r][i] = trunc2(xn, tf);
+                        *(float2*)(py0 + 2 * r * kFullThreads) = trunc2(yn, tf);
+                    }
+                }
             }
         }
-        const float* prr = pr + 2 * r * kFullThreads;
 #pragma unroll
-        for (int t = 0; t < NB / 16; ++t) {
-            float4* d1 = (float4*)(val + baseB[r] + (size_t)t * kTileVals);
+        for (int r = 0; r < RPT; ++r) {
+            if (!ok[r]) continue;
 #pragma unroll
-            for (int v = 0; v < 4; ++v) {
-                const float2 b0 = *(const float2*)(prr + (t * 16 + 4 * v + 0) * kFullNR);
-                const float2 b1 = *(const float2*)(prr + (t * 16 + 4 * v + 1) * kFullNR);
-                const float2 b2 = *(const float2*)(prr + (t * 16 + 4 * v + 2) * kFullNR);
-                const float2 b3 = *(const float2*)(prr + (t * 16 + 4 * v + 3) * kFullNR);
-                d1[v] = make_float4(b0.x, b1.x, b2.x, b3.x);
-                d1[4 + v] = make_float4(b0.y, b1.y, b2.y, b3.y);
+            for (int t = 0; t < 2; ++t) {
+                float4* d0 = (float4*)(val + baseA[r] + (size_t)t * kTileVals);
+#pragma unroll
+                for (int v = 0; v < 4; ++v) {
+                    const float2 a0 = x[r][t * 16 + 4 * v], a1 = x[r][t * 16 + 4 * v + 1];
+                    const float2 a2 = x[r][t * 16 + 4 * v + 2], a3 = x[r][t * 16 + 4 * v + 3];
+                    d0[v] = make_float4(a0.x, a1.x, a2.x, a3.x);
+                    d0[4 + v] = make_float4(a0.y, a1.y, a2.y, a3.y);
+                }
+            }
+            const float* prr = pr + 2 * r * kFullThreads;
+#pragma unroll
+            for (int t = 0; t < NB / 16; ++t) {
+                float4* d1 = (float4*)(val + baseB[r] + (size_t)t * kTileVals);
+#pragma unroll
+                for (int v = 0; v < 4; ++v) {
+                    const float2 b0 = *(const float2*)(prr + (t * 16 + 4 * v + 0) * kFullNR);
+                    const float2 b1 = *(const float2*)(prr + (t * 16 + 4 * v + 1) * kFullNR);
+                    const float2 b2 = *(const float2*)(prr + (t * 16 + 4 * v + 2) * kFullNR);
+                    const float2 b3 = *(const float2*)(prr + (t * 16 + 4 * v + 3) * kFullNR);
+                    d1[v] = make_float4(b0.x, b1.x, b2.x, b3.x);
+                    d1[4 + v] = make_float4(b0.y, b1.y, b2.y, b3.y);
+                }
             }
         }
-    }
+    }   // row chunks
 }
 
 // drop tiles whose 6x16 values are all zero; in -> out
@@ -1193,10 +1198,20 @@ static cudaError_t apply_mode_t(Ctx* c, int which) {
         if (e != cudaSuccess) return e;
     }
     const std::vector<int>& nfull = MODE == 0 ? c->h_colour_nfull : c->h_ocolour_nfull;
-    const int gxf = (c->n_mol + kFullCH - 1) / kFullCH;
+    // row chunks per block in x: enough CTAs to fill the GPU a few times over,
+    // each looping over its chunks with one coefficient table
+    static int full_occ[2] = {0, 0};
+    if (full && full_occ[MODE] == 0) {
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&full_occ[MODE], k_apply_full<MODE>, kFullThreads,
+                                                          full_apply_smem<MODE>());
+        if (e != cudaSuccess) return e;
+        full_occ[MODE] = std::max(full_occ[MODE], 1);
+    }
+    const int chunks = (c->n_mol + kFullCH - 1) / kFullCH;
     for (int col = 0; col < c->n_colours; ++col) {
         const int nf = full ? nfull[col] : 0;
         if (nf > 0) {
+            const int gxf = std::min(chunks, std::max(1, (kFullWaves * c->n_sm * full_occ[MODE] + nf - 1) / nf));
             k_apply_full<MODE><<<dim3(gxf, nf), kFullThreads, full_apply_smem<MODE>(), c->stream>>>(a, ptr[col]);
             c->n_launch += 1;
         }

@@ -85,6 +85,7 @@ struct Ctx {
     int capY = 0;        // row blocks per tile of Y
     int apply_variant = 0;   // 0 specialised sweep kernels where they apply, 1 generic only
     int tf_split = 4;        // CTAs sharing one occupied tile's pairs in the transform (sscf_autotune)
+    int n_sm = 152;          // multiprocessors of the context's device
     bool have_guess = false;
     int iteration = 0;
     long long n_launch = 0;   // kernels launched by this context
