@@ -403,6 +403,7 @@ struct SweepArgs {
     const int* tile_nmo;
     const int* pr_n;
     const int* pr_lvl;
+    const int* pr_touch;     // tiles of each side a block's pairs touch: bits 0-2 side A, 3-5 side B
     const uint16_t* pr_ij;
     const void* pr_cs;
     const double* dsc;       // combinations: divide the pass's MOs by d_i first
@@ -882,6 +883,8 @@ __global__ void __launch_bounds__(kFullThreads) k_apply_full(SweepArgs a, int p0
         atomicOr(&s_mask[lv], 1u << il);
     }
     __syncthreads();
+    // tiles no selected pair touches keep their values: neither loaded nor stored
+    const int touch = a.pr_touch[e];
     float* val = (float*)a.out_val;   // in place
     float* pr = panel + 2 * threadIdx.x;   // row pair r at pr + 2 r kFullThreads
     for (int k0 = k_first; k0 < n_rows; k0 += gridDim.x * kFullCH) {
@@ -907,7 +910,7 @@ __global__ void __launch_bounds__(kFullThreads) k_apply_full(SweepArgs a, int p0
 #pragma unroll
             for (int t = 0; t < 2; ++t) {
                 float4 u0[4], u1[4];
-                if (ok[r]) {
+                if (ok[r] && (touch >> t & 1)) {
                     load_pair_rows(val + baseA[r] + (size_t)t * kTileVals, u0, u1);
                 } else {
 #pragma unroll
@@ -924,7 +927,7 @@ __global__ void __launch_bounds__(kFullThreads) k_apply_full(SweepArgs a, int p0
 #pragma unroll
             for (int t = 0; t < NB / 16; ++t) {
                 float4 v0[4], v1[4];
-                if (ok[r]) {
+                if (ok[r] && (touch >> (3 + t) & 1)) {
                     load_pair_rows(val + baseB[r] + (size_t)t * kTileVals, v0, v1);
                 } else {
 #pragma unroll
@@ -975,6 +978,7 @@ __global__ void __launch_bounds__(kFullThreads) k_apply_full(SweepArgs a, int p0
             if (!ok[r]) continue;
 #pragma unroll
             for (int t = 0; t < 2; ++t) {
+                if (!(touch >> t & 1)) continue;
                 float4* d0 = (float4*)(val + baseA[r] + (size_t)t * kTileVals);
 #pragma unroll
                 for (int v = 0; v < 4; ++v) {
@@ -987,6 +991,7 @@ __global__ void __launch_bounds__(kFullThreads) k_apply_full(SweepArgs a, int p0
             const float* prr = pr + 2 * r * kFullThreads;
 #pragma unroll
             for (int t = 0; t < NB / 16; ++t) {
+                if (!(touch >> (3 + t) & 1)) continue;
                 float4* d1 = (float4*)(val + baseB[r] + (size_t)t * kTileVals);
 #pragma unroll
                 for (int v = 0; v < 4; ++v) {
@@ -1146,6 +1151,7 @@ static void fill_args(Ctx* c, SweepArgs& a, int mode, int which) {
     a.tile_nmo = c->d_tile_nmo;
     a.pr_n = c->d_pr_n;
     a.pr_lvl = c->d_pr_lvl;
+    a.pr_touch = c->d_pr_touch;
     a.pr_ij = c->d_pr_ij;
     a.pr_cs = c->d_pr_cs;
     a.dsc = c->d_scale;
