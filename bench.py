@@ -62,6 +62,19 @@ def parse():
     return ap.parse_args()
 
 
+def oracle_rate_one_core(n_mol: int, eps: float):
+    """The oracle's iteration rate with one BLAS thread, in a child process (thread counts are read at import)."""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    code = ("import json, bench; r = bench.oracle_iteration_rate(%d, %r, 1); print(json.dumps(r[:2]))"
+            % (n_mol, eps))
+    try:
+        out = subprocess.run([sys.executable, "-c", code], cwd=ROOT, env=env, capture_output=True, text=True,
+                             timeout=600)
+        return tuple(json.loads(out.stdout.strip().splitlines()[-1]))
+    except (subprocess.SubprocessError, ValueError, IndexError):
+        return None
+
+
 def host_cores() -> int:
     try:
         return len(os.sched_getaffinity(0))
@@ -393,6 +406,10 @@ def main():
         cpu = {"value": rate, "unit": UNIT, "cores": host_cores(), "kind": "oracle",
                "sample": f"3 SCC iterations of oracle B (FP64, numpy) on a {args.sample_mol}-molecule "
                          f"sub-cube ({n_at} atoms), {dt:.1f} s"}
+        one = oracle_rate_one_core(args.sample_mol, args.eps)
+        if one is not None:
+            cpu["one_core"] = {"value": one[0], "unit": UNIT, "cores": 1,
+                               "sample": f"1 SCC iteration of the same sample with one BLAS thread, {one[1]:.1f} s"}
 
     launches = int(round(mean("launches")))
     line = {
