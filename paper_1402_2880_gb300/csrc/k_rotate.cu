@@ -417,6 +417,7 @@ struct SweepArgs {
     int* out_nt;
     int* out_tile;
     void* out_val;
+    unsigned char* out_nz;   // flags of out: 0 = the tile is all zero (written by the closure, kept by the sweep)
     unsigned* err;
 };
 
@@ -525,6 +526,10 @@ __global__ void __launch_bounds__(256) k_closure(SweepArgs a) {
     }
     if (threadIdx.x == 0) a.out_nt[r] = n1;
     __syncthreads();
+    // tiles copied from the input survived the last compaction (or come from the
+    // guess or a restart) and may be nonzero; inserted tiles are zero
+    for (int s = threadIdx.x; s < n1; s += blockDim.x)
+        a.out_nz[(size_t)r * a.cap + s] = map[lt(a.out_tile[(size_t)r * a.cap + s])] >= 0 ? 1 : 0;
     const T* inv = (const T*)a.in_val;
     T* outv = (T*)a.out_val;
     for (int idx = threadIdx.x; idx < n1 * kTileVals; idx += blockDim.x) {
@@ -789,6 +794,7 @@ __global__ void __launch_bounds__(apply_threads<T>()) k_apply_colour(SweepArgs a
         const int rb = sg / (6 * NT), rem = sg - rb * (6 * NT), p = rem / 6, kr = rem - p * 6;
         const int sl = s_slot[rb][p];
         if (sl < 0) continue;
+        if (kr == 0) a.out_nz[(size_t)s_row[rb] * a.cap + sl] = 1;   // may be nonzero now
         V out[kVPer];
         T* e2 = (T*)out;
         const T* srcp = panel + (p * 16) * NRP + rb * 6 + kr;
@@ -805,17 +811,19 @@ __global__ void __launch_bounds__(apply_threads<T>()) k_apply_colour(SweepArgs a
 // occupied-pass combinations (MODE 1, A occupied x B occupied, A != B). The
 // in-block colour of such a block is (i + j) mod 32. Same updates, order and
 // truncation as k_apply_colour, laid out for fewer shared-memory round trips:
-// each thread owns kFullRPT pairs of adjacent AO rows; the 32 A-side values of those rows
+// each thread owns a pair of adjacent AO rows; the 32 A-side values of those rows
 // stay in registers (the index i is static once the slot loop is unrolled),
 // the NB B-side values sit in a thread-private shared-memory panel indexed by
 // j = (level - i) mod 32. The block's pairs are expanded into a dense
 // [level][i] coefficient table with a selection mask per level. No barrier is
 // needed after the table is built: a thread reads back only the rows it wrote.
+// A warp whose rows hold only zeros in the block's touched tiles (per-tile
+// flags written by the closure and raised by the sweep) skips its chunk: the
+// updates would leave those zeros as they are.
 constexpr int kFullWaves = 16;                    // resident-CTA multiples per launch (row chunks loop beyond)
-constexpr int kFullRPT = 1;                       // adjacent AO-row pairs per thread (2 measured slower)
-constexpr int kFullCH = 32 * kFullRPT;            // row blocks per CTA
+constexpr int kFullCH = 32;                       // row blocks per CTA
 constexpr int kFullNR = kFullCH * kAoPerMol;      // AO rows per CTA (panel stride, floats)
-constexpr int kFullThreads = kFullNR / (2 * kFullRPT);
+constexpr int kFullThreads = kFullNR / 2;         // one pair of adjacent AO rows per thread (two pairs measured slower)
 template <int MODE> struct FullShape;
 template <> struct FullShape<0> {   // rotations: B = one virtual tile, coefficients (c, c, s, s)
     static constexpr int nb = 16;
@@ -841,7 +849,10 @@ __device__ __forceinline__ void load_pair_rows(const float* src, float4 (&r0)[4]
 template <int MODE>
 __global__ void __launch_bounds__(kFullThreads) k_apply_full(SweepArgs a, int p0) {
     constexpr int NB = FullShape<MODE>::nb;
-    constexpr int RPT = kFullRPT;
+    // zero-row skipping pays in rotation sweeps (inserted virtual and occupied tiles
+    // stay zero for many colours); in occupied passes almost every row holds a
+    // nonzero tile and the checks cost more than they save (measured)
+    constexpr bool kFullSkip = MODE == 0;
     using Coef = typename FullShape<MODE>::Coef;
     extern __shared__ unsigned char smraw[];
     float* panel = (float*)smraw;                           // [NB B columns][kFullNR rows]
@@ -886,61 +897,74 @@ __global__ void __launch_bounds__(kFullThreads) k_apply_full(SweepArgs a, int p0
     // tiles no selected pair touches keep their values: neither loaded nor stored
     const int touch = a.pr_touch[e];
     float* val = (float*)a.out_val;   // in place
-    float* pr = panel + 2 * threadIdx.x;   // row pair r at pr + 2 r kFullThreads
+    float* pr = panel + 2 * threadIdx.x;   // this thread's two panel rows
+    const int lane = threadIdx.x & 31;
+    const int rb = threadIdx.x / 3, k2 = 2 * (threadIdx.x - 3 * rb);   // row block, first of two AO rows
     for (int k0 = k_first; k0 < n_rows; k0 += gridDim.x * kFullCH) {
         const int nk = min(kFullCH, n_rows - k0);
-        if (threadIdx.x == 0) atomicAdd(a.upd, (unsigned long long)np * (unsigned long long)(nk * 6));
-        // row pair r of this thread: pair index p = threadIdx.x + r * kFullThreads,
-        // row block p / 3, AO rows 2 (p % 3) and 2 (p % 3) + 1, panel rows 2p and 2p + 1
-        if (threadIdx.x / 3 >= nk) continue;
-        size_t baseA[RPT], baseB[RPT];
-        bool ok[RPT];
+        const bool act = rb < nk;
+        int row = 0, slA = 0, slB = 0;
+        if constexpr (kFullSkip) {
+            bool nz = false;
+            if (act) {
+                row = a.cci_row[pa + k0 + rb];
+                slA = a.cci_slot[pa + k0 + rb];
+                slB = a.cci_slot[pb + k0 + rb];
+                const unsigned char* f = a.out_nz + (size_t)row * a.cap;
 #pragma unroll
-        for (int r = 0; r < RPT; ++r) {
-            const int pp = threadIdx.x + r * kFullThreads, rb = pp / 3, k2 = 2 * (pp - 3 * rb);
-            ok[r] = rb < nk;
-            const int rr = ok[r] ? rb : 0;
-            const int row = a.cci_row[pa + k0 + rr];
-            baseA[r] = ((size_t)row * a.cap + a.cci_slot[pa + k0 + rr]) * kTileVals + k2 * kTileW;
-            baseB[r] = ((size_t)row * a.cap + a.cci_slot[pb + k0 + rr]) * kTileVals + k2 * kTileW;
+                for (int t = 0; t < 2; ++t) nz |= (touch >> t & 1) && f[slA + t];
+#pragma unroll
+                for (int t = 0; t < NB / 16; ++t) nz |= (touch >> (3 + t) & 1) && f[slB + t];
+            }
+            // rows whose touched tiles are all zero stay zero under the block's updates
+            // (x - c y and c x + s y of zeros, truncation keeps zeros): a warp whose
+            // rows are all such skips the chunk
+            if (__ballot_sync(0xffffffffu, nz) == 0u) continue;
+            const unsigned live = __ballot_sync(0xffffffffu, act);
+            if (lane == 0) atomicAdd(a.upd, (unsigned long long)np * (unsigned long long)(2 * __popc(live)));
+            if (!act) continue;
+        } else {
+            if (threadIdx.x == 0) atomicAdd(a.upd, (unsigned long long)np * (unsigned long long)(nk * 6));
+            if (!act) continue;
+            row = a.cci_row[pa + k0 + rb];
+            slA = a.cci_slot[pa + k0 + rb];
+            slB = a.cci_slot[pb + k0 + rb];
         }
-        float2 x[RPT][32];
+        const size_t baseA = ((size_t)row * a.cap + slA) * kTileVals + k2 * kTileW;
+        const size_t baseB = ((size_t)row * a.cap + slB) * kTileVals + k2 * kTileW;
+        float2 x[32];
 #pragma unroll
-        for (int r = 0; r < RPT; ++r) {
+        for (int t = 0; t < 2; ++t) {
+            float4 u0[4], u1[4];
+            if (touch >> t & 1) {
+                load_pair_rows(val + baseA + (size_t)t * kTileVals, u0, u1);
+            } else {
 #pragma unroll
-            for (int t = 0; t < 2; ++t) {
-                float4 u0[4], u1[4];
-                if (ok[r] && (touch >> t & 1)) {
-                    load_pair_rows(val + baseA[r] + (size_t)t * kTileVals, u0, u1);
-                } else {
-#pragma unroll
-                    for (int v = 0; v < 4; ++v) u0[v] = u1[v] = make_float4(0.f, 0.f, 0.f, 0.f);
-                }
-#pragma unroll
-                for (int v = 0; v < 4; ++v) {
-                    x[r][t * 16 + 4 * v + 0] = make_float2(u0[v].x, u1[v].x);
-                    x[r][t * 16 + 4 * v + 1] = make_float2(u0[v].y, u1[v].y);
-                    x[r][t * 16 + 4 * v + 2] = make_float2(u0[v].z, u1[v].z);
-                    x[r][t * 16 + 4 * v + 3] = make_float2(u0[v].w, u1[v].w);
-                }
+                for (int v = 0; v < 4; ++v) u0[v] = u1[v] = make_float4(0.f, 0.f, 0.f, 0.f);
             }
 #pragma unroll
-            for (int t = 0; t < NB / 16; ++t) {
-                float4 v0[4], v1[4];
-                if (ok[r] && (touch >> (3 + t) & 1)) {
-                    load_pair_rows(val + baseB[r] + (size_t)t * kTileVals, v0, v1);
-                } else {
+            for (int v = 0; v < 4; ++v) {
+                x[t * 16 + 4 * v + 0] = make_float2(u0[v].x, u1[v].x);
+                x[t * 16 + 4 * v + 1] = make_float2(u0[v].y, u1[v].y);
+                x[t * 16 + 4 * v + 2] = make_float2(u0[v].z, u1[v].z);
+                x[t * 16 + 4 * v + 3] = make_float2(u0[v].w, u1[v].w);
+            }
+        }
 #pragma unroll
-                    for (int v = 0; v < 4; ++v) v0[v] = v1[v] = make_float4(0.f, 0.f, 0.f, 0.f);
-                }
-                float* prr = pr + 2 * r * kFullThreads;
+        for (int t = 0; t < NB / 16; ++t) {
+            float4 v0[4], v1[4];
+            if (touch >> (3 + t) & 1) {
+                load_pair_rows(val + baseB + (size_t)t * kTileVals, v0, v1);
+            } else {
 #pragma unroll
-                for (int v = 0; v < 4; ++v) {
-                    *(float2*)(prr + (t * 16 + 4 * v + 0) * kFullNR) = make_float2(v0[v].x, v1[v].x);
-                    *(float2*)(prr + (t * 16 + 4 * v + 1) * kFullNR) = make_float2(v0[v].y, v1[v].y);
-                    *(float2*)(prr + (t * 16 + 4 * v + 2) * kFullNR) = make_float2(v0[v].z, v1[v].z);
-                    *(float2*)(prr + (t * 16 + 4 * v + 3) * kFullNR) = make_float2(v0[v].w, v1[v].w);
-                }
+                for (int v = 0; v < 4; ++v) v0[v] = v1[v] = make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+#pragma unroll
+            for (int v = 0; v < 4; ++v) {
+                *(float2*)(pr + (t * 16 + 4 * v + 0) * kFullNR) = make_float2(v0[v].x, v1[v].x);
+                *(float2*)(pr + (t * 16 + 4 * v + 1) * kFullNR) = make_float2(v0[v].y, v1[v].y);
+                *(float2*)(pr + (t * 16 + 4 * v + 2) * kFullNR) = make_float2(v0[v].z, v1[v].z);
+                *(float2*)(pr + (t * 16 + 4 * v + 3) * kFullNR) = make_float2(v0[v].w, v1[v].w);
             }
         }
         const float tf = a.trunc_f;
@@ -951,58 +975,59 @@ __global__ void __launch_bounds__(kFullThreads) k_apply_full(SweepArgs a, int p0
 #pragma unroll
             for (int i = 0; i < 32; ++i) {
                 if (m & (1u << i)) {
-                    float* py0 = pr + ((lv - i) & 31) * kFullNR;
+                    float2* py = (float2*)(pr + ((lv - i) & 31) * kFullNR);
                     const Coef c4 = cl[i];
-                    float2 y[RPT];
-#pragma unroll
-                    for (int r = 0; r < RPT; ++r) y[r] = *(const float2*)(py0 + 2 * r * kFullThreads);
-#pragma unroll
-                    for (int r = 0; r < RPT; ++r) {
-                        float2 xn, yn;
-                        if constexpr (MODE == 0) {
-                            const float2 cc = make_float2(c4.x, c4.y);
-                            xn = __ffma2_rn(cc, x[r][i], __fmul2_rn(make_float2(c4.z, c4.w), y[r]));
-                            yn = __ffma2_rn(cc, y[r], __fmul2_rn(make_float2(-c4.z, -c4.w), x[r][i]));
-                        } else {
-                            xn = __ffma2_rn(c4, y[r], x[r][i]);
-                            yn = __ffma2_rn(c4, x[r][i], y[r]);
-                        }
-                        x[r][i] = trunc2(xn, tf);
-                        *(float2*)(py0 + 2 * r * kFullThreads) = trunc2(yn, tf);
+                    const float2 y = *py;
+                    float2 xn, yn;
+                    if constexpr (MODE == 0) {
+                        const float2 cc = make_float2(c4.x, c4.y);
+                        xn = __ffma2_rn(cc, x[i], __fmul2_rn(make_float2(c4.z, c4.w), y));
+                        yn = __ffma2_rn(cc, y, __fmul2_rn(make_float2(-c4.z, -c4.w), x[i]));
+                    } else {
+                        xn = __ffma2_rn(c4, y, x[i]);
+                        yn = __ffma2_rn(c4, x[i], y);
                     }
+                    x[i] = trunc2(xn, tf);
+                    *py = trunc2(yn, tf);
                 }
             }
         }
+        // store, and mark the tiles that hold a nonzero value now (a flag is never
+        // cleared during the sweep: 1 only means "may be nonzero")
+        unsigned char* f = a.out_nz + (size_t)row * a.cap;
 #pragma unroll
-        for (int r = 0; r < RPT; ++r) {
-            if (!ok[r]) continue;
+        for (int t = 0; t < 2; ++t) {
+            if (!(touch >> t & 1)) continue;
+            float4* d0 = (float4*)(val + baseA + (size_t)t * kTileVals);
+            bool any = false;
 #pragma unroll
-            for (int t = 0; t < 2; ++t) {
-                if (!(touch >> t & 1)) continue;
-                float4* d0 = (float4*)(val + baseA[r] + (size_t)t * kTileVals);
-#pragma unroll
-                for (int v = 0; v < 4; ++v) {
-                    const float2 a0 = x[r][t * 16 + 4 * v], a1 = x[r][t * 16 + 4 * v + 1];
-                    const float2 a2 = x[r][t * 16 + 4 * v + 2], a3 = x[r][t * 16 + 4 * v + 3];
-                    d0[v] = make_float4(a0.x, a1.x, a2.x, a3.x);
-                    d0[4 + v] = make_float4(a0.y, a1.y, a2.y, a3.y);
-                }
+            for (int v = 0; v < 4; ++v) {
+                const float2 a0 = x[t * 16 + 4 * v], a1 = x[t * 16 + 4 * v + 1];
+                const float2 a2 = x[t * 16 + 4 * v + 2], a3 = x[t * 16 + 4 * v + 3];
+                d0[v] = make_float4(a0.x, a1.x, a2.x, a3.x);
+                d0[4 + v] = make_float4(a0.y, a1.y, a2.y, a3.y);
+                any |= a0.x != 0.f || a0.y != 0.f || a1.x != 0.f || a1.y != 0.f || a2.x != 0.f || a2.y != 0.f ||
+                       a3.x != 0.f || a3.y != 0.f;
             }
-            const float* prr = pr + 2 * r * kFullThreads;
+            if (kFullSkip && any) f[slA + t] = 1;
+        }
 #pragma unroll
-            for (int t = 0; t < NB / 16; ++t) {
-                if (!(touch >> (3 + t) & 1)) continue;
-                float4* d1 = (float4*)(val + baseB[r] + (size_t)t * kTileVals);
+        for (int t = 0; t < NB / 16; ++t) {
+            if (!(touch >> (3 + t) & 1)) continue;
+            float4* d1 = (float4*)(val + baseB + (size_t)t * kTileVals);
+            bool any = false;
 #pragma unroll
-                for (int v = 0; v < 4; ++v) {
-                    const float2 b0 = *(const float2*)(prr + (t * 16 + 4 * v + 0) * kFullNR);
-                    const float2 b1 = *(const float2*)(prr + (t * 16 + 4 * v + 1) * kFullNR);
-                    const float2 b2 = *(const float2*)(prr + (t * 16 + 4 * v + 2) * kFullNR);
-                    const float2 b3 = *(const float2*)(prr + (t * 16 + 4 * v + 3) * kFullNR);
-                    d1[v] = make_float4(b0.x, b1.x, b2.x, b3.x);
-                    d1[4 + v] = make_float4(b0.y, b1.y, b2.y, b3.y);
-                }
+            for (int v = 0; v < 4; ++v) {
+                const float2 b0 = *(const float2*)(pr + (t * 16 + 4 * v + 0) * kFullNR);
+                const float2 b1 = *(const float2*)(pr + (t * 16 + 4 * v + 1) * kFullNR);
+                const float2 b2 = *(const float2*)(pr + (t * 16 + 4 * v + 2) * kFullNR);
+                const float2 b3 = *(const float2*)(pr + (t * 16 + 4 * v + 3) * kFullNR);
+                d1[v] = make_float4(b0.x, b1.x, b2.x, b3.x);
+                d1[4 + v] = make_float4(b0.y, b1.y, b2.y, b3.y);
+                any |= b0.x != 0.f || b0.y != 0.f || b1.x != 0.f || b1.y != 0.f || b2.x != 0.f || b2.y != 0.f ||
+                       b3.x != 0.f || b3.y != 0.f;
             }
+            if (kFullSkip && any) f[slB + t] = 1;
         }
     }   // row chunks
 }
@@ -1173,6 +1198,7 @@ static cudaError_t closure_t(Ctx* c, int mode, int which) {
     a.out_nt = c->d_c_nt[out];
     a.out_tile = c->d_c_tile[out];
     a.out_val = c->d_c_val[out];
+    a.out_nz = c->d_c_nz[out];
     const size_t smem = closure_smem_bytes(c);
     if (smem > (size_t)kMaxDynSmem) return cudaErrorInvalidValue;
     cudaError_t e = cudaFuncSetAttribute(k_closure<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -1189,6 +1215,7 @@ static cudaError_t apply_mode_t(Ctx* c, int which) {
     a.in_nt = a.out_nt = c->d_c_nt[c->cur];
     a.in_tile = a.out_tile = c->d_c_tile[c->cur];
     a.in_val = a.out_val = c->d_c_val[c->cur];
+    a.out_nz = c->d_c_nz[c->cur];
     const size_t smem = (size_t)NT * 16 * apply_nrp<T>() * sizeof(T) + (size_t)2 * PCAP * sizeof(T) + (size_t)PCAP * 4;
     cudaError_t e = cudaFuncSetAttribute(k_apply_colour<T, MODE, NT, PCAP>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -1217,7 +1244,7 @@ static cudaError_t apply_mode_t(Ctx* c, int which) {
     for (int col = 0; col < c->n_colours; ++col) {
         const int nf = full ? nfull[col] : 0;
         if (nf > 0) {
-            const int gxf = std::min(chunks, std::max(1, (kFullWaves * c->n_sm * full_occ[MODE] + nf - 1) / nf));
+            const int gxf = std::min(chunks, std::max(1, (kFullWaves * c->n_sm * full_occ[MODE]) / std::max(nf, 1) + 1));
             k_apply_full<MODE><<<dim3(gxf, nf), kFullThreads, full_apply_smem<MODE>(), c->stream>>>(a, ptr[col]);
             c->n_launch += 1;
         }

@@ -176,6 +176,7 @@ struct Ctx {
     int* d_c_nt[2] = {nullptr, nullptr};
     int* d_c_tile[2] = {nullptr, nullptr};
     void* d_c_val[2] = {nullptr, nullptr};
+    unsigned char* d_c_nz[2] = {nullptr, nullptr};   // per (row block, slot): 0 = tile known all-zero during a sweep
     int cur = 0;
     int* d_cci_ptr = nullptr;     // n_tiles + 1
     int* d_cci_cnt = nullptr;     // n_tiles
