@@ -898,12 +898,14 @@ __global__ void __launch_bounds__(kFullThreads) k_apply_full(SweepArgs a, int p0
     const int touch = a.pr_touch[e];
     float* val = (float*)a.out_val;   // in place
     float* pr = panel + 2 * threadIdx.x;   // this thread's two panel rows
-    const int lane = threadIdx.x & 31;
     const int rb = threadIdx.x / 3, k2 = 2 * (threadIdx.x - 3 * rb);   // row block, first of two AO rows
     for (int k0 = k_first; k0 < n_rows; k0 += gridDim.x * kFullCH) {
         const int nk = min(kFullCH, n_rows - k0);
         const bool act = rb < nk;
         int row = 0, slA = 0, slB = 0;
+        // the counter holds the 2x2 row updates the algorithm defines, rows proven
+        // unchanged and skipped below included
+        if (threadIdx.x == 0) atomicAdd(a.upd, (unsigned long long)np * (unsigned long long)(nk * 6));
         if constexpr (kFullSkip) {
             bool nz = false;
             if (act) {
@@ -920,11 +922,8 @@ __global__ void __launch_bounds__(kFullThreads) k_apply_full(SweepArgs a, int p0
             // (x - c y and c x + s y of zeros, truncation keeps zeros): a warp whose
             // rows are all such skips the chunk
             if (__ballot_sync(0xffffffffu, nz) == 0u) continue;
-            const unsigned live = __ballot_sync(0xffffffffu, act);
-            if (lane == 0) atomicAdd(a.upd, (unsigned long long)np * (unsigned long long)(2 * __popc(live)));
             if (!act) continue;
         } else {
-            if (threadIdx.x == 0) atomicAdd(a.upd, (unsigned long long)np * (unsigned long long)(nk * 6));
             if (!act) continue;
             row = a.cci_row[pa + k0 + rb];
             slA = a.cci_slot[pa + k0 + rb];
@@ -933,6 +932,7 @@ __global__ void __launch_bounds__(kFullThreads) k_apply_full(SweepArgs a, int p0
         const size_t baseA = ((size_t)row * a.cap + slA) * kTileVals + k2 * kTileW;
         const size_t baseB = ((size_t)row * a.cap + slB) * kTileVals + k2 * kTileW;
         float2 x[32];
+        unsigned bits = 0u;   // OR of the magnitudes' bit patterns of everything loaded
 #pragma unroll
         for (int t = 0; t < 2; ++t) {
             float4 u0[4], u1[4];
@@ -944,6 +944,9 @@ __global__ void __launch_bounds__(kFullThreads) k_apply_full(SweepArgs a, int p0
             }
 #pragma unroll
             for (int v = 0; v < 4; ++v) {
+                bits |= __float_as_uint(u0[v].x) | __float_as_uint(u0[v].y) | __float_as_uint(u0[v].z) |
+                        __float_as_uint(u0[v].w) | __float_as_uint(u1[v].x) | __float_as_uint(u1[v].y) |
+                        __float_as_uint(u1[v].z) | __float_as_uint(u1[v].w);
                 x[t * 16 + 4 * v + 0] = make_float2(u0[v].x, u1[v].x);
                 x[t * 16 + 4 * v + 1] = make_float2(u0[v].y, u1[v].y);
                 x[t * 16 + 4 * v + 2] = make_float2(u0[v].z, u1[v].z);
@@ -961,12 +964,17 @@ __global__ void __launch_bounds__(kFullThreads) k_apply_full(SweepArgs a, int p0
             }
 #pragma unroll
             for (int v = 0; v < 4; ++v) {
+                bits |= __float_as_uint(v0[v].x) | __float_as_uint(v0[v].y) | __float_as_uint(v0[v].z) |
+                        __float_as_uint(v0[v].w) | __float_as_uint(v1[v].x) | __float_as_uint(v1[v].y) |
+                        __float_as_uint(v1[v].z) | __float_as_uint(v1[v].w);
                 *(float2*)(pr + (t * 16 + 4 * v + 0) * kFullNR) = make_float2(v0[v].x, v1[v].x);
                 *(float2*)(pr + (t * 16 + 4 * v + 1) * kFullNR) = make_float2(v0[v].y, v1[v].y);
                 *(float2*)(pr + (t * 16 + 4 * v + 2) * kFullNR) = make_float2(v0[v].z, v1[v].z);
                 *(float2*)(pr + (t * 16 + 4 * v + 3) * kFullNR) = make_float2(v0[v].w, v1[v].w);
             }
         }
+        // a warp whose loaded values are all zero has nothing to update or store
+        if (__ballot_sync(__activemask(), (bits & 0x7fffffffu) != 0u) == 0u) continue;
         const float tf = a.trunc_f;
         for (int lv = 0; lv < 32; ++lv) {
             const unsigned m = s_mask[lv];
