@@ -794,12 +794,16 @@ __global__ void __launch_bounds__(apply_threads<T>()) k_apply_colour(SweepArgs a
         const int rb = sg / (6 * NT), rem = sg - rb * (6 * NT), p = rem / 6, kr = rem - p * 6;
         const int sl = s_slot[rb][p];
         if (sl < 0) continue;
-        if (kr == 0) a.out_nz[(size_t)s_row[rb] * a.cap + sl] = 1;   // may be nonzero now
         V out[kVPer];
         T* e2 = (T*)out;
         const T* srcp = panel + (p * 16) * NRP + rb * 6 + kr;
+        bool any = false;
 #pragma unroll
-        for (int col = 0; col < 16; ++col) e2[col] = srcp[col * NRP];
+        for (int col = 0; col < 16; ++col) {
+            e2[col] = srcp[col * NRP];
+            any |= e2[col] != (T)0;
+        }
+        if (any) a.out_nz[(size_t)s_row[rb] * a.cap + sl] = 1;   // the tile may be nonzero now
         V* dst = (V*)(val + ((size_t)s_row[rb] * a.cap + sl) * kTileVals + kr * 16);
 #pragma unroll
         for (int v = 0; v < kVPer; ++v) dst[v] = out[v];
@@ -820,6 +824,7 @@ __global__ void __launch_bounds__(apply_threads<T>()) k_apply_colour(SweepArgs a
 // A warp whose rows hold only zeros in the block's touched tiles (per-tile
 // flags written by the closure and raised by the sweep) skips its chunk: the
 // updates would leave those zeros as they are.
+constexpr int kFullSkipModes = 3;                 // bit m: mode m checks the tile flags before loading
 constexpr int kFullWaves = 16;                    // resident-CTA multiples per launch (row chunks loop beyond)
 constexpr int kFullCH = 32;                       // row blocks per CTA
 constexpr int kFullNR = kFullCH * kAoPerMol;      // AO rows per CTA (panel stride, floats)
@@ -849,10 +854,11 @@ __device__ __forceinline__ void load_pair_rows(const float* src, float4 (&r0)[4]
 template <int MODE>
 __global__ void __launch_bounds__(kFullThreads) k_apply_full(SweepArgs a, int p0) {
     constexpr int NB = FullShape<MODE>::nb;
-    // zero-row skipping pays in rotation sweeps (inserted virtual and occupied tiles
-    // stay zero for many colours); in occupied passes almost every row holds a
-    // nonzero tile and the checks cost more than they save (measured)
-    constexpr bool kFullSkip = MODE == 0;
+    // tiles the closure inserted stay zero for many colours, so the flag check
+    // before loading skips many row chunks of a rotation sweep (27.5 -> 16.4 ms at
+    // 4096 molecules); in occupied passes most zero chunks are caught after
+    // loading, and the check before it adds little (112.5 -> 111.7 ms)
+    constexpr bool kFullSkip = kFullSkipModes >> MODE & 1;
     using Coef = typename FullShape<MODE>::Coef;
     extern __shared__ unsigned char smraw[];
     float* panel = (float*)smraw;                           // [NB B columns][kFullNR rows]
