@@ -903,146 +903,176 @@ __global__ void __launch_bounds__(kFullThreads) k_apply_full(SweepArgs a, int p0
     // tiles no selected pair touches keep their values: neither loaded nor stored
     const int touch = a.pr_touch[e];
     float* val = (float*)a.out_val;   // in place
-    float* pr = panel + 2 * threadIdx.x;   // this thread's two panel rows
-    const int rb = threadIdx.x / 3, k2 = 2 * (threadIdx.x - 3 * rb);   // row block, first of two AO rows
+    // Each row chunk runs in two phases. First every thread loads its own row
+    // pair (the B side into its panel rows) and tells whether any value it
+    // loaded is nonzero; rows whose touched tiles are all zero stay zero under
+    // the block's updates (x - c y and c x + s y of zeros, truncation keeps
+    // zeros). The row pairs with work are then packed to the first threads of
+    // the CTA, which reload the A side and run the updates, so that whole warps
+    // of zero rows go idle.
+    __shared__ int s_src[kFullThreads];
+    __shared__ int s_wcnt[kFullThreads / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int rb = threadIdx.x / 3, k2 = 2 * (threadIdx.x - 3 * rb);   // own row block, first of two AO rows
     for (int k0 = k_first; k0 < n_rows; k0 += gridDim.x * kFullCH) {
         const int nk = min(kFullCH, n_rows - k0);
-        const bool act = rb < nk;
-        int row = 0, slA = 0, slB = 0;
         // the counter holds the 2x2 row updates the algorithm defines, rows proven
-        // unchanged and skipped below included
+        // unchanged and skipped included
         if (threadIdx.x == 0) atomicAdd(a.upd, (unsigned long long)np * (unsigned long long)(nk * 6));
-        if constexpr (kFullSkip) {
-            bool nz = false;
-            if (act) {
-                row = a.cci_row[pa + k0 + rb];
-                slA = a.cci_slot[pa + k0 + rb];
-                slB = a.cci_slot[pb + k0 + rb];
+        bool work = false;
+        if (rb < nk) {
+            const int row = a.cci_row[pa + k0 + rb];
+            const int slA = a.cci_slot[pa + k0 + rb], slB = a.cci_slot[pb + k0 + rb];
+            bool nz = true;
+            if constexpr (kFullSkip) {
                 const unsigned char* f = a.out_nz + (size_t)row * a.cap;
+                nz = false;
 #pragma unroll
                 for (int t = 0; t < 2; ++t) nz |= (touch >> t & 1) && f[slA + t];
 #pragma unroll
                 for (int t = 0; t < NB / 16; ++t) nz |= (touch >> (3 + t) & 1) && f[slB + t];
             }
-            // rows whose touched tiles are all zero stay zero under the block's updates
-            // (x - c y and c x + s y of zeros, truncation keeps zeros): a warp whose
-            // rows are all such skips the chunk
-            if (__ballot_sync(0xffffffffu, nz) == 0u) continue;
-            if (!act) continue;
-        } else {
-            if (!act) continue;
-            row = a.cci_row[pa + k0 + rb];
-            slA = a.cci_slot[pa + k0 + rb];
-            slB = a.cci_slot[pb + k0 + rb];
-        }
-        const size_t baseA = ((size_t)row * a.cap + slA) * kTileVals + k2 * kTileW;
-        const size_t baseB = ((size_t)row * a.cap + slB) * kTileVals + k2 * kTileW;
-        float2 x[32];
-        unsigned bits = 0u;   // OR of the magnitudes' bit patterns of everything loaded
+            if (nz) {
+                unsigned bits = 0u;   // OR of the bit patterns of everything loaded
+                const size_t baseA = ((size_t)row * a.cap + slA) * kTileVals + k2 * kTileW;
+                const size_t baseB = ((size_t)row * a.cap + slB) * kTileVals + k2 * kTileW;
 #pragma unroll
-        for (int t = 0; t < 2; ++t) {
-            float4 u0[4], u1[4];
-            if (touch >> t & 1) {
-                load_pair_rows(val + baseA + (size_t)t * kTileVals, u0, u1);
-            } else {
+                for (int t = 0; t < 2; ++t) {
+                    if (!(touch >> t & 1)) continue;
+                    float4 u0[4], u1[4];
+                    load_pair_rows(val + baseA + (size_t)t * kTileVals, u0, u1);
 #pragma unroll
-                for (int v = 0; v < 4; ++v) u0[v] = u1[v] = make_float4(0.f, 0.f, 0.f, 0.f);
-            }
+                    for (int v = 0; v < 4; ++v)
+                        bits |= __float_as_uint(u0[v].x) | __float_as_uint(u0[v].y) | __float_as_uint(u0[v].z) |
+                                __float_as_uint(u0[v].w) | __float_as_uint(u1[v].x) | __float_as_uint(u1[v].y) |
+                                __float_as_uint(u1[v].z) | __float_as_uint(u1[v].w);
+                }
+                float* pw = panel + 2 * threadIdx.x;
 #pragma unroll
-            for (int v = 0; v < 4; ++v) {
-                bits |= __float_as_uint(u0[v].x) | __float_as_uint(u0[v].y) | __float_as_uint(u0[v].z) |
-                        __float_as_uint(u0[v].w) | __float_as_uint(u1[v].x) | __float_as_uint(u1[v].y) |
-                        __float_as_uint(u1[v].z) | __float_as_uint(u1[v].w);
-                x[t * 16 + 4 * v + 0] = make_float2(u0[v].x, u1[v].x);
-                x[t * 16 + 4 * v + 1] = make_float2(u0[v].y, u1[v].y);
-                x[t * 16 + 4 * v + 2] = make_float2(u0[v].z, u1[v].z);
-                x[t * 16 + 4 * v + 3] = make_float2(u0[v].w, u1[v].w);
-            }
-        }
-#pragma unroll
-        for (int t = 0; t < NB / 16; ++t) {
-            float4 v0[4], v1[4];
-            if (touch >> (3 + t) & 1) {
-                load_pair_rows(val + baseB + (size_t)t * kTileVals, v0, v1);
-            } else {
-#pragma unroll
-                for (int v = 0; v < 4; ++v) v0[v] = v1[v] = make_float4(0.f, 0.f, 0.f, 0.f);
-            }
-#pragma unroll
-            for (int v = 0; v < 4; ++v) {
-                bits |= __float_as_uint(v0[v].x) | __float_as_uint(v0[v].y) | __float_as_uint(v0[v].z) |
-                        __float_as_uint(v0[v].w) | __float_as_uint(v1[v].x) | __float_as_uint(v1[v].y) |
-                        __float_as_uint(v1[v].z) | __float_as_uint(v1[v].w);
-                *(float2*)(pr + (t * 16 + 4 * v + 0) * kFullNR) = make_float2(v0[v].x, v1[v].x);
-                *(float2*)(pr + (t * 16 + 4 * v + 1) * kFullNR) = make_float2(v0[v].y, v1[v].y);
-                *(float2*)(pr + (t * 16 + 4 * v + 2) * kFullNR) = make_float2(v0[v].z, v1[v].z);
-                *(float2*)(pr + (t * 16 + 4 * v + 3) * kFullNR) = make_float2(v0[v].w, v1[v].w);
-            }
-        }
-        // a warp whose loaded values are all zero has nothing to update or store
-        if (__ballot_sync(__activemask(), (bits & 0x7fffffffu) != 0u) == 0u) continue;
-        const float tf = a.trunc_f;
-        for (int lv = 0; lv < 32; ++lv) {
-            const unsigned m = s_mask[lv];
-            if (m == 0u) continue;
-            const Coef* cl = coef + lv * 32;
-#pragma unroll
-            for (int i = 0; i < 32; ++i) {
-                if (m & (1u << i)) {
-                    float2* py = (float2*)(pr + ((lv - i) & 31) * kFullNR);
-                    const Coef c4 = cl[i];
-                    const float2 y = *py;
-                    float2 xn, yn;
-                    if constexpr (MODE == 0) {
-                        const float2 cc = make_float2(c4.x, c4.y);
-                        xn = __ffma2_rn(cc, x[i], __fmul2_rn(make_float2(c4.z, c4.w), y));
-                        yn = __ffma2_rn(cc, y, __fmul2_rn(make_float2(-c4.z, -c4.w), x[i]));
+                for (int t = 0; t < NB / 16; ++t) {
+                    float4 v0[4], v1[4];
+                    if (touch >> (3 + t) & 1) {
+                        load_pair_rows(val + baseB + (size_t)t * kTileVals, v0, v1);
                     } else {
-                        xn = __ffma2_rn(c4, y, x[i]);
-                        yn = __ffma2_rn(c4, x[i], y);
+#pragma unroll
+                        for (int v = 0; v < 4; ++v) v0[v] = v1[v] = make_float4(0.f, 0.f, 0.f, 0.f);
                     }
-                    x[i] = trunc2(xn, tf);
-                    *py = trunc2(yn, tf);
+#pragma unroll
+                    for (int v = 0; v < 4; ++v) {
+                        bits |= __float_as_uint(v0[v].x) | __float_as_uint(v0[v].y) | __float_as_uint(v0[v].z) |
+                                __float_as_uint(v0[v].w) | __float_as_uint(v1[v].x) | __float_as_uint(v1[v].y) |
+                                __float_as_uint(v1[v].z) | __float_as_uint(v1[v].w);
+                        *(float2*)(pw + (t * 16 + 4 * v + 0) * kFullNR) = make_float2(v0[v].x, v1[v].x);
+                        *(float2*)(pw + (t * 16 + 4 * v + 1) * kFullNR) = make_float2(v0[v].y, v1[v].y);
+                        *(float2*)(pw + (t * 16 + 4 * v + 2) * kFullNR) = make_float2(v0[v].z, v1[v].z);
+                        *(float2*)(pw + (t * 16 + 4 * v + 3) * kFullNR) = make_float2(v0[v].w, v1[v].w);
+                    }
+                }
+                work = (bits & 0x7fffffffu) != 0u;
+            }
+        }
+        // pack the row pairs with work to the first threads
+        const unsigned bal = __ballot_sync(0xffffffffu, work);
+        if (lane == 0) s_wcnt[warp] = __popc(bal);
+        __syncthreads();
+        int before = 0, n_work = 0;
+#pragma unroll
+        for (int w = 0; w < kFullThreads / 32; ++w) {
+            before += w < warp ? s_wcnt[w] : 0;
+            n_work += s_wcnt[w];
+        }
+        if (work) s_src[before + __popc(bal & ((1u << lane) - 1u))] = threadIdx.x;
+        __syncthreads();
+        if ((int)threadIdx.x < n_work) {
+            const int src = s_src[threadIdx.x];
+            const int rbs = src / 3, k2s = 2 * (src - 3 * rbs);
+            const int row = a.cci_row[pa + k0 + rbs];
+            const int slA = a.cci_slot[pa + k0 + rbs], slB = a.cci_slot[pb + k0 + rbs];
+            const size_t baseA = ((size_t)row * a.cap + slA) * kTileVals + k2s * kTileW;
+            const size_t baseB = ((size_t)row * a.cap + slB) * kTileVals + k2s * kTileW;
+            float* ps = panel + 2 * src;   // the source's panel rows
+            float2 x[32];
+#pragma unroll
+            for (int t = 0; t < 2; ++t) {
+                float4 u0[4], u1[4];
+                if (touch >> t & 1) {
+                    load_pair_rows(val + baseA + (size_t)t * kTileVals, u0, u1);
+                } else {
+#pragma unroll
+                    for (int v = 0; v < 4; ++v) u0[v] = u1[v] = make_float4(0.f, 0.f, 0.f, 0.f);
+                }
+#pragma unroll
+                for (int v = 0; v < 4; ++v) {
+                    x[t * 16 + 4 * v + 0] = make_float2(u0[v].x, u1[v].x);
+                    x[t * 16 + 4 * v + 1] = make_float2(u0[v].y, u1[v].y);
+                    x[t * 16 + 4 * v + 2] = make_float2(u0[v].z, u1[v].z);
+                    x[t * 16 + 4 * v + 3] = make_float2(u0[v].w, u1[v].w);
                 }
             }
-        }
-        // store, and mark the tiles that hold a nonzero value now (a flag is never
-        // cleared during the sweep: 1 only means "may be nonzero")
-        unsigned char* f = a.out_nz + (size_t)row * a.cap;
+            const float tf = a.trunc_f;
+            for (int lv = 0; lv < 32; ++lv) {
+                const unsigned m = s_mask[lv];
+                if (m == 0u) continue;
+                const Coef* cl = coef + lv * 32;
 #pragma unroll
-        for (int t = 0; t < 2; ++t) {
-            if (!(touch >> t & 1)) continue;
-            float4* d0 = (float4*)(val + baseA + (size_t)t * kTileVals);
-            bool any = false;
-#pragma unroll
-            for (int v = 0; v < 4; ++v) {
-                const float2 a0 = x[t * 16 + 4 * v], a1 = x[t * 16 + 4 * v + 1];
-                const float2 a2 = x[t * 16 + 4 * v + 2], a3 = x[t * 16 + 4 * v + 3];
-                d0[v] = make_float4(a0.x, a1.x, a2.x, a3.x);
-                d0[4 + v] = make_float4(a0.y, a1.y, a2.y, a3.y);
-                any |= a0.x != 0.f || a0.y != 0.f || a1.x != 0.f || a1.y != 0.f || a2.x != 0.f || a2.y != 0.f ||
-                       a3.x != 0.f || a3.y != 0.f;
+                for (int i = 0; i < 32; ++i) {
+                    if (m & (1u << i)) {
+                        float2* py = (float2*)(ps + ((lv - i) & 31) * kFullNR);
+                        const Coef c4 = cl[i];
+                        const float2 y = *py;
+                        float2 xn, yn;
+                        if constexpr (MODE == 0) {
+                            const float2 cc = make_float2(c4.x, c4.y);
+                            xn = __ffma2_rn(cc, x[i], __fmul2_rn(make_float2(c4.z, c4.w), y));
+                            yn = __ffma2_rn(cc, y, __fmul2_rn(make_float2(-c4.z, -c4.w), x[i]));
+                        } else {
+                            xn = __ffma2_rn(c4, y, x[i]);
+                            yn = __ffma2_rn(c4, x[i], y);
+                        }
+                        x[i] = trunc2(xn, tf);
+                        *py = trunc2(yn, tf);
+                    }
+                }
             }
-            if (kFullSkip && any) f[slA + t] = 1;
-        }
+            // store, and mark the tiles that hold a nonzero value now (a flag is
+            // never cleared during the sweep: 1 only means "may be nonzero")
+            unsigned char* f = a.out_nz + (size_t)row * a.cap;
 #pragma unroll
-        for (int t = 0; t < NB / 16; ++t) {
-            if (!(touch >> (3 + t) & 1)) continue;
-            float4* d1 = (float4*)(val + baseB + (size_t)t * kTileVals);
-            bool any = false;
+            for (int t = 0; t < 2; ++t) {
+                if (!(touch >> t & 1)) continue;
+                float4* d0 = (float4*)(val + baseA + (size_t)t * kTileVals);
+                bool any = false;
 #pragma unroll
-            for (int v = 0; v < 4; ++v) {
-                const float2 b0 = *(const float2*)(pr + (t * 16 + 4 * v + 0) * kFullNR);
-                const float2 b1 = *(const float2*)(pr + (t * 16 + 4 * v + 1) * kFullNR);
-                const float2 b2 = *(const float2*)(pr + (t * 16 + 4 * v + 2) * kFullNR);
-                const float2 b3 = *(const float2*)(pr + (t * 16 + 4 * v + 3) * kFullNR);
-                d1[v] = make_float4(b0.x, b1.x, b2.x, b3.x);
-                d1[4 + v] = make_float4(b0.y, b1.y, b2.y, b3.y);
-                any |= b0.x != 0.f || b0.y != 0.f || b1.x != 0.f || b1.y != 0.f || b2.x != 0.f || b2.y != 0.f ||
-                       b3.x != 0.f || b3.y != 0.f;
+                for (int v = 0; v < 4; ++v) {
+                    const float2 a0 = x[t * 16 + 4 * v], a1 = x[t * 16 + 4 * v + 1];
+                    const float2 a2 = x[t * 16 + 4 * v + 2], a3 = x[t * 16 + 4 * v + 3];
+                    d0[v] = make_float4(a0.x, a1.x, a2.x, a3.x);
+                    d0[4 + v] = make_float4(a0.y, a1.y, a2.y, a3.y);
+                    any |= a0.x != 0.f || a0.y != 0.f || a1.x != 0.f || a1.y != 0.f || a2.x != 0.f ||
+                           a2.y != 0.f || a3.x != 0.f || a3.y != 0.f;
+                }
+                if (kFullSkip && any) f[slA + t] = 1;
             }
-            if (kFullSkip && any) f[slB + t] = 1;
+#pragma unroll
+            for (int t = 0; t < NB / 16; ++t) {
+                if (!(touch >> (3 + t) & 1)) continue;
+                float4* d1 = (float4*)(val + baseB + (size_t)t * kTileVals);
+                bool any = false;
+#pragma unroll
+                for (int v = 0; v < 4; ++v) {
+                    const float2 b0 = *(const float2*)(ps + (t * 16 + 4 * v + 0) * kFullNR);
+                    const float2 b1 = *(const float2*)(ps + (t * 16 + 4 * v + 1) * kFullNR);
+                    const float2 b2 = *(const float2*)(ps + (t * 16 + 4 * v + 2) * kFullNR);
+                    const float2 b3 = *(const float2*)(ps + (t * 16 + 4 * v + 3) * kFullNR);
+                    d1[v] = make_float4(b0.x, b1.x, b2.x, b3.x);
+                    d1[4 + v] = make_float4(b0.y, b1.y, b2.y, b3.y);
+                    any |= b0.x != 0.f || b0.y != 0.f || b1.x != 0.f || b1.y != 0.f || b2.x != 0.f ||
+                           b2.y != 0.f || b3.x != 0.f || b3.y != 0.f;
+                }
+                if (kFullSkip && any) f[slB + t] = 1;
+            }
         }
+        __syncthreads();   // the next chunk rewrites the panel rows and the list
     }   // row chunks
 }
 
