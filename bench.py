@@ -269,6 +269,12 @@ def main():
         flushing = c_bytes < 2 * L2_BYTES
         if flushing and flush is None:
             flush = torch.empty(64 << 20, dtype=torch.float32, device=dev)
+        # the end-to-end leg below repeats the same iterations from this state
+        # (restored from a host checkpoint) when C is small enough to copy out
+        n_stored = int(warm["nnz_c"] // 96) if warm else 0
+        snap = None
+        if n_stored * 96 * 8 < 4e9:
+            snap = (ctx.get_C_tiles(), ctx.get_charges())
         ctx.profile(True)
         infos = []
         torch.cuda.synchronize(dev)
@@ -291,8 +297,10 @@ def main():
         ctx.profile(False)
         ms = sum(a.elapsed_time(b_) for a, b_ in ev)
         # end to end through the C-ABI: host charges in, host charges out, every step
+        if snap is not None:
+            ctx.set_C_tiles(*snap[0])
         pinned = [torch.empty(s.n_atoms, dtype=torch.float64, pin_memory=True).numpy() for _ in range(3)]
-        for a_, b_ in zip(pinned, ctx.get_charges()):
+        for a_, b_ in zip(pinned, snap[1] if snap is not None else ctx.get_charges()):
             a_[:] = b_
         torch.cuda.synchronize(dev)
         t0 = time.perf_counter()
@@ -305,7 +313,7 @@ def main():
         n_mo = ctx.n_mo
         ctx.close()
         return dict(ms=ms, infos=infos, prof=prof, e2e_dt=e2e_dt, prep=prep, c_bytes=c_bytes,
-                    flushing=flushing, n_mo=n_mo, tuned=tuned)
+                    flushing=flushing, n_mo=n_mo, tuned=tuned, same_steps=snap is not None)
 
     sampler = ClockSampler(local_rank)
     sampler.start()
@@ -435,7 +443,9 @@ def main():
         "cluster_iter_per_s": (max(args.clusters, 1) if args.clusters > 0 else n_gpus) * K / (t_max / 1e3),
         "clocks": clocks,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 3 * 8 * n_atoms_local,
-                "d2h_bytes_per_step": 3 * 8 * n_atoms_local},
+                "d2h_bytes_per_step": 3 * 8 * n_atoms_local,
+                "iterations": ("the timed ones again, from a checkpoint of C and the charges"
+                               if all(r["same_steps"] for r in runs) else "the ones after the timed ones")},
         "gpu_launches": launches * K,
         "roofline": roofline,
         "kernels": kernels,
