@@ -719,7 +719,14 @@ __global__ void __launch_bounds__(apply_threads<T>()) k_apply_colour(SweepArgs a
     __syncthreads();
     constexpr int R = ApplyShape<T>::rows;
     const int row = threadIdx.x * R;
-    if (row < nk * 6) {
+    // a warp whose rows hold only zeros in the block's tiles has nothing to update
+    bool nzrow = false;
+    if (row < nk * 6)
+        for (int cidx = 0; cidx < NT * 16 && !nzrow; ++cidx)
+#pragma unroll
+            for (int r2 = 0; r2 < R; ++r2) nzrow |= panel[cidx * NRP + row + r2] != (T)0;
+    const bool warp_busy = __any_sync(0xffffffffu, nzrow);
+    if (row < nk * 6 && warp_busy) {
         T* pr = panel + row;
         for (int sub = 0; sub < kMaxSub; ++sub) {
             const int q1 = s_lvl[sub + 1];
