@@ -1085,47 +1085,58 @@ __global__ void __launch_bounds__(kFullThreads) k_apply_full(SweepArgs a, int p0
 
 // drop tiles whose 6x16 values are all zero; in -> out
 // (skipped entirely when an earlier kernel of the pass set the error word:
-// `out` is then the pass's untouched input and stays as it was)
+// `out` is then the pass's untouched input and stays as it was).
+// One CTA per row block: a warp per tile marks the nonzero tiles in a shared
+// bitmask, one thread turns the mask into word offsets, and the warps copy the
+// nonzero tiles to their compacted slots (order kept); three barriers per row.
+constexpr int kCompactMaxWords = 1024;   // 32768 slots (the 16-bit slot limit)
 template <typename T>
-__global__ void k_compact(int cap, const int* __restrict__ in_nt, const int* __restrict__ in_tile,
-                          const T* __restrict__ in_val, int* __restrict__ out_nt, int* __restrict__ out_tile,
-                          T* __restrict__ out_val, const unsigned* __restrict__ err) {
-    __shared__ int wcnt[32];
-    __shared__ int s_base;
+__global__ void __launch_bounds__(256) k_compact(int cap, const int* __restrict__ in_nt,
+                                                 const int* __restrict__ in_tile, const T* __restrict__ in_val,
+                                                 int* __restrict__ out_nt, int* __restrict__ out_tile,
+                                                 T* __restrict__ out_val, const unsigned* __restrict__ err) {
+    __shared__ unsigned s_bits[kCompactMaxWords];
+    __shared__ int s_pre[kCompactMaxWords];
     if (*err & (kErrCapacity | kErrSortSize)) return;
     const int r = blockIdx.x;
     const int n = in_nt[r];
+    const int nw = (n + 31) >> 5;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-    if (threadIdx.x == 0) s_base = 0;
+    using VT = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
+    constexpr int kPer = kTileVals * (int)sizeof(T) / 16;   // 16-byte pieces per tile (24 or 48)
+    for (int i = threadIdx.x; i < nw; i += blockDim.x) s_bits[i] = 0u;
     __syncthreads();
-    // process in chunks of nwarps tiles, one warp per tile, order preserved
-    for (int s0 = 0; s0 < n; s0 += nwarps) {
-        const int s = s0 + warp;
+    for (int s = warp; s < n; s += nwarps) {
+        const VT* v = (const VT*)(in_val + ((size_t)r * cap + s) * kTileVals);
         bool nz = false;
-        if (s < n) {
-            const T* v = in_val + ((size_t)r * cap + s) * kTileVals;
-            for (int i = lane; i < kTileVals; i += 32) nz |= (v[i] != (T)0);
+        for (int i = lane; i < kPer; i += 32) {
+            const VT x = v[i];
+            if constexpr (sizeof(T) == 4)
+                nz |= x.x != 0.f || x.y != 0.f || x.z != 0.f || x.w != 0.f;
+            else
+                nz |= x.x != 0.0 || x.y != 0.0;
         }
-        nz = __any_sync(0xffffffffu, nz);
-        if (lane == 0) wcnt[warp] = (s < n && nz) ? 1 : 0;
-        __syncthreads();
-        int pos = s_base;
-        for (int w = 0; w < warp; ++w) pos += wcnt[w];
-        if (s < n && nz) {
-            const T* v = in_val + ((size_t)r * cap + s) * kTileVals;
-            T* o = out_val + ((size_t)r * cap + pos) * kTileVals;
-            for (int i = lane; i < kTileVals; i += 32) o[i] = v[i];
-            if (lane == 0) out_tile[(size_t)r * cap + pos] = in_tile[(size_t)r * cap + s];
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            int tot = 0;
-            for (int w = 0; w < nwarps; ++w) tot += wcnt[w];
-            s_base += tot;
-        }
-        __syncthreads();
+        if (__any_sync(0xffffffffu, nz) && lane == 0) atomicOr(&s_bits[s >> 5], 1u << (s & 31));
     }
-    if (threadIdx.x == 0) out_nt[r] = s_base;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int run = 0;
+        for (int w = 0; w < nw; ++w) {
+            s_pre[w] = run;
+            run += __popc(s_bits[w]);
+        }
+        out_nt[r] = run;
+    }
+    __syncthreads();
+    for (int s = warp; s < n; s += nwarps) {
+        const unsigned w = s_bits[s >> 5];
+        if (!(w >> (s & 31) & 1u)) continue;
+        const int pos = s_pre[s >> 5] + __popc(w & ((1u << (s & 31)) - 1u));
+        const VT* v = (const VT*)(in_val + ((size_t)r * cap + s) * kTileVals);
+        VT* o = (VT*)(out_val + ((size_t)r * cap + pos) * kTileVals);
+        for (int i = lane; i < kPer; i += 32) o[i] = v[i];
+        if (lane == 0) out_tile[(size_t)r * cap + pos] = in_tile[(size_t)r * cap + s];
+    }
 }
 
 }  // namespace
