@@ -754,6 +754,7 @@ int sscf_create(const sscf_system* sys, const sscf_params* prm, void* cuda_strea
         AL(c.d_c_tile[b], (size_t)c.n_mol * c.cap * 4);
         AL(c.d_c_val[b], (size_t)c.n_mol * c.cap * kTileVals * ts);
         AL(c.d_c_nz[b], (size_t)c.n_mol * c.cap);
+        if (b == 0) AL(c.d_unit_lab, (size_t)2 * c.n_groups * 4);
     }
     AL(c.d_cci_ptr, (size_t)(c.n_tiles + 1) * 4);
     AL(c.d_cci_cnt, (size_t)c.n_tiles * 4);

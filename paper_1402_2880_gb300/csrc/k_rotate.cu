@@ -390,6 +390,7 @@ struct SweepArgs {
     const int* cl_vt0;
     const int* clblk_ptr;    // closure: blocks of the pass by cluster
     const int* clblk;
+    const int* unit_lab;     // closure: component label of every unit (2 per group), cluster-local
     const int* gnb_row;
     const int* gnb_col;
     const int* group_nmol;
@@ -421,12 +422,66 @@ struct SweepArgs {
     unsigned* err;
 };
 
-constexpr int kClosureIters = 256;
 
 // truncation test |x| < threshold, decided exactly in the storage precision
 __device__ __forceinline__ bool below(double x, const SweepArgs& a) { return fabs(x) < a.trunc; }
 __device__ __forceinline__ bool below(float x, const SweepArgs& a) { return fabsf(x) < a.trunc_f; }
 static_assert(sizeof(float) == 4, "");
+
+// Connected components of a pass's units (the occupied or the virtual tiles
+// of one group) under its active blocks, one CTA per cluster. The closure of a
+// row is then the set of units whose component holds a unit the row has:
+// "a block with pairs has both of its sides or neither", applied until nothing
+// changes, is exactly that. Unit u of a cluster with ng groups: occupied
+// tiles of local group u (u < ng), virtual tiles of local group u - ng.
+// Hook-and-compress: roots are linked to the smaller root across every active
+// block, then every label is replaced by its root, until no block links two
+// roots. A label only ever points to a smaller unit of the same component.
+__global__ void __launch_bounds__(1024) k_closure_labels(SweepArgs a, int* __restrict__ unit_lab) {
+    extern __shared__ int slab[];   // 2 ng labels
+    const int k = blockIdx.x;
+    const int g0 = a.cl_g0[k], ng = a.cl_g0[k + 1] - g0, nu = 2 * ng;
+    const int jb0 = a.clblk_ptr[k], jb1 = a.clblk_ptr[k + 1];
+    const bool groups = a.mode == 1 && a.which == 0;   // occupied and virtual tiles of a group move together
+    for (int u = threadIdx.x; u < nu; u += blockDim.x) slab[u] = u;
+    __syncthreads();
+    auto find = [&](int u) {
+        int v = slab[u];
+        while (v != u) {
+            u = v;
+            v = slab[u];
+        }
+        return u;
+    };
+    // every round that links at least one pair of roots removes a root, so at
+    // most nu rounds can change anything
+    for (int it = 0; it <= nu; ++it) {
+        int changed = 0;
+        const int n_edges = (jb1 - jb0) + (groups ? ng : 0);
+        for (int j = threadIdx.x; j < n_edges; j += blockDim.x) {
+            int u, v;
+            if (j < jb1 - jb0) {
+                const int e = a.clblk[jb0 + j];
+                if (a.pr_n[e] == 0) continue;
+                u = a.gnb_row[e] - g0;
+                v = a.mode == 0 ? ng + (a.gnb_col[e] - g0) : a.gnb_col[e] - g0;
+            } else {
+                u = j - (jb1 - jb0);
+                v = ng + u;
+            }
+            const int ru = find(u), rv = find(v);
+            if (ru != rv) {
+                atomicMin(&slab[max(ru, rv)], min(ru, rv));
+                changed = 1;
+            }
+        }
+        const int any = __syncthreads_or(changed);
+        for (int u = threadIdx.x; u < nu; u += blockDim.x) slab[u] = find(u);
+        __syncthreads();
+        if (!any) break;
+    }
+    for (int u = threadIdx.x; u < nu; u += blockDim.x) unit_lab[2 * g0 + u] = slab[u];
+}
 
 template <typename T>
 __global__ void __launch_bounds__(256) k_closure(SweepArgs a) {
@@ -441,11 +496,12 @@ __global__ void __launch_bounds__(256) k_closure(SweepArgs a) {
     const int gw = (a.max_cl_groups + 31) >> 5;
     unsigned* occ = (unsigned*)smraw;
     unsigned* vir = occ + gw;
-    short* map = (short*)(vir + gw);             // tiles of the cluster (occupied, then virtual): old slot or -1
+    unsigned* comp = vir + gw;                   // 2 gw words: components present in the row
+    short* map = (short*)(comp + 2 * gw);        // tiles of the cluster (occupied, then virtual): old slot or -1
     auto lt = [&](int t) { return t < a.n_occ_tiles ? t - ot0 : not_ + (t - vt0); };
     __shared__ int part[256];
     __shared__ int s_total;
-    for (int i = threadIdx.x; i < gw; i += blockDim.x) occ[i] = vir[i] = 0u;
+    for (int i = threadIdx.x; i < gw; i += blockDim.x) occ[i] = vir[i] = comp[i] = comp[gw + i] = 0u;
     for (int i = threadIdx.x; i < not_ + nvt; i += blockDim.x) map[i] = -1;
     __syncthreads();
     const int n0 = a.in_nt[r];
@@ -464,39 +520,27 @@ __global__ void __launch_bounds__(256) k_closure(SweepArgs a) {
         }
     }
     __syncthreads();
-    const int jb0 = a.clblk_ptr[k], jb1 = a.clblk_ptr[k + 1];
-    for (int it = 0; it < kClosureIters; ++it) {
-        int changed = 0;
-        for (int j = jb0 + threadIdx.x; j < jb1; j += blockDim.x) {
-            const int e = a.clblk[j];
-            if (a.pr_n[e] == 0) continue;
-            const int A = a.gnb_row[e] - g0, B = a.gnb_col[e] - g0;
-            const unsigned ba = 1u << (A & 31), bb = 1u << (B & 31);
-            const bool ha = (occ[A >> 5] & ba) != 0;
-            const bool hb = a.mode == 0 ? (vir[B >> 5] & bb) != 0 : (occ[B >> 5] & bb) != 0;
-            if (ha == hb) continue;
-            changed = 1;
-            atomicOr(&occ[A >> 5], ba);
-            if (a.mode == 0) {
-                atomicOr(&vir[B >> 5], bb);
-            } else {
-                atomicOr(&occ[B >> 5], bb);
-                if (a.which == 0) {
-                    atomicOr(&vir[A >> 5], ba);
-                    atomicOr(&vir[B >> 5], bb);
-                }
-            }
+    // the components that hold a unit of this row
+    for (int u = threadIdx.x; u < 2 * ng; u += blockDim.x) {
+        const int g = u < ng ? u : u - ng;
+        const bool has = ((u < ng ? occ[g >> 5] : vir[g >> 5]) >> (g & 31)) & 1u;
+        if (has) {
+            const int l = a.unit_lab[2 * g0 + u];
+            atomicOr(&comp[l >> 5], 1u << (l & 31));
         }
-        if (!__syncthreads_or(changed)) break;
     }
+    __syncthreads();
+    auto on = [&](int u) {
+        const int l = a.unit_lab[2 * g0 + u];
+        return ((comp[l >> 5] >> (l & 31)) & 1u) != 0u;
+    };
     // new sorted tile list: occupied units by group, then virtual units
     const int per = (2 * ng + blockDim.x - 1) / blockDim.x;
     const int u0 = threadIdx.x * per, u1 = min(2 * ng, u0 + per);
     int cnt = 0;
     for (int u = u0; u < u1; ++u) {
         const int g = u < ng ? u : u - ng;
-        const bool on = u < ng ? (occ[g >> 5] >> (g & 31)) & 1 : (vir[g >> 5] >> (g & 31)) & 1;
-        if (on) cnt += u < ng ? a.group_not[g0 + g] : a.group_nvt[g0 + g];
+        if (on(u)) cnt += u < ng ? a.group_not[g0 + g] : a.group_nvt[g0 + g];
     }
     part[threadIdx.x] = cnt;
     __syncthreads();
@@ -518,8 +562,7 @@ __global__ void __launch_bounds__(256) k_closure(SweepArgs a) {
     int pos = part[threadIdx.x];
     for (int u = u0; u < u1; ++u) {
         const int g = u < ng ? u : u - ng;
-        const bool on = u < ng ? (occ[g >> 5] >> (g & 31)) & 1 : (vir[g >> 5] >> (g & 31)) & 1;
-        if (!on) continue;
+        if (!on(u)) continue;
         const int t0 = u < ng ? a.group_ot0[g0 + g] : a.group_vt0[g0 + g];
         const int nt = u < ng ? a.group_not[g0 + g] : a.group_nvt[g0 + g];
         for (int i = 0; i < nt; ++i) a.out_tile[(size_t)r * a.cap + pos++] = t0 + i;
@@ -1142,7 +1185,7 @@ __global__ void __launch_bounds__(256) k_compact(int cap, const int* __restrict_
 }  // namespace
 
 size_t closure_smem_bytes(const Ctx* c) {
-    return (size_t)2 * ((c->max_cl_groups + 31) / 32) * 4 + (size_t)((c->max_cl_tiles + 1) & ~1) * 2 + 16;
+    return (size_t)4 * ((c->max_cl_groups + 31) / 32) * 4 + (size_t)((c->max_cl_tiles + 1) & ~1) * 2 + 16;
 }
 
 // --------------------------------------------------------------------------
@@ -1261,10 +1304,16 @@ static cudaError_t closure_t(Ctx* c, int mode, int which) {
     a.out_tile = c->d_c_tile[out];
     a.out_val = c->d_c_val[out];
     a.out_nz = c->d_c_nz[out];
+    a.unit_lab = c->d_unit_lab;
     const size_t smem = closure_smem_bytes(c);
     if (smem > (size_t)kMaxDynSmem) return cudaErrorInvalidValue;
     cudaError_t e = cudaFuncSetAttribute(k_closure<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
+    const size_t lsmem = (size_t)2 * c->max_cl_groups * 4;
+    if (lsmem > (size_t)kMaxDynSmem) return cudaErrorInvalidValue;
+    e = cudaFuncSetAttribute(k_closure_labels, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lsmem);
+    if (e != cudaSuccess) return e;
+    k_closure_labels<<<c->n_clusters, 1024, lsmem, c->stream>>>(a, c->d_unit_lab);
     k_closure<T><<<c->n_mol, 256, smem, c->stream>>>(a);
     c->cur = out;
     return cudaGetLastError();
@@ -1330,7 +1379,7 @@ static cudaError_t apply_t(Ctx* c, int mode, int which) {
 }
 
 cudaError_t launch_closure(Ctx* c, int mode, int which) {
-    c->n_launch += 1;
+    c->n_launch += 2;
     return c->prec == SSCF_FP64 ? closure_t<double>(c, mode, which) : closure_t<float>(c, mode, which);
 }
 

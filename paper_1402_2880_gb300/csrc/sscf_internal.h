@@ -151,6 +151,7 @@ struct Ctx {
     int* d_cl_vt0 = nullptr;          // n_clusters + 1: first virtual tile of every cluster
     int* d_clblk_ptr[2] = {nullptr, nullptr};   // blocks of every cluster: [0] all directed, [1] A <= B
     int* d_clblk[2] = {nullptr, nullptr};
+    int* d_unit_lab = nullptr;        // 2 n_groups: closure component labels (cluster-local)
     int* d_cl_nmol = nullptr;
     int* d_group_cl = nullptr;        // cluster of every group
     void* d_cl_sel = nullptr;         // per-cluster top-k state (6 words each)
