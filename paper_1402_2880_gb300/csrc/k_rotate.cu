@@ -103,7 +103,8 @@ __global__ void k_rot_hist(int shift, int n_gnb, const int* __restrict__ gnb_row
 }
 
 // one thread per cluster: pick the bin holding the kmax-th largest key
-__global__ void k_rot_pick(int shift, int n_clusters, ClSel* cl, unsigned long long* hist) {
+// (last_shift: the final pass; keys below it are zero for every candidate)
+__global__ void k_rot_pick(int shift, int last_shift, int n_clusters, ClSel* cl, unsigned long long* hist) {
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= n_clusters) return;
     ClSel s = cl[c];
@@ -121,7 +122,7 @@ __global__ void k_rot_pick(int shift, int n_clusters, ClSel* cl, unsigned long l
         s.rank -= cum;
         for (int i = 0; i < 256; ++i) h[i] = 0ull;
     }
-    if (shift == 0) s.thr = s.cand > s.kmax ? s.prefix : 0ull;
+    if (shift == last_shift) s.thr = s.cand > s.kmax ? s.prefix : 0ull;
     cl[c] = s;
 }
 
@@ -1203,11 +1204,15 @@ static cudaError_t select_rot_t(Ctx* c) {
                                                     c->d_group_nvt, c->d_group_cl, c->d_rot_blk_tp0, (const T*)c->d_F,
                                                     tau, c->d_sc, cl);
     const int hb = std::min(c->n_gnb, 1024);
-    for (int shift = 56; shift >= 0; shift -= 8) {
+    // the keys are the bit patterns of |F| as doubles; a float widened to double
+    // has its 29 lowest mantissa bits zero, so for FP32 storage the radix passes
+    // below bit 24 would only ever pick bin 0 and are left out
+    const int last = std::is_same<T, float>::value ? 24 : 0;
+    for (int shift = 56; shift >= last; shift -= 8) {
         k_rot_hist<T><<<hb, 256, 0, c->stream>>>(shift, c->n_gnb, c->d_gnb_row, c->d_gnb_col, c->d_group_nmol,
                                                  c->d_group_nvt, c->d_group_cl, c->d_rot_blk_tp0, (const T*)c->d_F,
                                                  tau, cl, c->d_cl_hist);
-        k_rot_pick<<<(c->n_clusters + 127) / 128, 128, 0, c->stream>>>(shift, c->n_clusters, cl, c->d_cl_hist);
+        k_rot_pick<<<(c->n_clusters + 127) / 128, 128, 0, c->stream>>>(shift, last, c->n_clusters, cl, c->d_cl_hist);
     }
     k_rot_lists<T><<<c->n_gnb, 128, 0, c->stream>>>(
         c->n_gnb, c->d_gnb_row, c->d_gnb_col, c->d_group_nmol, c->d_group_nvt, c->d_group_occ0_mo,
@@ -1217,7 +1222,7 @@ static cudaError_t select_rot_t(Ctx* c) {
 }
 
 cudaError_t launch_select_rot(Ctx* c) {
-    c->n_launch += 18;
+    c->n_launch += c->prec == SSCF_FP64 ? 2 + 2 * 8 : 2 + 2 * 5;   // stats, lists, radix passes (hist + pick)
     return c->prec == SSCF_FP64 ? select_rot_t<double>(c) : select_rot_t<float>(c);
 }
 
