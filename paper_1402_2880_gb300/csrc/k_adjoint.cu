@@ -81,7 +81,7 @@ __global__ void __launch_bounds__(256) k_zmul(int n_tiles, int n_occ_tiles, int 
                                               const T* __restrict__ F, int* __restrict__ z_nt,
                                               int* __restrict__ z_tile, T* __restrict__ z_val,
                                               unsigned* __restrict__ err) {
-    extern __shared__ unsigned char smraw[];
+    extern __shared__ __align__(16) unsigned char smraw[];
     const int gw = (n_groups + 31) >> 5;
     unsigned* pres = (unsigned*)smraw;          // gw: groups with occupied tiles in row r
     unsigned* outg = pres + gw;                 // gw: groups of Z's tiles

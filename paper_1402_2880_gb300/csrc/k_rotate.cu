@@ -486,7 +486,7 @@ __global__ void __launch_bounds__(1024) k_closure_labels(SweepArgs a, int* __res
 
 template <typename T>
 __global__ void __launch_bounds__(256) k_closure(SweepArgs a) {
-    extern __shared__ unsigned char smraw[];
+    extern __shared__ __align__(16) unsigned char smraw[];
     // everything a row block touches belongs to its own cluster: group bits and
     // the tile map are indexed inside the cluster's ranges
     const int r = blockIdx.x;
@@ -657,7 +657,7 @@ __device__ __forceinline__ float2 trunc2(float2 v, float t) {
 template <typename T, int MODE, int NT, int PCAP>
 __global__ void __launch_bounds__(apply_threads<T>()) k_apply_colour(SweepArgs a, int p0) {
     constexpr int CH = ApplyShape<T>::chunk, NRP = apply_nrp<T>();
-    extern __shared__ unsigned char smraw[];
+    extern __shared__ __align__(16) unsigned char smraw[];
     T* panel = (T*)smraw;                                    // [NT tiles][16][NRP]
     T* pcs = panel + NT * 16 * NRP;                          // np * 2 coefficients
     unsigned* poff = (unsigned*)(pcs + 2 * PCAP);            // np packed panel offsets
@@ -875,6 +875,9 @@ __global__ void __launch_bounds__(apply_threads<T>()) k_apply_colour(SweepArgs a
 // A warp whose rows hold only zeros in the block's touched tiles (per-tile
 // flags written by the closure and raised by the sweep) skips its chunk: the
 // updates would leave those zeros as they are.
+constexpr int kFullDenseMin = 12;                 // pairs in a level from which MODE 1 runs it without branches
+constexpr int kFullBatch = 8;                     // slots loaded ahead in a branch-free level (multiple of 4)
+constexpr int kFullMinCtas[2] = {6, 5};          // resident CTAs per SM the register budget is cut for
 constexpr int kFullSkipModes = 3;                 // bit m: mode m checks the tile flags before loading
 constexpr int kFullWaves = 16;                    // resident-CTA multiples per launch (row chunks loop beyond)
 constexpr int kFullCH = 32;                       // row blocks per CTA
@@ -885,9 +888,9 @@ template <> struct FullShape<0> {   // rotations: B = one virtual tile, coeffici
     static constexpr int nb = 16;
     using Coef = float4;
 };
-template <> struct FullShape<1> {   // combinations: B = two occupied tiles, coefficients (-c, -c)
+template <> struct FullShape<1> {   // combinations: B = two occupied tiles, coefficient -c
     static constexpr int nb = 32;
-    using Coef = float2;
+    using Coef = float;
 };
 template <int MODE> __host__ __device__ constexpr size_t full_apply_smem() {
     return (size_t)FullShape<MODE>::nb * kFullNR * 4 + (size_t)32 * 32 * sizeof(typename FullShape<MODE>::Coef);
@@ -903,7 +906,7 @@ __device__ __forceinline__ void load_pair_rows(const float* src, float4 (&r0)[4]
 }
 
 template <int MODE>
-__global__ void __launch_bounds__(kFullThreads) k_apply_full(SweepArgs a, int p0) {
+__global__ void __launch_bounds__(kFullThreads, kFullMinCtas[MODE]) k_apply_full(SweepArgs a, int p0) {
     constexpr int NB = FullShape<MODE>::nb;
     // tiles the closure inserted stay zero for many colours, so the flag check
     // before loading skips many row chunks of a rotation sweep (27.5 -> 16.4 ms at
@@ -911,7 +914,7 @@ __global__ void __launch_bounds__(kFullThreads) k_apply_full(SweepArgs a, int p0
     // loading, and the check before it adds little (112.5 -> 111.7 ms)
     constexpr bool kFullSkip = kFullSkipModes >> MODE & 1;
     using Coef = typename FullShape<MODE>::Coef;
-    extern __shared__ unsigned char smraw[];
+    extern __shared__ __align__(16) unsigned char smraw[];
     float* panel = (float*)smraw;                           // [NB B columns][kFullNR rows]
     Coef* coef = (Coef*)(panel + NB * kFullNR);             // [32 levels][32 i]
     __shared__ unsigned s_mask[32];
@@ -932,7 +935,7 @@ __global__ void __launch_bounds__(kFullThreads) k_apply_full(SweepArgs a, int p0
     }
     for (int i = threadIdx.x; i < 32 * 32; i += blockDim.x) {
         if constexpr (MODE == 0) coef[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-        else coef[i] = make_float2(0.f, 0.f);
+        else coef[i] = 0.f;
     }
     if (threadIdx.x < 32) s_mask[threadIdx.x] = 0u;
     __syncthreads();
@@ -946,7 +949,7 @@ __global__ void __launch_bounds__(kFullThreads) k_apply_full(SweepArgs a, int p0
             const float sn = cs[2 * q + 1];
             coef[lv * 32 + il] = make_float4(c, c, sn, sn);
         } else {
-            coef[lv * 32 + il] = make_float2(-c, -c);
+            coef[lv * 32 + il] = -c;   // a slot without a pair keeps c = 0
         }
         atomicOr(&s_mask[lv], 1u << il);
     }
@@ -985,38 +988,39 @@ __global__ void __launch_bounds__(kFullThreads) k_apply_full(SweepArgs a, int p0
             }
             if (nz) {
                 unsigned bits = 0u;   // OR of the bit patterns of everything loaded
-                const size_t baseA = ((size_t)row * a.cap + slA) * kTileVals + k2 * kTileW;
-                const size_t baseB = ((size_t)row * a.cap + slB) * kTileVals + k2 * kTileW;
 #pragma unroll
-                for (int t = 0; t < 2; ++t) {
-                    if (!(touch >> t & 1)) continue;
-                    float4 u0[4], u1[4];
-                    load_pair_rows(val + baseA + (size_t)t * kTileVals, u0, u1);
+                for (int s = 0; s < 2; ++s) {
+                    const size_t base = ((size_t)row * a.cap + (s ? slB : slA)) * kTileVals + k2 * kTileW;
 #pragma unroll
-                    for (int v = 0; v < 4; ++v)
-                        bits |= __float_as_uint(u0[v].x) | __float_as_uint(u0[v].y) | __float_as_uint(u0[v].z) |
-                                __float_as_uint(u0[v].w) | __float_as_uint(u1[v].x) | __float_as_uint(u1[v].y) |
-                                __float_as_uint(u1[v].z) | __float_as_uint(u1[v].w);
-                }
-                float* pw = panel + 2 * threadIdx.x;
+                    for (int t = 0; t < (s ? NB / 16 : 2); ++t) {
+                        // rotations: the B side goes to the thread's panel rows now
+                        // (the pairs are few, and a reload after packing costs more
+                        // than the bank conflicts of reading them from there)
+                        const bool to_panel = MODE == 0 && s == 1;
+                        float4 u0[4], u1[4];
+                        if (touch >> (3 * s + t) & 1) {
+                            load_pair_rows(val + base + (size_t)t * kTileVals, u0, u1);
+                        } else if (to_panel) {
 #pragma unroll
-                for (int t = 0; t < NB / 16; ++t) {
-                    float4 v0[4], v1[4];
-                    if (touch >> (3 + t) & 1) {
-                        load_pair_rows(val + baseB + (size_t)t * kTileVals, v0, v1);
-                    } else {
+                            for (int v = 0; v < 4; ++v) u0[v] = u1[v] = make_float4(0.f, 0.f, 0.f, 0.f);
+                        } else {
+                            continue;
+                        }
 #pragma unroll
-                        for (int v = 0; v < 4; ++v) v0[v] = v1[v] = make_float4(0.f, 0.f, 0.f, 0.f);
-                    }
+                        for (int v = 0; v < 4; ++v)
+                            bits |= __float_as_uint(u0[v].x) | __float_as_uint(u0[v].y) | __float_as_uint(u0[v].z) |
+                                    __float_as_uint(u0[v].w) | __float_as_uint(u1[v].x) | __float_as_uint(u1[v].y) |
+                                    __float_as_uint(u1[v].z) | __float_as_uint(u1[v].w);
+                        if (to_panel) {
+                            float* pw = panel + 2 * threadIdx.x;
 #pragma unroll
-                    for (int v = 0; v < 4; ++v) {
-                        bits |= __float_as_uint(v0[v].x) | __float_as_uint(v0[v].y) | __float_as_uint(v0[v].z) |
-                                __float_as_uint(v0[v].w) | __float_as_uint(v1[v].x) | __float_as_uint(v1[v].y) |
-                                __float_as_uint(v1[v].z) | __float_as_uint(v1[v].w);
-                        *(float2*)(pw + (t * 16 + 4 * v + 0) * kFullNR) = make_float2(v0[v].x, v1[v].x);
-                        *(float2*)(pw + (t * 16 + 4 * v + 1) * kFullNR) = make_float2(v0[v].y, v1[v].y);
-                        *(float2*)(pw + (t * 16 + 4 * v + 2) * kFullNR) = make_float2(v0[v].z, v1[v].z);
-                        *(float2*)(pw + (t * 16 + 4 * v + 3) * kFullNR) = make_float2(v0[v].w, v1[v].w);
+                            for (int v = 0; v < 4; ++v) {
+                                *(float2*)(pw + (t * 16 + 4 * v + 0) * kFullNR) = make_float2(u0[v].x, u1[v].x);
+                                *(float2*)(pw + (t * 16 + 4 * v + 1) * kFullNR) = make_float2(u0[v].y, u1[v].y);
+                                *(float2*)(pw + (t * 16 + 4 * v + 2) * kFullNR) = make_float2(u0[v].z, u1[v].z);
+                                *(float2*)(pw + (t * 16 + 4 * v + 3) * kFullNR) = make_float2(u0[v].w, u1[v].w);
+                            }
+                        }
                     }
                 }
                 work = (bits & 0x7fffffffu) != 0u;
@@ -1041,7 +1045,27 @@ __global__ void __launch_bounds__(kFullThreads) k_apply_full(SweepArgs a, int p0
             const int slA = a.cci_slot[pa + k0 + rbs], slB = a.cci_slot[pb + k0 + rbs];
             const size_t baseA = ((size_t)row * a.cap + slA) * kTileVals + k2s * kTileW;
             const size_t baseB = ((size_t)row * a.cap + slB) * kTileVals + k2s * kTileW;
-            float* ps = panel + 2 * src;   // the source's panel rows
+            // combinations: the B side goes to the thread's own panel rows now
+            // (consecutive threads, consecutive 8-byte words: no bank conflicts in
+            // the dense level loop)
+            float* ps = panel + 2 * (MODE == 0 ? src : (int)threadIdx.x);
+#pragma unroll
+            for (int t = 0; t < (MODE == 1 ? NB / 16 : 0); ++t) {
+                float4 v0[4], v1[4];
+                if (touch >> (3 + t) & 1) {
+                    load_pair_rows(val + baseB + (size_t)t * kTileVals, v0, v1);
+                } else {
+#pragma unroll
+                    for (int v = 0; v < 4; ++v) v0[v] = v1[v] = make_float4(0.f, 0.f, 0.f, 0.f);
+                }
+#pragma unroll
+                for (int v = 0; v < 4; ++v) {
+                    *(float2*)(ps + (t * 16 + 4 * v + 0) * kFullNR) = make_float2(v0[v].x, v1[v].x);
+                    *(float2*)(ps + (t * 16 + 4 * v + 1) * kFullNR) = make_float2(v0[v].y, v1[v].y);
+                    *(float2*)(ps + (t * 16 + 4 * v + 2) * kFullNR) = make_float2(v0[v].z, v1[v].z);
+                    *(float2*)(ps + (t * 16 + 4 * v + 3) * kFullNR) = make_float2(v0[v].w, v1[v].w);
+                }
+            }
             float2 x[32];
 #pragma unroll
             for (int t = 0; t < 2; ++t) {
@@ -1065,6 +1089,38 @@ __global__ void __launch_bounds__(kFullThreads) k_apply_full(SweepArgs a, int p0
                 const unsigned m = s_mask[lv];
                 if (m == 0u) continue;
                 const Coef* cl = coef + lv * 32;
+                if constexpr (MODE == 1) {
+                    if (__popc(m) >= kFullDenseMin) {
+                        // most slots of the level hold a pair: run all 32 without a
+                        // branch; an empty slot (c = 0, threshold 0) leaves both of
+                        // its values as they are. kFullBatch loads in flight before
+                        // their updates.
+                        const float4* cl4 = (const float4*)cl;
+#pragma unroll
+                        for (int i0 = 0; i0 < 32; i0 += kFullBatch) {
+                            float2 yv[kFullBatch];
+                            float4 cv[kFullBatch / 4];
+#pragma unroll
+                            for (int u = 0; u < kFullBatch / 4; ++u) cv[u] = cl4[i0 / 4 + u];
+#pragma unroll
+                            for (int u = 0; u < kFullBatch; ++u)
+                                yv[u] = *(const float2*)(ps + ((lv - i0 - u) & 31) * kFullNR);
+#pragma unroll
+                            for (int u = 0; u < kFullBatch; ++u) {
+                                const int i = i0 + u;
+                                const float4 c4 = cv[u / 4];
+                                const float c = (u & 3) == 0 ? c4.x : (u & 3) == 1 ? c4.y : (u & 3) == 2 ? c4.z : c4.w;
+                                const float t = (m >> i & 1u) ? tf : 0.f;
+                                const float2 cc = make_float2(c, c);
+                                const float2 xn = __ffma2_rn(cc, yv[u], x[i]);
+                                const float2 yn = __ffma2_rn(cc, x[i], yv[u]);
+                                x[i] = trunc2(xn, t);
+                                *(float2*)(ps + ((lv - i) & 31) * kFullNR) = trunc2(yn, t);
+                            }
+                        }
+                        continue;
+                    }
+                }
 #pragma unroll
                 for (int i = 0; i < 32; ++i) {
                     if (m & (1u << i)) {
@@ -1077,8 +1133,9 @@ __global__ void __launch_bounds__(kFullThreads) k_apply_full(SweepArgs a, int p0
                             xn = __ffma2_rn(cc, x[i], __fmul2_rn(make_float2(c4.z, c4.w), y));
                             yn = __ffma2_rn(cc, y, __fmul2_rn(make_float2(-c4.z, -c4.w), x[i]));
                         } else {
-                            xn = __ffma2_rn(c4, y, x[i]);
-                            yn = __ffma2_rn(c4, x[i], y);
+                            const float2 cc = make_float2(c4, c4);
+                            xn = __ffma2_rn(cc, y, x[i]);
+                            yn = __ffma2_rn(cc, x[i], y);
                         }
                         x[i] = trunc2(xn, tf);
                         *py = trunc2(yn, tf);
@@ -1352,7 +1409,7 @@ static cudaError_t apply_mode_t(Ctx* c, int which) {
     static int full_occ[2] = {0, 0};
     if (full && full_occ[MODE] == 0) {
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&full_occ[MODE], k_apply_full<MODE>, kFullThreads,
-                                                          full_apply_smem<MODE>());
+                                                              full_apply_smem<MODE>());
         if (e != cudaSuccess) return e;
         full_occ[MODE] = std::max(full_occ[MODE], 1);
     }
