@@ -879,7 +879,7 @@ constexpr int kFullDenseMin = 12;                 // pairs in a level from which
 constexpr int kFullBatch = 8;                     // slots loaded ahead in a branch-free level (multiple of 4)
 constexpr int kFullMinCtas[2] = {6, 5};          // resident CTAs per SM the register budget is cut for
 constexpr int kFullSkipModes = 3;                 // bit m: mode m checks the tile flags before loading
-constexpr int kFullWaves = 16;                    // resident-CTA multiples per launch (row chunks loop beyond)
+constexpr int kFullWaves[2] = {16, 4};            // resident-CTA multiples per launch (row chunks loop beyond)
 constexpr int kFullCH = 32;                       // row blocks per CTA
 constexpr int kFullNR = kFullCH * kAoPerMol;      // AO rows per CTA (panel stride, floats)
 constexpr int kFullThreads = kFullNR / 2;         // one pair of adjacent AO rows per thread (two pairs measured slower)
@@ -964,10 +964,155 @@ __global__ void __launch_bounds__(kFullThreads, kFullMinCtas[MODE]) k_apply_full
     // zeros). The row pairs with work are then packed to the first threads of
     // the CTA, which reload the A side and run the updates, so that whole warps
     // of zero rows go idle.
-    __shared__ int s_src[kFullThreads];
+    __shared__ int s_list[2 * kFullThreads];   // row pairs with work, not yet run
     __shared__ int s_wcnt[kFullThreads / 32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int rb = threadIdx.x / 3, k2 = 2 * (threadIdx.x - 3 * rb);   // own row block, first of two AO rows
+    // the updates of one row pair with work: entry = (row block in the block's
+    // row list) * 3 + pair; rotations read the B side from the panel rows phase
+    // one wrote for it in chunk k0
+    auto run = [&](const int ent, const int k0) {
+        const int kr = ent / 3, k2s = 2 * (ent - 3 * kr);
+        const int row = a.cci_row[pa + kr];
+        const int slA = a.cci_slot[pa + kr], slB = a.cci_slot[pb + kr];
+        const size_t baseA = ((size_t)row * a.cap + slA) * kTileVals + k2s * kTileW;
+        const size_t baseB = ((size_t)row * a.cap + slB) * kTileVals + k2s * kTileW;
+        // combinations: the B side goes to the thread's own panel rows now
+        // (consecutive threads, consecutive 8-byte words: no bank conflicts in
+        // the dense level loop)
+        float* ps = panel + 2 * (MODE == 0 ? ent - 3 * k0 : (int)threadIdx.x);
+#pragma unroll
+        for (int t = 0; t < (MODE == 1 ? NB / 16 : 0); ++t) {
+            float4 v0[4], v1[4];
+            if (touch >> (3 + t) & 1) {
+                load_pair_rows(val + baseB + (size_t)t * kTileVals, v0, v1);
+            } else {
+#pragma unroll
+                for (int v = 0; v < 4; ++v) v0[v] = v1[v] = make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+#pragma unroll
+            for (int v = 0; v < 4; ++v) {
+                *(float2*)(ps + (t * 16 + 4 * v + 0) * kFullNR) = make_float2(v0[v].x, v1[v].x);
+                *(float2*)(ps + (t * 16 + 4 * v + 1) * kFullNR) = make_float2(v0[v].y, v1[v].y);
+                *(float2*)(ps + (t * 16 + 4 * v + 2) * kFullNR) = make_float2(v0[v].z, v1[v].z);
+                *(float2*)(ps + (t * 16 + 4 * v + 3) * kFullNR) = make_float2(v0[v].w, v1[v].w);
+            }
+        }
+        float2 x[32];
+#pragma unroll
+        for (int t = 0; t < 2; ++t) {
+            float4 u0[4], u1[4];
+            if (touch >> t & 1) {
+                load_pair_rows(val + baseA + (size_t)t * kTileVals, u0, u1);
+            } else {
+#pragma unroll
+                for (int v = 0; v < 4; ++v) u0[v] = u1[v] = make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+#pragma unroll
+            for (int v = 0; v < 4; ++v) {
+                x[t * 16 + 4 * v + 0] = make_float2(u0[v].x, u1[v].x);
+                x[t * 16 + 4 * v + 1] = make_float2(u0[v].y, u1[v].y);
+                x[t * 16 + 4 * v + 2] = make_float2(u0[v].z, u1[v].z);
+                x[t * 16 + 4 * v + 3] = make_float2(u0[v].w, u1[v].w);
+            }
+        }
+        const float tf = a.trunc_f;
+        for (int lv = 0; lv < 32; ++lv) {
+            const unsigned m = s_mask[lv];
+            if (m == 0u) continue;
+            const Coef* cl = coef + lv * 32;
+            if constexpr (MODE == 1) {
+                if (__popc(m) >= kFullDenseMin) {
+                    // most slots of the level hold a pair: run all 32 without a
+                    // branch; an empty slot (c = 0, threshold 0) leaves both of
+                    // its values as they are. kFullBatch loads in flight before
+                    // their updates.
+                    const float4* cl4 = (const float4*)cl;
+#pragma unroll
+                    for (int i0 = 0; i0 < 32; i0 += kFullBatch) {
+                        float2 yv[kFullBatch];
+                        float4 cv[kFullBatch / 4];
+#pragma unroll
+                        for (int u = 0; u < kFullBatch / 4; ++u) cv[u] = cl4[i0 / 4 + u];
+#pragma unroll
+                        for (int u = 0; u < kFullBatch; ++u)
+                            yv[u] = *(const float2*)(ps + ((lv - i0 - u) & 31) * kFullNR);
+#pragma unroll
+                        for (int u = 0; u < kFullBatch; ++u) {
+                            const int i = i0 + u;
+                            const float4 c4 = cv[u / 4];
+                            const float c = (u & 3) == 0 ? c4.x : (u & 3) == 1 ? c4.y : (u & 3) == 2 ? c4.z : c4.w;
+                            const float t = (m >> i & 1u) ? tf : 0.f;
+                            const float2 cc = make_float2(c, c);
+                            const float2 xn = __ffma2_rn(cc, yv[u], x[i]);
+                            const float2 yn = __ffma2_rn(cc, x[i], yv[u]);
+                            x[i] = trunc2(xn, t);
+                            *(float2*)(ps + ((lv - i) & 31) * kFullNR) = trunc2(yn, t);
+                        }
+                    }
+                    continue;
+                }
+            }
+#pragma unroll
+            for (int i = 0; i < 32; ++i) {
+                if (m & (1u << i)) {
+                    float2* py = (float2*)(ps + ((lv - i) & 31) * kFullNR);
+                    const Coef c4 = cl[i];
+                    const float2 y = *py;
+                    float2 xn, yn;
+                    if constexpr (MODE == 0) {
+                        const float2 cc = make_float2(c4.x, c4.y);
+                        xn = __ffma2_rn(cc, x[i], __fmul2_rn(make_float2(c4.z, c4.w), y));
+                        yn = __ffma2_rn(cc, y, __fmul2_rn(make_float2(-c4.z, -c4.w), x[i]));
+                    } else {
+                        const float2 cc = make_float2(c4, c4);
+                        xn = __ffma2_rn(cc, y, x[i]);
+                        yn = __ffma2_rn(cc, x[i], y);
+                    }
+                    x[i] = trunc2(xn, tf);
+                    *py = trunc2(yn, tf);
+                }
+            }
+        }
+        // store, and mark the tiles that hold a nonzero value now (a flag is
+        // never cleared during the sweep: 1 only means "may be nonzero")
+        unsigned char* f = a.out_nz + (size_t)row * a.cap;
+#pragma unroll
+        for (int t = 0; t < 2; ++t) {
+            if (!(touch >> t & 1)) continue;
+            float4* d0 = (float4*)(val + baseA + (size_t)t * kTileVals);
+            bool any = false;
+#pragma unroll
+            for (int v = 0; v < 4; ++v) {
+                const float2 a0 = x[t * 16 + 4 * v], a1 = x[t * 16 + 4 * v + 1];
+                const float2 a2 = x[t * 16 + 4 * v + 2], a3 = x[t * 16 + 4 * v + 3];
+                d0[v] = make_float4(a0.x, a1.x, a2.x, a3.x);
+                d0[4 + v] = make_float4(a0.y, a1.y, a2.y, a3.y);
+                any |= a0.x != 0.f || a0.y != 0.f || a1.x != 0.f || a1.y != 0.f || a2.x != 0.f ||
+                       a2.y != 0.f || a3.x != 0.f || a3.y != 0.f;
+            }
+            if (kFullSkip && any) f[slA + t] = 1;
+        }
+#pragma unroll
+        for (int t = 0; t < NB / 16; ++t) {
+            if (!(touch >> (3 + t) & 1)) continue;
+            float4* d1 = (float4*)(val + baseB + (size_t)t * kTileVals);
+            bool any = false;
+#pragma unroll
+            for (int v = 0; v < 4; ++v) {
+                const float2 b0 = *(const float2*)(ps + (t * 16 + 4 * v + 0) * kFullNR);
+                const float2 b1 = *(const float2*)(ps + (t * 16 + 4 * v + 1) * kFullNR);
+                const float2 b2 = *(const float2*)(ps + (t * 16 + 4 * v + 2) * kFullNR);
+                const float2 b3 = *(const float2*)(ps + (t * 16 + 4 * v + 3) * kFullNR);
+                d1[v] = make_float4(b0.x, b1.x, b2.x, b3.x);
+                d1[4 + v] = make_float4(b0.y, b1.y, b2.y, b3.y);
+                any |= b0.x != 0.f || b0.y != 0.f || b1.x != 0.f || b1.y != 0.f || b2.x != 0.f ||
+                       b2.y != 0.f || b3.x != 0.f || b3.y != 0.f;
+            }
+            if (kFullSkip && any) f[slB + t] = 1;
+        }
+    };
+    int n_acc = 0;   // entries in s_list (the same in every thread)
     for (int k0 = k_first; k0 < n_rows; k0 += gridDim.x * kFullCH) {
         const int nk = min(kFullCH, n_rows - k0);
         // the counter holds the 2x2 row updates the algorithm defines, rows proven
@@ -1036,152 +1181,24 @@ __global__ void __launch_bounds__(kFullThreads, kFullMinCtas[MODE]) k_apply_full
             before += w < warp ? s_wcnt[w] : 0;
             n_work += s_wcnt[w];
         }
-        if (work) s_src[before + __popc(bal & ((1u << lane) - 1u))] = threadIdx.x;
+        if (work) s_list[n_acc + before + __popc(bal & ((1u << lane) - 1u))] = 3 * k0 + threadIdx.x;
+        n_acc += n_work;
         __syncthreads();
-        if ((int)threadIdx.x < n_work) {
-            const int src = s_src[threadIdx.x];
-            const int rbs = src / 3, k2s = 2 * (src - 3 * rbs);
-            const int row = a.cci_row[pa + k0 + rbs];
-            const int slA = a.cci_slot[pa + k0 + rbs], slB = a.cci_slot[pb + k0 + rbs];
-            const size_t baseA = ((size_t)row * a.cap + slA) * kTileVals + k2s * kTileW;
-            const size_t baseB = ((size_t)row * a.cap + slB) * kTileVals + k2s * kTileW;
-            // combinations: the B side goes to the thread's own panel rows now
-            // (consecutive threads, consecutive 8-byte words: no bank conflicts in
-            // the dense level loop)
-            float* ps = panel + 2 * (MODE == 0 ? src : (int)threadIdx.x);
-#pragma unroll
-            for (int t = 0; t < (MODE == 1 ? NB / 16 : 0); ++t) {
-                float4 v0[4], v1[4];
-                if (touch >> (3 + t) & 1) {
-                    load_pair_rows(val + baseB + (size_t)t * kTileVals, v0, v1);
-                } else {
-#pragma unroll
-                    for (int v = 0; v < 4; ++v) v0[v] = v1[v] = make_float4(0.f, 0.f, 0.f, 0.f);
-                }
-#pragma unroll
-                for (int v = 0; v < 4; ++v) {
-                    *(float2*)(ps + (t * 16 + 4 * v + 0) * kFullNR) = make_float2(v0[v].x, v1[v].x);
-                    *(float2*)(ps + (t * 16 + 4 * v + 1) * kFullNR) = make_float2(v0[v].y, v1[v].y);
-                    *(float2*)(ps + (t * 16 + 4 * v + 2) * kFullNR) = make_float2(v0[v].z, v1[v].z);
-                    *(float2*)(ps + (t * 16 + 4 * v + 3) * kFullNR) = make_float2(v0[v].w, v1[v].w);
-                }
+        // rotations run the chunk's row pairs now; combinations collect a CTA's
+        // worth over several chunks first, so that the updates run in full warps
+        while (MODE == 0 ? n_acc > 0 : n_acc >= kFullThreads) {
+            const int take = min(n_acc, kFullThreads);
+            const int ent = (int)threadIdx.x < take ? s_list[threadIdx.x] : -1;
+            if constexpr (MODE == 1) {
+                __syncthreads();   // entries read: move the rest to the front
+                for (int i = threadIdx.x; i < n_acc - take; i += blockDim.x) s_list[i] = s_list[take + i];
             }
-            float2 x[32];
-#pragma unroll
-            for (int t = 0; t < 2; ++t) {
-                float4 u0[4], u1[4];
-                if (touch >> t & 1) {
-                    load_pair_rows(val + baseA + (size_t)t * kTileVals, u0, u1);
-                } else {
-#pragma unroll
-                    for (int v = 0; v < 4; ++v) u0[v] = u1[v] = make_float4(0.f, 0.f, 0.f, 0.f);
-                }
-#pragma unroll
-                for (int v = 0; v < 4; ++v) {
-                    x[t * 16 + 4 * v + 0] = make_float2(u0[v].x, u1[v].x);
-                    x[t * 16 + 4 * v + 1] = make_float2(u0[v].y, u1[v].y);
-                    x[t * 16 + 4 * v + 2] = make_float2(u0[v].z, u1[v].z);
-                    x[t * 16 + 4 * v + 3] = make_float2(u0[v].w, u1[v].w);
-                }
-            }
-            const float tf = a.trunc_f;
-            for (int lv = 0; lv < 32; ++lv) {
-                const unsigned m = s_mask[lv];
-                if (m == 0u) continue;
-                const Coef* cl = coef + lv * 32;
-                if constexpr (MODE == 1) {
-                    if (__popc(m) >= kFullDenseMin) {
-                        // most slots of the level hold a pair: run all 32 without a
-                        // branch; an empty slot (c = 0, threshold 0) leaves both of
-                        // its values as they are. kFullBatch loads in flight before
-                        // their updates.
-                        const float4* cl4 = (const float4*)cl;
-#pragma unroll
-                        for (int i0 = 0; i0 < 32; i0 += kFullBatch) {
-                            float2 yv[kFullBatch];
-                            float4 cv[kFullBatch / 4];
-#pragma unroll
-                            for (int u = 0; u < kFullBatch / 4; ++u) cv[u] = cl4[i0 / 4 + u];
-#pragma unroll
-                            for (int u = 0; u < kFullBatch; ++u)
-                                yv[u] = *(const float2*)(ps + ((lv - i0 - u) & 31) * kFullNR);
-#pragma unroll
-                            for (int u = 0; u < kFullBatch; ++u) {
-                                const int i = i0 + u;
-                                const float4 c4 = cv[u / 4];
-                                const float c = (u & 3) == 0 ? c4.x : (u & 3) == 1 ? c4.y : (u & 3) == 2 ? c4.z : c4.w;
-                                const float t = (m >> i & 1u) ? tf : 0.f;
-                                const float2 cc = make_float2(c, c);
-                                const float2 xn = __ffma2_rn(cc, yv[u], x[i]);
-                                const float2 yn = __ffma2_rn(cc, x[i], yv[u]);
-                                x[i] = trunc2(xn, t);
-                                *(float2*)(ps + ((lv - i) & 31) * kFullNR) = trunc2(yn, t);
-                            }
-                        }
-                        continue;
-                    }
-                }
-#pragma unroll
-                for (int i = 0; i < 32; ++i) {
-                    if (m & (1u << i)) {
-                        float2* py = (float2*)(ps + ((lv - i) & 31) * kFullNR);
-                        const Coef c4 = cl[i];
-                        const float2 y = *py;
-                        float2 xn, yn;
-                        if constexpr (MODE == 0) {
-                            const float2 cc = make_float2(c4.x, c4.y);
-                            xn = __ffma2_rn(cc, x[i], __fmul2_rn(make_float2(c4.z, c4.w), y));
-                            yn = __ffma2_rn(cc, y, __fmul2_rn(make_float2(-c4.z, -c4.w), x[i]));
-                        } else {
-                            const float2 cc = make_float2(c4, c4);
-                            xn = __ffma2_rn(cc, y, x[i]);
-                            yn = __ffma2_rn(cc, x[i], y);
-                        }
-                        x[i] = trunc2(xn, tf);
-                        *py = trunc2(yn, tf);
-                    }
-                }
-            }
-            // store, and mark the tiles that hold a nonzero value now (a flag is
-            // never cleared during the sweep: 1 only means "may be nonzero")
-            unsigned char* f = a.out_nz + (size_t)row * a.cap;
-#pragma unroll
-            for (int t = 0; t < 2; ++t) {
-                if (!(touch >> t & 1)) continue;
-                float4* d0 = (float4*)(val + baseA + (size_t)t * kTileVals);
-                bool any = false;
-#pragma unroll
-                for (int v = 0; v < 4; ++v) {
-                    const float2 a0 = x[t * 16 + 4 * v], a1 = x[t * 16 + 4 * v + 1];
-                    const float2 a2 = x[t * 16 + 4 * v + 2], a3 = x[t * 16 + 4 * v + 3];
-                    d0[v] = make_float4(a0.x, a1.x, a2.x, a3.x);
-                    d0[4 + v] = make_float4(a0.y, a1.y, a2.y, a3.y);
-                    any |= a0.x != 0.f || a0.y != 0.f || a1.x != 0.f || a1.y != 0.f || a2.x != 0.f ||
-                           a2.y != 0.f || a3.x != 0.f || a3.y != 0.f;
-                }
-                if (kFullSkip && any) f[slA + t] = 1;
-            }
-#pragma unroll
-            for (int t = 0; t < NB / 16; ++t) {
-                if (!(touch >> (3 + t) & 1)) continue;
-                float4* d1 = (float4*)(val + baseB + (size_t)t * kTileVals);
-                bool any = false;
-#pragma unroll
-                for (int v = 0; v < 4; ++v) {
-                    const float2 b0 = *(const float2*)(ps + (t * 16 + 4 * v + 0) * kFullNR);
-                    const float2 b1 = *(const float2*)(ps + (t * 16 + 4 * v + 1) * kFullNR);
-                    const float2 b2 = *(const float2*)(ps + (t * 16 + 4 * v + 2) * kFullNR);
-                    const float2 b3 = *(const float2*)(ps + (t * 16 + 4 * v + 3) * kFullNR);
-                    d1[v] = make_float4(b0.x, b1.x, b2.x, b3.x);
-                    d1[4 + v] = make_float4(b0.y, b1.y, b2.y, b3.y);
-                    any |= b0.x != 0.f || b0.y != 0.f || b1.x != 0.f || b1.y != 0.f || b2.x != 0.f ||
-                           b2.y != 0.f || b3.x != 0.f || b3.y != 0.f;
-                }
-                if (kFullSkip && any) f[slB + t] = 1;
-            }
+            n_acc -= take;
+            if (ent >= 0) run(ent, k0);
+            __syncthreads();   // the next chunk rewrites the panel rows and the list
         }
-        __syncthreads();   // the next chunk rewrites the panel rows and the list
     }   // row chunks
+    if (MODE == 1 && n_acc > 0 && (int)threadIdx.x < n_acc) run(s_list[threadIdx.x], 0);
 }
 
 // drop tiles whose 6x16 values are all zero; in -> out
@@ -1417,7 +1434,7 @@ static cudaError_t apply_mode_t(Ctx* c, int which) {
     for (int col = 0; col < c->n_colours; ++col) {
         const int nf = full ? nfull[col] : 0;
         if (nf > 0) {
-            const int gxf = std::min(chunks, std::max(1, (kFullWaves * c->n_sm * full_occ[MODE]) / std::max(nf, 1) + 1));
+            const int gxf = std::min(chunks, std::max(1, (kFullWaves[MODE] * c->n_sm * full_occ[MODE]) / std::max(nf, 1) + 1));
             k_apply_full<MODE><<<dim3(gxf, nf), kFullThreads, full_apply_smem<MODE>(), c->stream>>>(a, ptr[col]);
             c->n_launch += 1;
         }
