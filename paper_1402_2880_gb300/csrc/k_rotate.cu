@@ -957,13 +957,14 @@ __global__ void __launch_bounds__(kFullThreads, kFullMinCtas[MODE]) k_apply_full
     // tiles no selected pair touches keep their values: neither loaded nor stored
     const int touch = a.pr_touch[e];
     float* val = (float*)a.out_val;   // in place
-    // Each row chunk runs in two phases. First every thread loads its own row
-    // pair (the B side into its panel rows) and tells whether any value it
-    // loaded is nonzero; rows whose touched tiles are all zero stay zero under
-    // the block's updates (x - c y and c x + s y of zeros, truncation keeps
-    // zeros). The row pairs with work are then packed to the first threads of
-    // the CTA, which reload the A side and run the updates, so that whole warps
-    // of zero rows go idle.
+    // Each row chunk runs in two phases. First every thread tells whether its
+    // own row pair has work: rows whose touched tiles are all zero stay zero
+    // under the block's updates (x - c y and c x + s y of zeros, truncation
+    // keeps zeros). Rotations look at the values (loading the B side into the
+    // thread's panel rows on the way), combinations at the tiles' flags. The row
+    // pairs with work are then packed to the first threads of the CTA, which
+    // load what they need and run the updates, so that whole warps of zero rows
+    // go idle.
     __shared__ int s_list[2 * kFullThreads];   // row pairs with work, not yet run
     __shared__ int s_wcnt[kFullThreads / 32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -1131,7 +1132,11 @@ __global__ void __launch_bounds__(kFullThreads, kFullMinCtas[MODE]) k_apply_full
 #pragma unroll
                 for (int t = 0; t < NB / 16; ++t) nz |= (touch >> (3 + t) & 1) && f[slB + t];
             }
-            if (nz) {
+            // combinations decide on the flags alone: a flagged row pair of zeros
+            // that runs through the updates stays zero, and loading every row
+            // pair to look costs more than it saves
+            if constexpr (MODE == 1) work = nz;
+            if (MODE == 0 && nz) {
                 unsigned bits = 0u;   // OR of the bit patterns of everything loaded
 #pragma unroll
                 for (int s = 0; s < 2; ++s) {
