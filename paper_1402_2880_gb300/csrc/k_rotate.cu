@@ -872,14 +872,14 @@ __global__ void __launch_bounds__(apply_threads<T>()) k_apply_colour(SweepArgs a
 // j = (level - i) mod 32. The block's pairs are expanded into a dense
 // [level][i] coefficient table with a selection mask per level. No barrier is
 // needed after the table is built: a thread reads back only the rows it wrote.
-// A warp whose rows hold only zeros in the block's touched tiles (per-tile
-// flags written by the closure and raised by the sweep) skips its chunk: the
-// updates would leave those zeros as they are.
+// Row pairs whose touched tiles are all flagged zero (per-tile flags written by
+// the closure and raised by the sweep) are skipped: the updates would leave
+// those zeros as they are. The others are collected over several row chunks so
+// that the level loop runs in full warps.
 constexpr int kFullDenseMin = 12;                 // pairs in a level from which MODE 1 runs it without branches
 constexpr int kFullBatch = 8;                     // slots loaded ahead in a branch-free level (multiple of 4)
 constexpr int kFullMinCtas[2] = {6, 5};          // resident CTAs per SM the register budget is cut for
-constexpr int kFullSkipModes = 3;                 // bit m: mode m checks the tile flags before loading
-constexpr int kFullWaves[2] = {16, 4};            // resident-CTA multiples per launch (row chunks loop beyond)
+constexpr int kFullWaves[2] = {16, 4};            // resident-CTA multiples per launch (fewer: more row chunks per CTA to collect from)
 constexpr int kFullCH = 32;                       // row blocks per CTA
 constexpr int kFullNR = kFullCH * kAoPerMol;      // AO rows per CTA (panel stride, floats)
 constexpr int kFullThreads = kFullNR / 2;         // one pair of adjacent AO rows per thread (two pairs measured slower)
@@ -908,11 +908,6 @@ __device__ __forceinline__ void load_pair_rows(const float* src, float4 (&r0)[4]
 template <int MODE>
 __global__ void __launch_bounds__(kFullThreads, kFullMinCtas[MODE]) k_apply_full(SweepArgs a, int p0) {
     constexpr int NB = FullShape<MODE>::nb;
-    // tiles the closure inserted stay zero for many colours, so the flag check
-    // before loading skips many row chunks of a rotation sweep (27.5 -> 16.4 ms at
-    // 4096 molecules); in occupied passes most zero chunks are caught after
-    // loading, and the check before it adds little (112.5 -> 111.7 ms)
-    constexpr bool kFullSkip = kFullSkipModes >> MODE & 1;
     using Coef = typename FullShape<MODE>::Coef;
     extern __shared__ __align__(16) unsigned char smraw[];
     float* panel = (float*)smraw;                           // [NB B columns][kFullNR rows]
@@ -957,33 +952,30 @@ __global__ void __launch_bounds__(kFullThreads, kFullMinCtas[MODE]) k_apply_full
     // tiles no selected pair touches keep their values: neither loaded nor stored
     const int touch = a.pr_touch[e];
     float* val = (float*)a.out_val;   // in place
-    // Each row chunk runs in two phases. First every thread tells whether its
-    // own row pair has work: rows whose touched tiles are all zero stay zero
-    // under the block's updates (x - c y and c x + s y of zeros, truncation
-    // keeps zeros). Rotations look at the values (loading the B side into the
-    // thread's panel rows on the way), combinations at the tiles' flags. The row
-    // pairs with work are then packed to the first threads of the CTA, which
-    // load what they need and run the updates, so that whole warps of zero rows
-    // go idle.
+    // Each row chunk first tells, per row pair, whether it has work: a row pair
+    // whose touched tiles are all flagged zero stays zero under the block's
+    // updates (x - c y and c x + s y of zeros, truncation keeps zeros), and so
+    // does a flagged row pair of zeros that runs through them. The row pairs
+    // with work are appended to a shared list; once it holds a CTA's worth,
+    // every thread takes one, loads both sides and runs the updates, so that the
+    // level loop runs in full warps. The rest runs at the end.
     __shared__ int s_list[2 * kFullThreads];   // row pairs with work, not yet run
     __shared__ int s_wcnt[kFullThreads / 32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int rb = threadIdx.x / 3, k2 = 2 * (threadIdx.x - 3 * rb);   // own row block, first of two AO rows
+    const int rb = threadIdx.x / 3;   // own row block (of the chunk)
     // the updates of one row pair with work: entry = (row block in the block's
-    // row list) * 3 + pair; rotations read the B side from the panel rows phase
-    // one wrote for it in chunk k0
-    auto run = [&](const int ent, const int k0) {
+    // row list) * 3 + pair
+    auto run = [&](const int ent) {
         const int kr = ent / 3, k2s = 2 * (ent - 3 * kr);
         const int row = a.cci_row[pa + kr];
         const int slA = a.cci_slot[pa + kr], slB = a.cci_slot[pb + kr];
         const size_t baseA = ((size_t)row * a.cap + slA) * kTileVals + k2s * kTileW;
         const size_t baseB = ((size_t)row * a.cap + slB) * kTileVals + k2s * kTileW;
-        // combinations: the B side goes to the thread's own panel rows now
-        // (consecutive threads, consecutive 8-byte words: no bank conflicts in
-        // the dense level loop)
-        float* ps = panel + 2 * (MODE == 0 ? ent - 3 * k0 : (int)threadIdx.x);
+        // the B side goes to the thread's own panel rows (consecutive threads,
+        // consecutive 8-byte words: no bank conflicts in the level loop)
+        float* ps = panel + 2 * threadIdx.x;
 #pragma unroll
-        for (int t = 0; t < (MODE == 1 ? NB / 16 : 0); ++t) {
+        for (int t = 0; t < NB / 16; ++t) {
             float4 v0[4], v1[4];
             if (touch >> (3 + t) & 1) {
                 load_pair_rows(val + baseB + (size_t)t * kTileVals, v0, v1);
@@ -1092,7 +1084,7 @@ __global__ void __launch_bounds__(kFullThreads, kFullMinCtas[MODE]) k_apply_full
                 any |= a0.x != 0.f || a0.y != 0.f || a1.x != 0.f || a1.y != 0.f || a2.x != 0.f ||
                        a2.y != 0.f || a3.x != 0.f || a3.y != 0.f;
             }
-            if (kFullSkip && any) f[slA + t] = 1;
+            if (any) f[slA + t] = 1;
         }
 #pragma unroll
         for (int t = 0; t < NB / 16; ++t) {
@@ -1110,7 +1102,7 @@ __global__ void __launch_bounds__(kFullThreads, kFullMinCtas[MODE]) k_apply_full
                 any |= b0.x != 0.f || b0.y != 0.f || b1.x != 0.f || b1.y != 0.f || b2.x != 0.f ||
                        b2.y != 0.f || b3.x != 0.f || b3.y != 0.f;
             }
-            if (kFullSkip && any) f[slB + t] = 1;
+            if (any) f[slB + t] = 1;
         }
     };
     int n_acc = 0;   // entries in s_list (the same in every thread)
@@ -1123,58 +1115,11 @@ __global__ void __launch_bounds__(kFullThreads, kFullMinCtas[MODE]) k_apply_full
         if (rb < nk) {
             const int row = a.cci_row[pa + k0 + rb];
             const int slA = a.cci_slot[pa + k0 + rb], slB = a.cci_slot[pb + k0 + rb];
-            bool nz = true;
-            if constexpr (kFullSkip) {
-                const unsigned char* f = a.out_nz + (size_t)row * a.cap;
-                nz = false;
+            const unsigned char* f = a.out_nz + (size_t)row * a.cap;
 #pragma unroll
-                for (int t = 0; t < 2; ++t) nz |= (touch >> t & 1) && f[slA + t];
+            for (int t = 0; t < 2; ++t) work |= (touch >> t & 1) && f[slA + t];
 #pragma unroll
-                for (int t = 0; t < NB / 16; ++t) nz |= (touch >> (3 + t) & 1) && f[slB + t];
-            }
-            // combinations decide on the flags alone: a flagged row pair of zeros
-            // that runs through the updates stays zero, and loading every row
-            // pair to look costs more than it saves
-            if constexpr (MODE == 1) work = nz;
-            if (MODE == 0 && nz) {
-                unsigned bits = 0u;   // OR of the bit patterns of everything loaded
-#pragma unroll
-                for (int s = 0; s < 2; ++s) {
-                    const size_t base = ((size_t)row * a.cap + (s ? slB : slA)) * kTileVals + k2 * kTileW;
-#pragma unroll
-                    for (int t = 0; t < (s ? NB / 16 : 2); ++t) {
-                        // rotations: the B side goes to the thread's panel rows now
-                        // (the pairs are few, and a reload after packing costs more
-                        // than the bank conflicts of reading them from there)
-                        const bool to_panel = MODE == 0 && s == 1;
-                        float4 u0[4], u1[4];
-                        if (touch >> (3 * s + t) & 1) {
-                            load_pair_rows(val + base + (size_t)t * kTileVals, u0, u1);
-                        } else if (to_panel) {
-#pragma unroll
-                            for (int v = 0; v < 4; ++v) u0[v] = u1[v] = make_float4(0.f, 0.f, 0.f, 0.f);
-                        } else {
-                            continue;
-                        }
-#pragma unroll
-                        for (int v = 0; v < 4; ++v)
-                            bits |= __float_as_uint(u0[v].x) | __float_as_uint(u0[v].y) | __float_as_uint(u0[v].z) |
-                                    __float_as_uint(u0[v].w) | __float_as_uint(u1[v].x) | __float_as_uint(u1[v].y) |
-                                    __float_as_uint(u1[v].z) | __float_as_uint(u1[v].w);
-                        if (to_panel) {
-                            float* pw = panel + 2 * threadIdx.x;
-#pragma unroll
-                            for (int v = 0; v < 4; ++v) {
-                                *(float2*)(pw + (t * 16 + 4 * v + 0) * kFullNR) = make_float2(u0[v].x, u1[v].x);
-                                *(float2*)(pw + (t * 16 + 4 * v + 1) * kFullNR) = make_float2(u0[v].y, u1[v].y);
-                                *(float2*)(pw + (t * 16 + 4 * v + 2) * kFullNR) = make_float2(u0[v].z, u1[v].z);
-                                *(float2*)(pw + (t * 16 + 4 * v + 3) * kFullNR) = make_float2(u0[v].w, u1[v].w);
-                            }
-                        }
-                    }
-                }
-                work = (bits & 0x7fffffffu) != 0u;
-            }
+            for (int t = 0; t < NB / 16; ++t) work |= (touch >> (3 + t) & 1) && f[slB + t];
         }
         // pack the row pairs with work to the first threads
         const unsigned bal = __ballot_sync(0xffffffffu, work);
@@ -1189,21 +1134,16 @@ __global__ void __launch_bounds__(kFullThreads, kFullMinCtas[MODE]) k_apply_full
         if (work) s_list[n_acc + before + __popc(bal & ((1u << lane) - 1u))] = 3 * k0 + threadIdx.x;
         n_acc += n_work;
         __syncthreads();
-        // rotations run the chunk's row pairs now; combinations collect a CTA's
-        // worth over several chunks first, so that the updates run in full warps
-        while (MODE == 0 ? n_acc > 0 : n_acc >= kFullThreads) {
-            const int take = min(n_acc, kFullThreads);
-            const int ent = (int)threadIdx.x < take ? s_list[threadIdx.x] : -1;
-            if constexpr (MODE == 1) {
-                __syncthreads();   // entries read: move the rest to the front
-                for (int i = threadIdx.x; i < n_acc - take; i += blockDim.x) s_list[i] = s_list[take + i];
-            }
-            n_acc -= take;
-            if (ent >= 0) run(ent, k0);
-            __syncthreads();   // the next chunk rewrites the panel rows and the list
+        if (n_acc >= kFullThreads) {
+            const int ent = s_list[threadIdx.x];
+            __syncthreads();   // entries read: move the rest (fewer than a CTA's worth) to the front
+            for (int i = threadIdx.x; i < n_acc - kFullThreads; i += blockDim.x) s_list[i] = s_list[kFullThreads + i];
+            n_acc -= kFullThreads;
+            run(ent);
+            __syncthreads();   // the list is rewritten by the next chunk
         }
     }   // row chunks
-    if (MODE == 1 && n_acc > 0 && (int)threadIdx.x < n_acc) run(s_list[threadIdx.x], 0);
+    if ((int)threadIdx.x < n_acc) run(s_list[threadIdx.x]);
 }
 
 // drop tiles whose 6x16 values are all zero; in -> out
