@@ -20,6 +20,7 @@ the lattice, per iteration, on the host cores.
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import os
 import statistics
@@ -380,6 +381,25 @@ def main():
     alu_peak = 152 * 128 * 2 * sm_clk / 1e12 * (1.0 if prec == SSCF_MIXED else 1.0 / 64)
     upd = {"apply_rot": mean("upd_rot"), "apply_ortho": mean("upd_combo")}
 
+    def measured_traffic(name):
+        """DRAM bytes per call of a launcher from a committed ncu capture of this
+        workload (profiles/dram_traffic_<name>_water4096_mixed.md), or None when
+        the kernel source or the workload differs from the captured one."""
+        path = os.path.join(ROOT, "profiles", f"dram_traffic_{name}_water4096_mixed.md")
+        try:
+            with open(path) as f:
+                line = next(l for l in f if l.startswith(f"traffic: {name} "))
+            with open(os.path.join(ROOT, "paper_1402_2880_gb300", "csrc", "k_rotate.cu"), "rb") as f:
+                digest = hashlib.sha256(f.read()).hexdigest()
+        except (OSError, StopIteration):
+            return None
+        fields = dict(kv.split("=", 1) for kv in line.split()[2:])
+        workload = (f"n_mol:{args.n_mol},eps:{args.eps:g},precision:{args.precision},"
+                    f"clusters:{max(args.clusters, 1)},steps:{K},warmup:{args.warmup}")
+        if fields.get("kernel_source_sha256") != digest or fields.get("workload") != workload:
+            return None
+        return float(fields["bytes_per_call"])
+
     def roof(name):
         calls = prof[name][1] / K
         t_call = prof[name][0] / max(prof[name][1], 1) / 1e3
@@ -387,7 +407,7 @@ def main():
             # 2x2 updates: 2 FMAs (4 flops) per AO row and pair
             achieved = 4.0 * upd[name] / max(calls, 1) / t_call / 1e12
             return {"kernel": name, "bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
-                    "frac": achieved / alu_peak, "traffic": None,
+                    "frac": achieved / alu_peak, "traffic": measured_traffic(name),
                     "peak_source": "derived: 152 SMs x 128 lanes x 2 flops x max SM clock",
                     "hbm_view": {"algorithmic_bytes": algo_bytes[name],
                                  "achieved_gbs": algo_bytes[name] / max(calls, 1) / t_call / 1e9,
