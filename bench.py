@@ -23,6 +23,7 @@ import argparse
 import hashlib
 import json
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -384,19 +385,23 @@ def main():
     def measured_traffic(name):
         """DRAM bytes per call of a launcher from a committed ncu capture of this
         workload (profiles/dram_traffic_<name>_water4096_mixed.md), or None when
-        the kernel source or the workload differs from the captured one."""
+        the kernel code or the workload differs from the captured one."""
         path = os.path.join(ROOT, "profiles", f"dram_traffic_{name}_water4096_mixed.md")
         try:
             with open(path) as f:
                 line = next(l for l in f if l.startswith(f"traffic: {name} "))
-            with open(os.path.join(ROOT, "paper_1402_2880_gb300", "csrc", "k_rotate.cu"), "rb") as f:
-                digest = hashlib.sha256(f.read()).hexdigest()
+            with open(os.path.join(ROOT, "paper_1402_2880_gb300", "csrc", "k_rotate.cu")) as f:
+                src = f.read()
+            # code only: comments and white space do not change the kernels
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            src = re.sub(r"//[^\n]*", "", src)
+            digest = hashlib.sha256(re.sub(r"\s+", "", src).encode()).hexdigest()
         except (OSError, StopIteration):
             return None
         fields = dict(kv.split("=", 1) for kv in line.split()[2:])
         workload = (f"n_mol:{args.n_mol},eps:{args.eps:g},precision:{args.precision},"
                     f"clusters:{max(args.clusters, 1)},steps:{K},warmup:{args.warmup}")
-        if fields.get("kernel_source_sha256") != digest or fields.get("workload") != workload:
+        if fields.get("kernel_code_sha256") != digest or fields.get("workload") != workload:
             return None
         return float(fields["bytes_per_call"])
 

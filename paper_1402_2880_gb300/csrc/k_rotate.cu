@@ -870,8 +870,8 @@ __global__ void __launch_bounds__(apply_threads<T>()) k_apply_colour(SweepArgs a
 // stay in registers (the index i is static once the slot loop is unrolled),
 // the NB B-side values sit in a thread-private shared-memory panel indexed by
 // j = (level - i) mod 32. The block's pairs are expanded into a dense
-// [level][i] coefficient table with a selection mask per level. No barrier is
-// needed after the table is built: a thread reads back only the rows it wrote.
+// [level][i] coefficient table with a selection mask per level. The level loop
+// needs no barrier: a thread reads back only the panel rows it wrote.
 // Row pairs whose touched tiles are all flagged zero (per-tile flags written by
 // the closure and raised by the sweep) are skipped: the updates would leave
 // those zeros as they are. The others are collected over several row chunks so
