@@ -238,7 +238,7 @@ __global__ void k_xc(int tile_lo, int n_rows, int cap, int capY, const int* __re
 // mixed precision flushes the FP32 partial sums to FP64 every 32 rows.
 // ---------------------------------------------------------------------------
 constexpr int kTfWarps = 8;
-constexpr int kStage = 8;   // row blocks staged per warp at a time
+constexpr int kStage = 4;   // row blocks staged per warp at a time
 
 template <typename T> struct V4;
 template <> struct V4<float> { using type = float4; };
