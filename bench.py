@@ -392,11 +392,13 @@ def main():
                 line = next(l for l in f if l.startswith(f"traffic: {name} "))
             with open(os.path.join(ROOT, "paper_1402_2880_gb300", "csrc", "k_rotate.cu")) as f:
                 src = f.read()
-            # code only: comments and white space do not change the kernels
+            # the device code up to the end of the full-block kernel (the host
+            # launchers follow it), without comments and white space
+            src = src[:src.index("\n}\n", src.index("k_apply_full(SweepArgs a, int p0) {")) + 3]
             src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
             src = re.sub(r"//[^\n]*", "", src)
             digest = hashlib.sha256(re.sub(r"\s+", "", src).encode()).hexdigest()
-        except (OSError, StopIteration):
+        except (OSError, StopIteration, ValueError):
             return None
         fields = dict(kv.split("=", 1) for kv in line.split()[2:])
         workload = (f"n_mol:{args.n_mol},eps:{args.eps:g},precision:{args.precision},"

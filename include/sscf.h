@@ -75,7 +75,9 @@ typedef struct {
     int cap_tiles;           /* per-row tile capacity of C; 0 picks the dense size       */
     int cap_y;               /* row blocks per tile of Y = X C; 0 picks the largest cluster */
     int apply_variant;       /* 0: specialised sweep kernels where a block allows them,
-                                1: the generic kernel for every block (same results)     */
+                                1: the generic kernel for every block,
+                                2: the specialised kernels with one CTA per block
+                                (all three give the same results; 1 and 2 are for tests) */
 } sscf_params;
 
 typedef struct {

@@ -526,7 +526,7 @@ int sscf_create(const sscf_system* sys, const sscf_params* prm, void* cuda_strea
     *out = nullptr;
     if (sys->n_atoms <= 0 || sys->n_atoms % 3 != 0) return SSCF_ERR_INVALID_ARG;
     if (prm->precision != SSCF_FP64 && prm->precision != SSCF_MIXED) return SSCF_ERR_INVALID_ARG;
-    if (prm->apply_variant != 0 && prm->apply_variant != 1) return SSCF_ERR_INVALID_ARG;
+    if (prm->apply_variant < 0 || prm->apply_variant > 2) return SSCF_ERR_INVALID_ARG;
     if (prm->cap_tiles < 0 || prm->cap_y < 0) return SSCF_ERR_INVALID_ARG;
     if (!(prm->r_cut > 0) || !(prm->r_decay > 0) || !(prm->group_cut > 0) || !(prm->eps >= 0) ||
         !(prm->U[0] > 0) || !(prm->U[1] > 0) || !(prm->rot_cap_factor > 0))

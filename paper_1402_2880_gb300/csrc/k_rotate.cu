@@ -1359,7 +1359,7 @@ static cudaError_t apply_mode_t(Ctx* c, int which) {
     constexpr int CH = ApplyShape<T>::chunk;
     const int gx = (c->n_mol + CH - 1) / CH;
     // FP32 rotations and occupied passes: blocks between full groups take the register-resident kernel
-    const bool full = std::is_same<T, float>::value && (MODE == 0 || which == 1) && c->apply_variant == 0;
+    const bool full = std::is_same<T, float>::value && (MODE == 0 || which == 1) && c->apply_variant != 1;
     if (full) {
         e = cudaFuncSetAttribute(k_apply_full<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)full_apply_smem<MODE>());
@@ -1379,7 +1379,12 @@ static cudaError_t apply_mode_t(Ctx* c, int which) {
     for (int col = 0; col < c->n_colours; ++col) {
         const int nf = full ? nfull[col] : 0;
         if (nf > 0) {
-            const int gxf = std::min(chunks, std::max(1, (kFullWaves[MODE] * c->n_sm * full_occ[MODE]) / std::max(nf, 1) + 1));
+            // variant 2: one CTA takes all row chunks of its block (the longest
+            // collection of row pairs; same results)
+            const int gxf = c->apply_variant == 2
+                                ? 1
+                                : std::min(chunks, std::max(1, (kFullWaves[MODE] * c->n_sm * full_occ[MODE]) /
+                                                                   std::max(nf, 1) + 1));
             k_apply_full<MODE><<<dim3(gxf, nf), kFullThreads, full_apply_smem<MODE>(), c->stream>>>(a, ptr[col]);
             c->n_launch += 1;
         }

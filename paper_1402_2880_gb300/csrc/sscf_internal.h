@@ -83,7 +83,8 @@ struct Ctx {
     int n_gnb = 0;       // group-graph entries (directed, including (A, A))
     int cap = 0;         // tiles per row block of C
     int capY = 0;        // row blocks per tile of Y
-    int apply_variant = 0;   // 0 specialised sweep kernels where they apply, 1 generic only
+    int apply_variant = 0;   // 0 specialised sweep kernels where they apply, 1 generic only,
+                             // 2 specialised with one CTA per block
     int tf_split = 4;        // CTAs sharing one occupied tile's pairs in the transform (sscf_autotune)
     int n_sm = 152;          // multiprocessors of the context's device
     bool have_guess = false;
