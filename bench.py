@@ -182,6 +182,34 @@ def aggregate(local_atoms: float, local_ms: float, dist=None, device=None):
 
 
 # ---------------------------------------------------------------------------
+def kernel_code_digest(path: str) -> str:
+    """SHA-256 of the device code of k_rotate.cu up to the end of the full-block
+    kernel (the host launchers follow it), without comments and white space."""
+    with open(path) as f:
+        src = f.read()
+    src = src[:src.index("\n}\n", src.index("k_apply_full(SweepArgs a, int p0) {")) + 3]
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    src = re.sub(r"//[^\n]*", "", src)
+    return hashlib.sha256(re.sub(r"\s+", "", src).encode()).hexdigest()
+
+
+def measured_traffic(name: str, workload: str, root: str = ROOT):
+    """DRAM bytes per call of a launcher from a committed ncu capture
+    (profiles/dram_traffic_<name>_water4096_mixed.md), or None when the kernel
+    code or the workload differs from the captured one."""
+    path = os.path.join(root, "profiles", f"dram_traffic_{name}_water4096_mixed.md")
+    try:
+        with open(path) as f:
+            line = next(l for l in f if l.startswith(f"traffic: {name} "))
+        digest = kernel_code_digest(os.path.join(root, "paper_1402_2880_gb300", "csrc", "k_rotate.cu"))
+    except (OSError, StopIteration, ValueError):
+        return None
+    fields = dict(kv.split("=", 1) for kv in line.split()[2:])
+    if fields.get("kernel_code_sha256") != digest or fields.get("workload") != workload:
+        return None
+    return float(fields["bytes_per_call"])
+
+
 def main():
     args = parse()
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -382,30 +410,9 @@ def main():
     alu_peak = 152 * 128 * 2 * sm_clk / 1e12 * (1.0 if prec == SSCF_MIXED else 1.0 / 64)
     upd = {"apply_rot": mean("upd_rot"), "apply_ortho": mean("upd_combo")}
 
-    def measured_traffic(name):
-        """DRAM bytes per call of a launcher from a committed ncu capture of this
-        workload (profiles/dram_traffic_<name>_water4096_mixed.md), or None when
-        the kernel code or the workload differs from the captured one."""
-        path = os.path.join(ROOT, "profiles", f"dram_traffic_{name}_water4096_mixed.md")
-        try:
-            with open(path) as f:
-                line = next(l for l in f if l.startswith(f"traffic: {name} "))
-            with open(os.path.join(ROOT, "paper_1402_2880_gb300", "csrc", "k_rotate.cu")) as f:
-                src = f.read()
-            # the device code up to the end of the full-block kernel (the host
-            # launchers follow it), without comments and white space
-            src = src[:src.index("\n}\n", src.index("k_apply_full(SweepArgs a, int p0) {")) + 3]
-            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-            src = re.sub(r"//[^\n]*", "", src)
-            digest = hashlib.sha256(re.sub(r"\s+", "", src).encode()).hexdigest()
-        except (OSError, StopIteration, ValueError):
-            return None
-        fields = dict(kv.split("=", 1) for kv in line.split()[2:])
-        workload = (f"n_mol:{args.n_mol},eps:{args.eps:g},precision:{args.precision},"
+
+    workload_key = (f"n_mol:{args.n_mol},eps:{args.eps:g},precision:{args.precision},"
                     f"clusters:{max(args.clusters, 1)},steps:{K},warmup:{args.warmup}")
-        if fields.get("kernel_code_sha256") != digest or fields.get("workload") != workload:
-            return None
-        return float(fields["bytes_per_call"])
 
     def roof(name):
         calls = prof[name][1] / K
@@ -414,7 +421,7 @@ def main():
             # 2x2 updates: 2 FMAs (4 flops) per AO row and pair
             achieved = 4.0 * upd[name] / max(calls, 1) / t_call / 1e12
             return {"kernel": name, "bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
-                    "frac": achieved / alu_peak, "traffic": measured_traffic(name),
+                    "frac": achieved / alu_peak, "traffic": measured_traffic(name, workload_key),
                     "peak_source": "derived: 152 SMs x 128 lanes x 2 flops x max SM clock",
                     "hbm_view": {"algorithmic_bytes": algo_bytes[name],
                                  "achieved_gbs": algo_bytes[name] / max(calls, 1) / t_call / 1e9,

@@ -1,7 +1,7 @@
 """Failure handling made on the host (no GPU fault is ever provoked).
 
-CPU: invalid layouts and non-finite coordinates are refused before any CUDA
-call; an allocator hook that refuses memory gives SSCF_ERR_OOM. GPU: a row
+CPU: invalid layouts, non-finite coordinates and unknown parameters are refused
+before any CUDA call; an allocator hook that refuses memory gives SSCF_ERR_OOM. GPU: a row
 capacity that is too small gives SSCF_ERR_CAPACITY and leaves C and the
 charges as they were.
 """
@@ -46,6 +46,15 @@ def test_cluster_order_refused():
     with pytest.raises(_lib_.SscfError) as e:
         _lib_.Context(s.species, s.xyz, s.group_of_mol, P, cluster_of_mol=cl)
     assert e.value.status == -1
+
+
+def test_unknown_sweep_variant_refused():
+    _lib_ = _lib()
+    s = lattice_water(8)
+    for v in (-1, 3):
+        with pytest.raises(_lib_.SscfError) as e:
+            _lib_.Context(s.species, s.xyz, s.group_of_mol, P, apply_variant=v)
+        assert e.value.status == -1
 
 
 def test_allocator_failure_reports_oom():
