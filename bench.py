@@ -409,8 +409,6 @@ def main():
     sm_clk = float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
     alu_peak = 152 * 128 * 2 * sm_clk / 1e12 * (1.0 if prec == SSCF_MIXED else 1.0 / 64)
     upd = {"apply_rot": mean("upd_rot"), "apply_ortho": mean("upd_combo")}
-
-
     workload_key = (f"n_mol:{args.n_mol},eps:{args.eps:g},precision:{args.precision},"
                     f"clusters:{max(args.clusters, 1)},steps:{K},warmup:{args.warmup}")
 
