@@ -896,6 +896,22 @@ template <int MODE> __host__ __device__ constexpr size_t full_apply_smem() {
     return (size_t)FullShape<MODE>::nb * kFullNR * 4 + (size_t)32 * 32 * sizeof(typename FullShape<MODE>::Coef);
 }
 
+// 1.0 where |v| >= t, 0.0 below (and for NaN): one compare that writes the
+// factor itself
+__device__ __forceinline__ float ge_abs_factor(float v, float t) {
+    float k;
+    asm("set.ge.f32.f32 %0, %1, %2;" : "=f"(k) : "f"(fabsf(v)), "f"(t));
+    return k;
+}
+
+// x with the values below t in magnitude set to zero, as a product with 0/1
+// factors: two compares on the ALU pipe and one packed multiply on the FMA
+// pipe instead of two compares and two selects (a value set to zero may come
+// out as -0, which every later test treats as zero)
+__device__ __forceinline__ float2 trunc2_mul(float2 v, float t) {
+    return __fmul2_rn(v, make_float2(ge_abs_factor(v.x, t), ge_abs_factor(v.y, t)));
+}
+
 __device__ __forceinline__ void load_pair_rows(const float* src, float4 (&r0)[4], float4 (&r1)[4]) {
     const float4* s = (const float4*)src;
 #pragma unroll
@@ -1039,8 +1055,8 @@ __global__ void __launch_bounds__(kFullThreads, kFullMinCtas[MODE]) k_apply_full
                             const float2 cc = make_float2(c, c);
                             const float2 xn = __ffma2_rn(cc, yv[u], x[i]);
                             const float2 yn = __ffma2_rn(cc, x[i], yv[u]);
-                            x[i] = trunc2(xn, t);
-                            *(float2*)(ps + ((lv - i) & 31) * kFullNR) = trunc2(yn, t);
+                            x[i] = trunc2_mul(xn, t);
+                            *(float2*)(ps + ((lv - i) & 31) * kFullNR) = trunc2_mul(yn, t);
                         }
                     }
                     continue;
