@@ -253,12 +253,15 @@ def ortho_pass(C: np.ndarray, S: np.ndarray, st: Structure, which: str,
     return eta, int(pa.size)
 
 
-def orthonormalise(C, S, st, which: str, eps: float, max_pass: int = 200):
+def orthonormalise(C, S, st, which: str, eps: float, max_pass: int = 200, tol_min: float = 0.0):
     """Repeat passes until the largest off-diagonal overlap is below eps / 100.
 
     Combinations truncate at 1e-3 eps (Section "Sparsity and numerical accuracy").
+    ``tol_min`` is a floor under the eps / 100 target; it matters only where
+    eps / 100 lies below what the arithmetic can resolve (eps -> 0, where the
+    target would be zero).
     """
-    tol = eps / 100.0
+    tol = max(eps / 100.0, tol_min)
     trunc = 1e-3 * eps
     for k in range(1, max_pass + 1):
         eta, n = ortho_pass(C, S, st, which, tol, trunc)
@@ -372,9 +375,10 @@ class StepInfo:
 class SparseSCF:
     """Plain sparse SCF on one cluster (oracle B)."""
 
-    def __init__(self, sys, p: dict, ortho_every: int = 1):
+    def __init__(self, sys, p: dict, ortho_every: int = 1, ortho_tol_min: float = 0.0):
         self.sys, self.p = sys, p
         self.ortho_every = ortho_every
+        self.ortho_tol_min = ortho_tol_min   # floor under every eps / 100 target (see orthonormalise)
         self.first, self.atom_of_ao, self.n_ao = model.ao_layout(sys.species)
         self.H0, self.S = model.build_h0_s(sys, p, dense=True)
         self.G = model.gamma_matrix(sys, p)
@@ -390,7 +394,7 @@ class SparseSCF:
 
     def start(self, eps: float) -> SparseState:
         C = initial_guess(self.sys, self.st, self.H0, self.S)
-        orthonormalise(C, self.S, self.st, "all", eps)
+        orthonormalise(C, self.S, self.st, "all", eps, tol_min=self.ortho_tol_min)
         q, dq, Q, E = self.charges_energy(C)
         return SparseState(C=C, dq_in=dq, Q_in=Q, q_prev=q, E_prev=E)
 
@@ -403,7 +407,7 @@ class SparseSCF:
         n_rot = rotate_sweep(s.C, F_ov, Fd, st, sel, eps)
         eta = 0.0
         if self.ortho_every:
-            tol = max(eps / 100.0, 0.0)
+            tol = max(eps / 100.0, self.ortho_tol_min)
             eta, _ = ortho_pass(s.C, self.S, st, "occ", tol, 1e-3 * eps)
         q, dq, Q, E = self.charges_energy(s.C)
         dq_max = float(np.max(np.abs(q - s.q_prev)))
@@ -438,7 +442,7 @@ class SparseSCF:
             if k > 0:
                 # the user-threshold SCF starts again from step III with the
                 # improved MOs: full orthonormalisation at the new threshold
-                orthonormalise(s.C, self.S, self.st, "all", eps_k)
+                orthonormalise(s.C, self.S, self.st, "all", eps_k, tol_min=self.ortho_tol_min)
             for _ in range(max_iter):
                 info = self.step(s, eps_k)
                 n_iter += 1
@@ -447,6 +451,6 @@ class SparseSCF:
                 if info.dq_max <= dq_k and abs(info.dE) <= e_k:
                     converged = True
                     break
-        orthonormalise(s.C, self.S, self.st, "occ", eps)
+        orthonormalise(s.C, self.S, self.st, "occ", eps, tol_min=self.ortho_tol_min)
         q, dq, Q, E = self.charges_energy(s.C)
         return dict(energy=E, q=q, dq=dq, C=s.C, iterations=n_iter, converged=converged)

@@ -248,3 +248,20 @@ def test_sparse_scf_matches_dense_below_scf_error():
     assert err < max(scf_error, 1e-9 * s.n_atoms)
     assert err / abs(ref.energy) < 100 * worst_rel_1e5
     assert np.abs(r["q"] - ref.q).max() < 1e-4
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("n", [8, 32])
+def test_sparse_scf_without_cutoff_equals_dense(n):
+    """The limit eps -> 0 of Section "Sparsity and numerical accuracy": with
+    nothing truncated and every coupling rotated, the sparse SCF reaches the
+    dense generalised-eigensolve ground state. The eps / 100 orthonormalisation
+    target is zero there, so it is floored at 1e-13 (FP64 resolution of the
+    normalised overlaps)."""
+    s = lattice_water(n, seed=0)
+    ref = dense.solve(s, P, dq_tol=1e-11, e_tol=1e-13)
+    assert ref.converged
+    r = sparse.SparseSCF(s, P, ortho_tol_min=1e-13).run(eps=0.0, dq_tol=1e-10, e_tol=1e-12)
+    assert r["converged"]
+    assert abs(r["energy"] - ref.energy) / s.n_atoms < 1e-10
+    assert np.abs(r["q"] - ref.q).max() < 1e-8
