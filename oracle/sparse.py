@@ -228,11 +228,16 @@ def truncate(v: np.ndarray, thr: float) -> np.ndarray:
 
 
 def ortho_pass(C: np.ndarray, S: np.ndarray, st: Structure, which: str,
-               tol: float, trunc: float):
-    """One pass of steps b-d; returns (eta, number of combinations)."""
+               tol: float, trunc: float, sigma: np.ndarray | None = None):
+    """One pass of steps b-d; returns (eta, number of combinations).
+
+    ``sigma`` (optional) supplies the overlaps of step b instead of computing
+    them, so that steps c-d can be checked alone on given overlaps.
+    """
     mos = np.arange(st.n_occ) if which == "occ" else np.arange(st.n_mo)
     Cm = C[:, mos]
-    sigma = Cm.T @ (S @ Cm)                      # step b: C^T S C
+    if sigma is None:
+        sigma = Cm.T @ (S @ Cm)                  # step b: C^T S C
     sigma = np.where(overlap_mask(st, mos), sigma, 0.0)
     d = np.sqrt(np.diag(sigma))
     C[:, mos] = Cm / d[None, :]                  # step c: normalise
