@@ -9,12 +9,21 @@ charge / energy accumulation), cut-off 1e-5.
 
 Input state (untimed): per-molecule guess, full orthonormalisation at the
 loose threshold 1e-3 (the paper's first SCF stage), charges of that state;
-then W warm-up iterations at the user threshold. The K timed iterations
-continue from there; C (>1 GB) is larger than the 129 MB L2, so no L2 flush
-is needed between iterations.
+then W warm-up iterations at the user threshold. That state (C and the
+charges) is checkpointed, and every one of the K timed steps restarts from
+it before it runs (outside the timed region): all K steps time the same
+iteration W + 1, so the result does not depend on K. C (>1 GB) is larger
+than the 129 MB L2, so no L2 flush is needed between steps.
+
+Beside the mixed-precision number the line reports the FP64 path on the same
+checkpoint (ms per iteration and the energy difference of that iteration),
+the converged accuracy of both paths on the 32-molecule cluster against the
+dense FP64 oracle, and the end-to-end rate through the C-ABI with the
+checkpoint and the charges copied in from page-locked host memory and the
+charges copied out, every step.
 
 ``--impl reference`` times the FP64 CPU oracle (the same SCC iteration,
-step by step) on a bounded sample of the same workload: a 5^3 sub-cube of
+step by step) on a bounded sample of the same workload: a 6^3 sub-cube of
 the lattice, per iteration, on the host cores.
 """
 from __future__ import annotations
@@ -61,6 +70,8 @@ def parse():
     ap.add_argument("--cap-y", type=int, default=0, help="row blocks per tile of Y (0: the largest cluster)")
     ap.add_argument("--graph", action="store_true", help="replay each SCC iteration as one CUDA graph")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default transform launch shape")
+    ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 path on the same checkpoint")
+    ap.add_argument("--no-accuracy", action="store_true", help="skip the converged 32-molecule accuracy check")
     return ap.parse_args()
 
 
@@ -183,14 +194,17 @@ def aggregate(local_atoms: float, local_ms: float, dist=None, device=None):
 
 # ---------------------------------------------------------------------------
 def kernel_code_digest(path: str) -> str:
-    """SHA-256 of the device code of k_rotate.cu up to the end of the full-block
-    kernel (the host launchers follow it), without comments and white space."""
-    with open(path) as f:
-        src = f.read()
-    src = src[:src.index("\n}\n", src.index("k_apply_full(SweepArgs a, int p0) {")) + 3]
-    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    src = re.sub(r"//[^\n]*", "", src)
-    return hashlib.sha256(re.sub(r"\s+", "", src).encode()).hexdigest()
+    """SHA-256 of the sweep kernels' source (k_rotate.cu: kernels and launchers)
+    and of the shared header beside it (sscf_internal.h: argument structs,
+    constants, layout), without comments and white space."""
+    parts = []
+    for f in (path, os.path.join(os.path.dirname(path), "sscf_internal.h")):
+        with open(f) as fh:
+            src = fh.read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        src = re.sub(r"//[^\n]*", "", src)
+        parts.append(re.sub(r"\s+", "", src))
+    return hashlib.sha256("\0".join(parts).encode()).hexdigest()
 
 
 def measured_traffic(name: str, workload: str, root: str = ROOT):
@@ -208,6 +222,41 @@ def measured_traffic(name: str, workload: str, root: str = ROOT):
     if fields.get("kernel_code_sha256") != digest or fields.get("workload") != workload:
         return None
     return float(fields["bytes_per_call"])
+
+
+def pinned_copy(a):
+    """A page-locked host copy of a numpy array (the end-to-end leg's inputs)."""
+    import numpy as np
+    import torch
+    t = torch.empty(a.shape, dtype=getattr(torch, str(a.dtype)), pin_memory=True)
+    out = t.numpy()
+    np.copyto(out, a)
+    return out
+
+
+def accuracy_config1(p):
+    """Converged 32-molecule cluster (4x4x2, eps 1e-6, convergence 1e-8 Ha):
+    |dE| per atom and the largest charge difference of the mixed and the FP64
+    path against the dense FP64 oracle's converged state, stored by
+    tests/golden/make_config1_dense.py (this leg runs no oracle code)."""
+    import numpy as np
+
+    from paper_1402_2880_gb300 import SSCF_FP64, SSCF_MIXED, Context
+    from synth import lattice_water
+    with open(os.path.join(ROOT, "tests", "golden", "config1_dense.json")) as f:
+        ref = json.load(f)
+    s = lattice_water(32, seed=0)
+    out = {}
+    for name, prec in (("mixed", SSCF_MIXED), ("fp64", SSCF_FP64)):
+        ctx = Context.from_system(s, p, precision=prec)
+        r = ctx.run(allow_not_converged=True)
+        q, _, _ = ctx.get_charges()
+        ctx.close()
+        out[name] = {"converged": bool(r["converged"]),
+                     "abs_dE_per_atom": abs(r["energy"] - ref["energy"]) / s.n_atoms,
+                     "max_abs_dq": float(np.abs(q - np.asarray(ref["q"])).max())}
+    out["oracle"] = ref["what"]
+    return out
 
 
 def main():
@@ -246,6 +295,7 @@ def main():
         dist.init_process_group("nccl", init_method="env://")
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
 
     from paper_1402_2880_gb300 import SSCF_FP64, SSCF_MIXED, SSCF_ORTHO_ALL, Context, build
     from synth import default_params, lattice_water
@@ -272,9 +322,31 @@ def main():
     K = args.steps
     flush = None
 
-    def run_one(s):
-        """Prepare one context (untimed), warm up, time K steps, then K end-to-end steps."""
+    def timed_steps(ctx, ck, n_steps, flushing):
+        """n_steps replays of the checkpointed iteration: restore (untimed), then one
+        sscf_step between CUDA events on the context's stream; returns (ms, infos)."""
         nonlocal flush
+        if flushing and flush is None:
+            flush = torch.empty(64 << 20, dtype=torch.float32, device=dev)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(n_steps)]
+        infos = []
+        for k in range(n_steps):
+            ctx.set_C_tiles(*ck[0])
+            ctx.set_charges(*ck[1])
+            if flushing:
+                with torch.cuda.stream(stream):
+                    flush.zero_()
+            ev[k][0].record(stream)
+            infos.append(ctx.step())
+            ev[k][1].record(stream)
+        torch.cuda.synchronize(dev)
+        return sum(a.elapsed_time(b_) for a, b_ in ev), infos
+
+    def run_one(s, fp64_leg: bool):
+        """Prepare one context (untimed), warm up, checkpoint, time K replays of the
+        next iteration, then K end-to-end replays; optionally the FP64 path on the
+        same checkpoint."""
         ctx = Context.from_system(s, p, precision=prec, stream=stream.cuda_stream, cap_tiles=args.cap_tiles,
                                   cap_y=args.cap_y)
         ctx.set_thresholds(args.prep_eps, 10 * args.prep_eps, 1e-8)
@@ -294,62 +366,63 @@ def main():
                     ctx.enable_graph(True)
             warm = ctx.step()
         torch.cuda.synchronize(dev)
-        # C below twice the 129 MB L2: flush L2 between timed steps (outside the events)
-        c_bytes = (4 if prec == SSCF_MIXED else 8) * (warm["nnz_c"] if warm else s.n_ao * 16)
+        ck = (ctx.get_C_tiles(), ctx.get_charges())
+        n_stored = int(ck[0][1].size)
+        c_bytes = (4 if prec == SSCF_MIXED else 8) * n_stored * 96
         flushing = c_bytes < 2 * L2_BYTES
-        if flushing and flush is None:
-            flush = torch.empty(64 << 20, dtype=torch.float32, device=dev)
-        # the end-to-end leg below repeats the same iterations from this state
-        # (restored from a host checkpoint) when C is small enough to copy out
-        n_stored = int(warm["nnz_c"] // 96) if warm else 0
-        snap = None
-        if n_stored * 96 * 8 < 4e9:
-            snap = (ctx.get_C_tiles(), ctx.get_charges())
+        # one untimed replay: the graph (if any) is captured for the restored buffer parity
+        ctx.set_C_tiles(*ck[0])
+        ctx.set_charges(*ck[1])
+        ctx.step()
         ctx.profile(True)
-        infos = []
-        torch.cuda.synchronize(dev)
-        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-              for _ in range(K if flushing else 1)]
-        if not flushing:
-            ev[0][0].record(stream)
-        for k in range(K):
-            if flushing:
-                with torch.cuda.stream(stream):
-                    flush.zero_()
-                ev[k][0].record(stream)
-            infos.append(ctx.step())
-            if flushing:
-                ev[k][1].record(stream)
-        if not flushing:
-            ev[0][1].record(stream)
-        torch.cuda.synchronize(dev)
+        ms, infos = timed_steps(ctx, ck, K, flushing)
         prof = ctx.profile_read()
         ctx.profile(False)
-        ms = sum(a.elapsed_time(b_) for a, b_ in ev)
-        # end to end through the C-ABI: host charges in, host charges out, every step
-        if snap is not None:
-            ctx.set_C_tiles(*snap[0])
-        pinned = [torch.empty(s.n_atoms, dtype=torch.float64, pin_memory=True).numpy() for _ in range(3)]
-        for a_, b_ in zip(pinned, snap[1] if snap is not None else ctx.get_charges()):
-            a_[:] = b_
+        # end to end through the C-ABI: the checkpoint (C and charges) in from
+        # page-locked host memory, one SCC iteration, the charges out, every step
+        pin_ck = tuple(pinned_copy(a) for a in ck[0])
+        pin_q = [pinned_copy(a) for a in ck[1]]
+        pin_out = [pinned_copy(a) for a in ck[1]]
+        h2d = sum(a.nbytes for a in pin_ck) + sum(a.nbytes for a in pin_q)
+        d2h = sum(a.nbytes for a in pin_out)
         torch.cuda.synchronize(dev)
         t0 = time.perf_counter()
         for _ in range(K):
-            ctx.set_charges(*pinned)
+            ctx.set_C_tiles(*pin_ck)
+            ctx.set_charges(*pin_q)
             ctx.step()
-            ctx.get_charges(out=pinned)
+            ctx.get_charges(out=pin_out)
         torch.cuda.synchronize(dev)
         e2e_dt = time.perf_counter() - t0
         n_mo = ctx.n_mo
         ctx.close()
+        fp64 = None
+        if fp64_leg and prec == SSCF_MIXED:
+            # the FP64 path on the same checkpoint (the FP32 values widen exactly)
+            c64 = Context.from_system(s, p, precision=SSCF_FP64, stream=stream.cuda_stream,
+                                      cap_tiles=args.cap_tiles, cap_y=args.cap_y)
+            c64.set_thresholds(args.eps, 10 * args.eps, 1e-6)
+            if not args.no_autotune:
+                c64.set_C_tiles(*ck[0])
+                c64.set_charges(*ck[1])
+                c64.autotune()
+            n64 = 2
+            ms64, inf64 = timed_steps(c64, ck, n64, flushing)
+            c64.close()
+            e_mixed = float(np.mean([inf["energy"] for inf in infos]))
+            fp64 = {"ms_per_step": ms64 / n64, "steps": n64, "energy": inf64[-1]["energy"],
+                    "energy_mixed": e_mixed,
+                    "abs_dE_per_atom_mixed_vs_fp64": abs(e_mixed - inf64[-1]["energy"]) / s.n_atoms,
+                    "n_rot": inf64[-1]["n_rot"], "n_combo": inf64[-1]["n_combo"]}
         return dict(ms=ms, infos=infos, prof=prof, e2e_dt=e2e_dt, prep=prep, c_bytes=c_bytes,
-                    flushing=flushing, n_mo=n_mo, tuned=tuned, same_steps=snap is not None)
+                    flushing=flushing, n_mo=n_mo, tuned=tuned, h2d=h2d, d2h=d2h, fp64=fp64,
+                    same_iteration=len({round(inf["energy"], 9) for inf in infos}) == 1)
 
     sampler = ClockSampler(local_rank)
     sampler.start()
     if dist is not None:
         dist.barrier()
-    runs = [run_one(s) for s in systems]
+    runs = [run_one(s, fp64_leg=(rank == 0 and i == 0 and not args.no_fp64)) for i, s in enumerate(systems)]
     if dist is not None:
         dist.barrier()
     clocks = sampler.stop()
@@ -402,41 +475,41 @@ def main():
     except OSError:
         pass
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
-    peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
+    peak_src = "measured (MEASURED_PEAKS.json hbm_gbs)" if "hbm_gbs" in peaks else "fallback 6800 GB/s"
 
     # FP32 (or FP64) ALU peak from unit counts and the maximum SM clock:
-    # 152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz; FP64 at 1/64 of it
+    # SMs (read from the device) x 128 FP32 lanes x 2 flops x max clock; FP64 at 1/64 of it
     sm_clk = float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
-    alu_peak = 152 * 128 * 2 * sm_clk / 1e12 * (1.0 if prec == SSCF_MIXED else 1.0 / 64)
+    alu_peak = n_sm * 128 * 2 * sm_clk / 1e12 * (1.0 if prec == SSCF_MIXED else 1.0 / 64)
     upd = {"apply_rot": mean("upd_rot"), "apply_ortho": mean("upd_combo")}
     workload_key = (f"n_mol:{args.n_mol},eps:{args.eps:g},precision:{args.precision},"
-                    f"clusters:{max(args.clusters, 1)},steps:{K},warmup:{args.warmup}")
+                    f"clusters:{max(args.clusters, 1)},replayed_iteration:{args.warmup + 1}")
 
     def roof(name):
+        """HBM roofline of one launcher (the headline: algorithmic bytes / time
+        against the measured copy bandwidth); the sweeps also get the ALU view."""
         calls = prof[name][1] / K
         t_call = prof[name][0] / max(prof[name][1], 1) / 1e3
-        if name in upd:
-            # 2x2 updates: 2 FMAs (4 flops) per AO row and pair
-            achieved = 4.0 * upd[name] / max(calls, 1) / t_call / 1e12
-            return {"kernel": name, "bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
-                    "frac": achieved / alu_peak, "traffic": measured_traffic(name, workload_key),
-                    "peak_source": "derived: 152 SMs x 128 lanes x 2 flops x max SM clock",
-                    "hbm_view": {"algorithmic_bytes": algo_bytes[name],
-                                 "achieved_gbs": algo_bytes[name] / max(calls, 1) / t_call / 1e9,
-                                 "peak_gbs": hbm_peak},
-                    "ms_per_step": per_step[name]}
         b = algo_bytes.get(name)
         if b is None:
             return None
         achieved = b / max(calls, 1) / t_call / 1e9
-        return {"kernel": name, "bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                "frac": achieved / hbm_peak, "traffic": None, "peak_source": peak_src,
-                "ms_per_step": per_step[name]}
+        r = {"kernel": name, "bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+             "frac": achieved / hbm_peak, "traffic": measured_traffic(name, workload_key),
+             "peak_source": peak_src, "algorithmic_bytes_per_call": b / max(calls, 1),
+             "ms_per_step": per_step[name]}
+        if name in upd:
+            # 2x2 updates: 2 FMAs (4 flops) per AO row and pair
+            a_alu = 4.0 * upd[name] / max(calls, 1) / t_call / 1e12
+            r["alu_view"] = {"achieved": a_alu, "peak": alu_peak, "unit": "TFLOP/s", "frac": a_alu / alu_peak,
+                             "peak_source": f"derived: {n_sm} SMs x 128 FP32 lanes x 2 flops x max SM clock "
+                                            f"{sm_clk / 1e6:.0f} MHz"}
+        return r
 
     # graph replays are not seen by the per-launcher events: no per-kernel split then
     roofline = roof(dominant) if dominant else None
     kernels = {k: {"ms_per_step": round(v, 3), "calls_per_step": prof[k][1] / K} for k, v in per_step.items()}
-    for name in ("apply_rot", "transform_ov", "transform_ss", "density", "xc_h"):
+    for name in ("apply_rot", "apply_ortho", "transform_ov", "transform_ss", "density", "xc_h", "xc_s"):
         if name in per_step and name != dominant:
             kernels[name]["roofline"] = roof(name)
 
@@ -445,13 +518,19 @@ def main():
         rate, dt, n_at = oracle_iteration_rate(args.sample_mol, args.eps, 3)
         cpu = {"value": rate, "unit": UNIT, "cores": host_cores(), "kind": "oracle",
                "sample": f"3 SCC iterations of oracle B (FP64, numpy) on a {args.sample_mol}-molecule "
-                         f"sub-cube ({n_at} atoms), {dt:.1f} s"}
+                         f"sub-cube of the same lattice ({n_at} atoms), {dt:.1f} s; its per-atom rate falls "
+                         f"as the cluster grows (dense N^3 products), so the rate on the full cluster is lower"}
         one = oracle_rate_one_core(args.sample_mol, args.eps)
         if one is not None:
             cpu["one_core"] = {"value": one[0], "unit": UNIT, "cores": 1,
                                "sample": f"1 SCC iteration of the same sample with one BLAS thread, {one[1]:.1f} s"}
 
+    accuracy = None
+    if not args.no_accuracy:
+        accuracy = accuracy_config1(p)
+
     launches = int(round(mean("launches")))
+    fp64 = runs[0]["fp64"]
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": n_gpus, "steps": K, "warmup": args.warmup,
         "ms_per_step": t_max / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -461,9 +540,13 @@ def main():
                                 + (f", {len(runs)} waves of {args.wave}" if len(runs) > 1 else "") + "), "
                                 if args.clusters > 0 else
                                 f"water lattice {args.n_mol} molecules ({n_atoms_local} atoms, {6 * args.n_mol} AOs), ")
-                               + f"{args.precision}, eps {args.eps:g}, one SCC iteration per step"
+                               + f"{args.precision}, eps {args.eps:g}; every step replays SCC iteration "
+                               + f"{args.warmup + 1} from a checkpoint of C and the charges (restored before "
+                               + "each step, outside the timed region)"
                                + (", CUDA graph" if args.graph else ""),
                    "n_mol": n_mol_local, "eps": args.eps, "precision": args.precision, "clusters": max(args.clusters, 1),
+                   "replayed_iteration": args.warmup + 1,
+                   "nnz_per_mo": nnz_c / n_mo_local,
                    "parallelism": ("clusters sharded over ranks" if args.clusters > 0 else "replicas")
                                   if n_gpus > 1 else "single",
                    "l2": (f"C holds {c_bytes / 1e6:.0f} MB, " + ("L2 flushed (256 MB write) before every timed step"
@@ -474,16 +557,20 @@ def main():
         "scf_iter_per_s": n_gpus * K / (t_max / 1e3),
         "cluster_iter_per_s": (max(args.clusters, 1) if args.clusters > 0 else n_gpus) * K / (t_max / 1e3),
         "clocks": clocks,
-        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 3 * 8 * n_atoms_local,
-                "d2h_bytes_per_step": 3 * 8 * n_atoms_local,
-                "iterations": ("the timed ones again, from a checkpoint of C and the charges"
-                               if all(r["same_steps"] for r in runs) else "the ones after the timed ones")},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": sum(r["h2d"] for r in runs),
+                "d2h_bytes_per_step": sum(r["d2h"] for r in runs),
+                "what": "per step through the C-ABI: sscf_set_C_tiles (checkpoint of C, FP64 tiles) and "
+                        "sscf_set_charges from page-locked host memory, sscf_step, sscf_get_charges"},
         "gpu_launches": launches * K,
         "roofline": roofline,
         "kernels": kernels,
         "cpu_baseline": cpu,
+        "fp64": fp64,
+        "mixed_speedup_vs_fp64": (fp64["ms_per_step"] / (t_max / K)) if fp64 else None,
+        "accuracy": accuracy,
         "state": {"energy": infos[-1]["energy"], "dq_max": infos[-1]["dq_max"], "n_rot": n_rot,
-                  "n_combo": n_combo, "nnz_per_mo": nnz_c / n_mo_local},
+                  "n_combo": n_combo, "nnz_per_mo": nnz_c / n_mo_local,
+                  "same_iteration_every_step": all(r["same_iteration"] for r in runs)},
     }
     print(json.dumps(line), flush=True)
     if dist is not None:

@@ -136,8 +136,12 @@ int sscf_guess(sscf_ctx* ctx);
  * sigma = C^T S C on neighbouring-group blocks, normalisation by diag(sigma),
  * first-order combinations C'_i = C_i - sigma_ij C_j / 2,
  * C'_j = C_j - sigma_ij C_i / 2 on pairs |sigma_ij| >= 1e-3 eta, truncation
- * at 1e-3 eps, until eta < eps / 100 or max_pass passes. `which` is
- * SSCF_ORTHO_ALL or SSCF_ORTHO_OCC. passes_out, eta_out may be NULL. */
+ * at 1e-3 eps, until eta < target or max_pass passes. The target is eps / 100
+ * (Section "Sparsity and numerical accuracy") floored at what the storage
+ * resolves: max(eps / 100, 2^-19) (32 units in the last place of FP32) in
+ * mixed precision, max(eps / 100, 1e-13) in FP64. The same target applies to
+ * the occupied pass of every sscf_step. `which` is SSCF_ORTHO_ALL or
+ * SSCF_ORTHO_OCC. passes_out, eta_out may be NULL. */
 int sscf_orthonormalise(sscf_ctx* ctx, int which, int max_pass, int* passes_out,
                         double* eta_out);
 
@@ -145,6 +149,27 @@ int sscf_orthonormalise(sscf_ctx* ctx, int which, int max_pass, int* passes_out,
  * kept from the last charge update; H = H0 + 1/2 S (Q_a + Q_b) on the
  * molecule-pair blocks, off-diagonal |H_mn| < eps set to zero. */
 int sscf_build_fock(sscf_ctx* ctx);
+
+/* A Fock (or any symmetric one-electron) matrix X built by the caller, for
+ * methods whose step IV is not the DFTB build (Section "Algorithm and
+ * computational details": only step IV is method specific; Section
+ * "Computation kernel for the matrix products C^T X C"). X is given as dense
+ * 6x6 blocks (row-major) on the molecule-pair pattern, in the pair order of
+ * sscf_get_blocks (host, n_mp * 36 doubles); block (n, m) must be the
+ * transpose of block (m, n). Off-diagonal |X_mn| < eps are set to zero, as
+ * in sscf_build_fock, and X replaces H until the next sscf_build_fock. Use it
+ * with sscf_rotate_sweep, sscf_orthonormalise and sscf_get_density_blocks;
+ * sscf_step and sscf_run build the DFTB H themselves. Errors: INVALID_ARG,
+ * NONFINITE, CUDA. */
+int sscf_set_fock_blocks(sscf_ctx* ctx, const double* X);
+
+/* Density matrix P = 2 C_occ C_occ^T (Eq. pop) of the current MOs on the
+ * molecule-pair pattern, the input of the caller's next Fock build: dense
+ * 6x6 blocks (row-major) in the pair order of sscf_get_blocks, into P (host,
+ * n_mp * 36 doubles), summed in FP64. Charges and mixing state are not
+ * changed. Errors: INVALID_ARG, STATE (before sscf_guess), OOM (its device
+ * buffer is allocated by the first call), CUDA. */
+int sscf_get_density_blocks(sscf_ctx* ctx, double* P);
 
 /* Step V (Section "Partial diagonalization"): F = C^T H C on the occupied-
  * virtual blocks of neighbouring groups plus diag(F); pairs with
@@ -190,9 +215,23 @@ int sscf_enable_graph(sscf_ctx* ctx, int enable);
 
 /* Loose stage (eps 1e-3, dq 1e-1), full orthonormalisation, user stage until
  * dq_max <= dq_tol and |dE| <= e_tol in every cluster, final occupied orthonormalisation to
- * eps / 100 and final charges and energy. Returns NOT_CONVERGED with the
- * state kept if max_scc is reached. */
+ * eps / 100 and final charges and energy. In mixed precision the SCC stages
+ * orthonormalise to max(eps / 100, 2^-19) (see sscf_orthonormalise); before
+ * the final orthonormalisation the context is widened to FP64
+ * (sscf_set_precision), so the final MOs, charges and energy are FP64 and the
+ * context stays FP64 afterwards. Returns NOT_CONVERGED with the state kept
+ * if max_scc is reached. */
 int sscf_run(sscf_ctx* ctx, sscf_step_info* info);
+
+/* Storage precision of a live context (no counterpart in the paper, whose
+ * orthonormalisation is FP64 and C^T H C FP32 throughout): SSCF_FP64 widens
+ * C, H and every per-step buffer to FP64, SSCF_MIXED rounds C to FP32. The MO
+ * coefficients and charges are kept (C converted value by value, H rebuilt
+ * from the current SCC input); the last transform's F and pair lists are
+ * dropped, and a captured CUDA graph is rebuilt at the next step. New buffers
+ * are allocated before the old ones are freed. Errors: INVALID_ARG, OOM (the
+ * context is then unchanged), CUDA. */
+int sscf_set_precision(sscf_ctx* ctx, int precision);
 
 /* Adjoint (no counterpart in the paper, which computes energies only): the
  * gradient of E = sum P*H0 + 1/2 dq^T gamma dq at the current MOs, assumed
@@ -241,8 +280,10 @@ int sscf_get_C_rows(sscf_ctx* ctx, int n, const int* rows, double* out);
  *   row block), vals (96 * n_stored doubles); any may be NULL, n_stored (if not
  *   NULL) receives the count, so a first call with NULL arrays sizes them.
  * sscf_set_C_tiles: the same arrays. Errors: INVALID_ARG (unsorted or foreign
- *   tile ids, negative counts), CAPACITY (more tiles than cap_tiles), NONFINITE;
- *   on any error the context is left unchanged. */
+ *   tile ids, negative counts), CAPACITY (more tiles than cap_tiles), NONFINITE,
+ *   OOM; on any of these the MOs are left unchanged. The arrays go to the device
+ *   in one copy each (page-locked host memory makes it faster) through a staging
+ *   buffer the context allocates at the first call and keeps, grown as needed. */
 int sscf_get_C_tiles(sscf_ctx* ctx, int32_t* nt, int32_t* tiles, double* vals, int64_t* n_stored);
 int sscf_set_C_tiles(sscf_ctx* ctx, const int32_t* nt, const int32_t* tiles, const double* vals);
 /* Columns of C for large systems: the MOs `cols` (n of them), dense over all
@@ -260,6 +301,14 @@ int sscf_get_H_dense(sscf_ctx* ctx, double* H, double* H0, double* S);
 /* Dense F_ov (n_occ x (n_mo - n_occ), zero off the kept blocks) and diag(F)
  * (n_mo) of the last transform. */
 int sscf_get_F_dense(sscf_ctx* ctx, double* F_ov, double* F_diag);
+/* sigma = C^T S C of the last orthonormalisation pass, before normalisation
+ * (Section "Orthonormalization", step b), dense over the pass's MOs (n x n,
+ * row-major, n = n_occ after an occupied pass, n_mo after a pass over all
+ * MOs; global MO order), zero off the blocks of neighbouring groups; the
+ * passes read entry (i, j) with i before j in pass order, and both halves
+ * hold it. n_out (may be NULL) receives n; sigma may be NULL to size it.
+ * Errors: STATE before the first orthonormalisation pass. */
+int sscf_get_overlap_dense(sscf_ctx* ctx, double* sigma, int* n_out);
 /* Charges: q_prev (last output charges), dq_in and Q_in (SCC input). */
 int sscf_get_charges(sscf_ctx* ctx, double* q_prev, double* dq_in, double* Q_in);
 int sscf_set_charges(sscf_ctx* ctx, const double* q_prev, const double* dq_in,
@@ -294,8 +343,9 @@ int sscf_get_pairs(sscf_ctx* ctx, int64_t capacity, int32_t* colour_out, int32_t
  * array of 16 MiB + 2304 bytes that every GPU loading the library holds
  * until the process exits. n above 2^21 (2,097,152) is rejected with
  * SSCF_ERR_INVALID_ARG. The first call on a device (with that device
- * current) looks up the array's device address; make that first call before
- * any stream capture. All calls share the array and it keeps the last call's
+ * current) looks up the array's device address, and so does the first call
+ * after that device's context was reset (cudaDeviceReset); make those calls
+ * before any stream capture. All calls share the array and it keeps the last call's
  * contents (each call clears what must start at zero); calls that overlap on
  * the GPU, from other streams or host threads, race on it. */
 int sscf_select_pairs_noalloc(const double* f, int64_t n, double tau, int64_t k_max, unsigned char* keep,

@@ -35,6 +35,7 @@ EXPORTED = [
     "sscf_select_pairs_noalloc", "sscf_gradients", "sscf_get_cluster_results",
     "sscf_enable_graph", "sscf_get_C_rows", "sscf_get_blocks",
     "sscf_get_C_cols", "sscf_get_F_entries", "sscf_get_C_tiles", "sscf_set_C_tiles", "sscf_autotune",
+    "sscf_set_precision", "sscf_set_fock_blocks", "sscf_get_density_blocks", "sscf_get_overlap_dense",
 ]
 
 
@@ -120,6 +121,10 @@ def load() -> ctypes.CDLL:
         "sscf_get_C_rows": (c_int, [c_vp, c_int, P(c_int), P(c_double)]),
         "sscf_get_C_cols": (c_int, [c_vp, c_int, P(c_int), P(c_double)]),
         "sscf_autotune": (c_int, [c_vp, P(c_int)]),
+        "sscf_set_precision": (c_int, [c_vp, c_int]),
+        "sscf_set_fock_blocks": (c_int, [c_vp, P(c_double)]),
+        "sscf_get_overlap_dense": (c_int, [c_vp, P(c_double), P(c_int)]),
+        "sscf_get_density_blocks": (c_int, [c_vp, P(c_double)]),
         "sscf_get_C_tiles": (c_int, [c_vp, P(ctypes.c_int32), P(ctypes.c_int32), P(c_double), P(c_i64)]),
         "sscf_set_C_tiles": (c_int, [c_vp, P(ctypes.c_int32), P(ctypes.c_int32), P(c_double)]),
         "sscf_get_F_entries": (c_int, [c_vp, c_int, P(c_int), P(c_int), P(c_double)]),
@@ -239,6 +244,10 @@ class Context:
                "sscf_orthonormalise")
         return n.value, eta.value
 
+    def set_precision(self, precision: int):
+        """Widen (SSCF_FP64) or narrow (SSCF_MIXED) the context's storage in place."""
+        _check(self.lib.sscf_set_precision(self.h, int(precision)), "sscf_set_precision")
+
     def build_fock(self):
         _check(self.lib.sscf_build_fock(self.h), "sscf_build_fock")
 
@@ -349,6 +358,19 @@ class Context:
                "sscf_get_blocks")
         return mn, H, H0, S
 
+    def set_fock_blocks(self, X):
+        """Caller-built Fock matrix: (n_mp, 6, 6) blocks in the pair order of get_blocks()."""
+        X = np.ascontiguousarray(X, dtype=np.float64)
+        _check(self.lib.sscf_set_fock_blocks(self.h, _ptr(X)), "sscf_set_fock_blocks")
+
+    def density_blocks(self) -> np.ndarray:
+        """P = 2 C_occ C_occ^T on the molecule-pair pattern, (n_mp, 6, 6) in the pair order of get_blocks()."""
+        n = ctypes.c_int64()
+        _check(self.lib.sscf_get_blocks(self.h, None, None, None, None, ctypes.byref(n)), "sscf_get_blocks")
+        P = np.empty((n.value, 6, 6))
+        _check(self.lib.sscf_get_density_blocks(self.h, _ptr(P)), "sscf_get_density_blocks")
+        return P
+
     def get_H(self):
         H, H0, S = (np.empty((self.n_ao, self.n_ao)) for _ in range(3))
         _check(self.lib.sscf_get_H_dense(self.h, _ptr(H), _ptr(H0), _ptr(S)), "sscf_get_H_dense")
@@ -359,6 +381,14 @@ class Context:
         d = np.empty(self.n_mo)
         _check(self.lib.sscf_get_F_dense(self.h, _ptr(F), _ptr(d)), "sscf_get_F_dense")
         return F, d
+
+    def get_overlap(self) -> np.ndarray:
+        """sigma = C^T S C of the last orthonormalisation pass (dense over the pass's MOs)."""
+        n = ctypes.c_int()
+        _check(self.lib.sscf_get_overlap_dense(self.h, None, ctypes.byref(n)), "sscf_get_overlap_dense")
+        sig = np.empty((n.value, n.value))
+        _check(self.lib.sscf_get_overlap_dense(self.h, _ptr(sig), None), "sscf_get_overlap_dense")
+        return sig
 
     def get_charges(self, out=None):
         q, dq, Q = out if out is not None else (np.empty(self.n_atoms) for _ in range(3))

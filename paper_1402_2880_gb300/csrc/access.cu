@@ -37,6 +37,45 @@ int fetch_values(Ctx& c, const void* dptr, size_t n, std::vector<double>& out) {
     return SSCF_OK;
 }
 
+// Restart of C: packed tiles (FP64, row block after row block) scattered into
+// the padded row layout of buffer 0, converted to the storage type.
+template <typename T>
+__global__ void k_scatter_tiles(int cap, const long long* __restrict__ row_off, const int* __restrict__ nt,
+                                const int* __restrict__ tiles, const double* __restrict__ vals,
+                                int* __restrict__ c_tile, T* __restrict__ c_val) {
+    const int r = blockIdx.x;
+    const long long o = row_off[r];
+    const int n = nt[r];
+    for (int s = threadIdx.x; s < n; s += blockDim.x) c_tile[(size_t)r * cap + s] = tiles[o + s];
+    const double* src = vals + o * kTileVals;
+    T* dst = c_val + (size_t)r * cap * kTileVals;
+    for (long long i = threadIdx.x; i < (long long)n * kTileVals; i += blockDim.x) dst[i] = (T)src[i];
+}
+
+// Non-finite check of the staged values (before anything of the context is written).
+__global__ void k_check_finite(long long n, const double* __restrict__ v, unsigned* __restrict__ bad) {
+    unsigned b = 0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        b |= isfinite(v[i]) ? 0u : 1u;
+    if (__any_sync(0xffffffffu, b != 0u) && (threadIdx.x & 31) == 0) atomicOr(bad, 1u);
+}
+
+// Staging buffer of the restart (kept and grown as needed).
+int stage(Ctx& c, size_t bytes, unsigned char** out) {
+    if (c.stage_bytes < bytes) {
+        dev_release(&c, c.d_stage);
+        c.d_stage = nullptr;
+        c.stage_bytes = 0;
+        void* p = nullptr;
+        int s = dev_alloc(&c, &p, bytes);
+        if (s != SSCF_OK) return s;
+        c.d_stage = (unsigned char*)p;
+        c.stage_bytes = bytes;
+    }
+    *out = c.d_stage;
+    return SSCF_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -165,28 +204,50 @@ int sscf_set_C_tiles(sscf_ctx* h, const int32_t* nt_in, const int32_t* tiles_in,
         }
         off += nt_in[r];
     }
-    for (int64_t i = 0; i < tot * kTileVals; ++i)
-        if (!std::isfinite(vals_in[i])) return SSCF_ERR_NONFINITE;
-    CKA(cudaStreamSynchronize(c.stream));
-    std::vector<int> tiles(c.cap);
-    std::vector<float> f((size_t)c.cap * kTileVals);
+    // one bulk copy of the packed arrays, a finiteness check on the device, then a
+    // scatter kernel into the padded rows
+    std::vector<long long> row_off(c.n_mol);
     off = 0;
     for (int r = 0; r < c.n_mol; ++r) {
-        const int n = nt_in[r];
-        if (n > 0) {
-            CKA(cudaMemcpy(c.d_c_tile[0] + (size_t)r * c.cap, tiles_in + off, (size_t)n * 4, cudaMemcpyHostToDevice));
-            void* dst = (unsigned char*)c.d_c_val[0] + (size_t)r * c.cap * kTileVals * c.tsize;
-            const double* src = vals_in + off * kTileVals;
-            if (c.prec == SSCF_FP64) {
-                CKA(cudaMemcpy(dst, src, (size_t)n * kTileVals * 8, cudaMemcpyHostToDevice));
-            } else {
-                for (size_t i = 0; i < (size_t)n * kTileVals; ++i) f[i] = (float)src[i];
-                CKA(cudaMemcpy(dst, f.data(), (size_t)n * kTileVals * 4, cudaMemcpyHostToDevice));
-            }
-        }
-        off += n;
+        row_off[r] = off;
+        off += nt_in[r];
     }
-    CKA(cudaMemcpy(c.d_c_nt[0], nt_in, (size_t)c.n_mol * 4, cudaMemcpyHostToDevice));
+    const size_t b_off = (size_t)c.n_mol * 8, b_nt = (size_t)c.n_mol * 4, b_tiles = ((size_t)tot * 4 + 15) & ~(size_t)15;
+    const size_t b_vals = (size_t)tot * kTileVals * 8;
+    unsigned char* st = nullptr;
+    int s = stage(c, b_off + ((b_nt + 15) & ~(size_t)15) + b_tiles + b_vals + 16, &st);
+    if (s != SSCF_OK) return s;
+    unsigned* d_bad = (unsigned*)(st + b_off + ((b_nt + 15) & ~(size_t)15) + b_tiles + b_vals);
+    long long* d_off = (long long*)st;
+    int* d_nt = (int*)(st + b_off);
+    int* d_tiles = (int*)(st + b_off + ((b_nt + 15) & ~(size_t)15));
+    double* d_vals = (double*)(st + b_off + ((b_nt + 15) & ~(size_t)15) + b_tiles);
+    CKA(cudaMemcpyAsync(d_off, row_off.data(), b_off, cudaMemcpyHostToDevice, c.stream));
+    CKA(cudaMemcpyAsync(d_nt, nt_in, b_nt, cudaMemcpyHostToDevice, c.stream));
+    CKA(cudaMemsetAsync(d_bad, 0, 4, c.stream));
+    if (tot > 0) {
+        CKA(cudaMemcpyAsync(d_tiles, tiles_in, (size_t)tot * 4, cudaMemcpyHostToDevice, c.stream));
+        CKA(cudaMemcpyAsync(d_vals, vals_in, b_vals, cudaMemcpyHostToDevice, c.stream));
+        const long long nv = tot * kTileVals;
+        const int blocks = (int)std::min<long long>((nv + 255) / 256, (long long)c.n_sm * 8);
+        k_check_finite<<<blocks, 256, 0, c.stream>>>(nv, d_vals, d_bad);
+        c.n_launch += 1;
+        CKA(cudaGetLastError());
+        unsigned bad = 0;
+        CKA(cudaMemcpyAsync(&bad, d_bad, 4, cudaMemcpyDeviceToHost, c.stream));
+        CKA(cudaStreamSynchronize(c.stream));
+        if (bad) return SSCF_ERR_NONFINITE;
+    }
+    if (c.prec == SSCF_FP64)
+        k_scatter_tiles<double><<<c.n_mol, 256, 0, c.stream>>>(c.cap, d_off, d_nt, d_tiles, d_vals, c.d_c_tile[0],
+                                                               (double*)c.d_c_val[0]);
+    else
+        k_scatter_tiles<float><<<c.n_mol, 256, 0, c.stream>>>(c.cap, d_off, d_nt, d_tiles, d_vals, c.d_c_tile[0],
+                                                              (float*)c.d_c_val[0]);
+    c.n_launch += 1;
+    CKA(cudaGetLastError());
+    CKA(cudaMemcpyAsync(c.d_c_nt[0], d_nt, b_nt, cudaMemcpyDeviceToDevice, c.stream));
+    CKA(cudaStreamSynchronize(c.stream));
     c.cur = 0;
     c.have_guess = true;
     return SSCF_OK;
@@ -374,6 +435,52 @@ int sscf_get_F_dense(sscf_ctx* h, double* F_ov, double* F_diag) {
     if (F_diag) {
         CKA(cudaStreamSynchronize(c.stream));
         CKA(cudaMemcpy(F_diag, c.d_Fd, (size_t)c.n_mo * 8, cudaMemcpyDeviceToHost));
+    }
+    return SSCF_OK;
+}
+
+// sigma = C^T S C of the last orthonormalisation pass (before normalisation),
+// dense over the pass's MOs: n_occ x n_occ after an occupied pass, n_mo x n_mo
+// after a pass over all MOs; zero off the kept blocks. The kernels read the
+// entries (i, j) with i before j in the pass order (lower group, or lower
+// local index inside one group); both halves hold those.
+int sscf_get_overlap_dense(sscf_ctx* h, double* sigma, int* n_out) {
+    if (!h) return SSCF_ERR_INVALID_ARG;
+    Ctx& c = h->c;
+    if (c.last_sched_kind != 2) return SSCF_ERR_STATE;
+    const int w = c.last_ortho_which;
+    const int n = w == 1 ? c.n_occ : c.n_mo;
+    if (n_out) *n_out = n;
+    if (!sigma) return SSCF_OK;
+    std::vector<double> v;
+    int s = fetch_values(c, c.d_sig, (size_t)std::max(c.n_ort_tp[w], 1) * 256, v);
+    if (s != SSCF_OK) return s;
+    std::memset(sigma, 0, sizeof(double) * (size_t)n * n);
+    auto side = [&](int g, int* t) {
+        int k = 0;
+        for (int i = 0; i < c.h_group_not[g]; ++i) t[k++] = c.h_group_ot0[g] + i;
+        if (w == 0)
+            for (int i = 0; i < c.h_group_nvt[g]; ++i) t[k++] = c.h_group_vt0[g] + i;
+        return k;
+    };
+    for (int e = 0; e < c.n_gnb; ++e) {
+        const int A = c.h_gnb_row[e], B = c.h_gnb_col[e];
+        if (A > B) continue;
+        int ta[3], tb[3];
+        const int na = side(A, ta), nb = side(B, tb);
+        for (int i = 0; i < na; ++i)
+            for (int j = 0; j < nb; ++j) {
+                const int tp = c.h_ort_blk_tp[w][(size_t)e * 9 + i * 3 + j];
+                if (tp < 0) continue;
+                for (int ca = 0; ca < c.h_tile_nmo[ta[i]]; ++ca)
+                    for (int cb = 0; cb < c.h_tile_nmo[tb[j]]; ++cb) {
+                        if (A == B && i == j && cb < ca) continue;
+                        const size_t gi = (size_t)c.h_tile_mo0[ta[i]] + ca, gj = (size_t)c.h_tile_mo0[tb[j]] + cb;
+                        const double x = v[(size_t)tp * 256 + ca * 16 + cb];
+                        sigma[gi * n + gj] = x;
+                        sigma[gj * n + gi] = x;
+                    }
+            }
     }
     return SSCF_OK;
 }

@@ -441,12 +441,28 @@ int prof_collect(Ctx& c) {
         CK(call);                 \
     } while (0)
 
+// Storage-type conversion of n values (FP32 <-> FP64).
+template <typename S, typename D>
+__global__ void k_convert(size_t n, const S* __restrict__ in, D* __restrict__ out) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        out[i] = (D)in[i];
+}
+
 void drop_graph(Ctx& c) {
     if (c.graph_exec) cudaGraphExecDestroy(c.graph_exec);
     if (c.graph) cudaGraphDestroy(c.graph);
     c.graph_exec = nullptr;
     c.graph = nullptr;
     c.graph_valid = false;
+}
+
+// Target of an orthonormalisation (Section "Sparsity and numerical accuracy":
+// eps / 100), floored at what the storage precision resolves: 32 u_fp32 =
+// 2^-19 for FP32 storage, where eps / 100 can lie below the rounding of the
+// stored MOs, and 1e-13 for FP64 storage, where it matters only as eps -> 0.
+double ortho_target(const Ctx& c, double eps) {
+    const double floor_ = c.prec == SSCF_MIXED ? 32.0 * 0x1p-24 : 1e-13;
+    return std::max(eps / 100.0, floor_);
 }
 
 int sync_scalars(Ctx& c) {
@@ -478,6 +494,19 @@ int dev_alloc(Ctx* c, void** p, size_t bytes) {
     c->allocations.push_back(q);
     *p = q;
     return SSCF_OK;
+}
+
+void dev_release(Ctx* c, void* p) {
+    if (!p) return;
+    for (size_t i = 0; i < c->allocations.size(); ++i)
+        if (c->allocations[i] == p) {
+            c->allocations.erase(c->allocations.begin() + (long)i);
+            break;
+        }
+    if (g_free)
+        g_free(p, g_alloc_user);
+    else
+        cudaFree(p);
 }
 
 void dev_free_all(Ctx* c) {
@@ -830,6 +859,56 @@ int sscf_set_thresholds(sscf_ctx* h, double eps, double dq_tol, double e_tol) {
     return SSCF_OK;
 }
 
+int sscf_set_precision(sscf_ctx* h, int precision) {
+    if (!h || (precision != SSCF_FP64 && precision != SSCF_MIXED)) return SSCF_ERR_INVALID_ARG;
+    Ctx& c = h->c;
+    if (precision == c.prec) return SSCF_OK;
+    drop_graph(c);
+    CK(cudaStreamSynchronize(c.stream));
+    const size_t ts = precision == SSCF_FP64 ? 8 : 4;
+    int max_ort = std::max(std::max(c.n_ort_tp[0], c.n_ort_tp[1]), 1);
+    // every buffer whose element type follows the storage precision, with its value count
+    void** bufs[] = {&c.d_Hb, &c.d_Sbt, &c.d_c_val[0], &c.d_c_val[1], &c.d_y_val,
+                     &c.d_F, &c.d_Fdiag_tiles, &c.d_sig, &c.d_pr_cs};
+    const size_t counts[] = {(size_t)c.n_mp * 36, (size_t)c.n_mp * 36, (size_t)c.n_mol * c.cap * kTileVals,
+                             (size_t)c.n_mol * c.cap * kTileVals, (size_t)c.n_tiles * c.capY * kTileVals,
+                             (size_t)std::max(c.n_rot_tp, 1) * 256, (size_t)c.n_tiles * 256, (size_t)max_ort * 256,
+                             (size_t)c.n_gnb * kOrthoCap * 2};
+    constexpr int nb = sizeof(counts) / sizeof(counts[0]);
+    void* fresh[nb] = {nullptr};
+    for (int i = 0; i < nb; ++i) {
+        if (dev_alloc(&c, &fresh[i], counts[i] * ts) != SSCF_OK) {
+            for (int j = 0; j < i; ++j) dev_release(&c, fresh[j]);
+            return SSCF_ERR_OOM;   // the context is unchanged
+        }
+    }
+    // only the current C buffer holds state; H and S in storage precision are
+    // rebuilt below, everything else is rewritten by the next step
+    const int cb = 2 + c.cur;
+    const size_t n = counts[cb];
+    const int th = 256, blocks = (int)std::min<size_t>((n + th - 1) / th, (size_t)c.n_sm * 16);
+    if (precision == SSCF_FP64)
+        k_convert<float, double><<<blocks, th, 0, c.stream>>>(n, (const float*)*bufs[cb], (double*)fresh[cb]);
+    else
+        k_convert<double, float><<<blocks, th, 0, c.stream>>>(n, (const double*)*bufs[cb], (float*)fresh[cb]);
+    c.n_launch += 1;
+    if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(c.stream) != cudaSuccess) {
+        cudaGetLastError();
+        for (int j = 0; j < nb; ++j) dev_release(&c, fresh[j]);
+        return SSCF_ERR_CUDA;
+    }
+    for (int i = 0; i < nb; ++i) {
+        dev_release(&c, *bufs[i]);
+        *bufs[i] = fresh[i];
+    }
+    c.prec = precision;
+    c.prm.precision = precision;
+    c.tsize = ts;
+    CK(launch_build_h(&c, c.prm.eps));
+    CK(cudaStreamSynchronize(c.stream));
+    return SSCF_OK;
+}
+
 int sscf_get_dims(const sscf_ctx* h, int* n_ao, int* n_mo, int* n_occ, int* n_groups, int* n_tiles,
                   int* n_colours) {
     if (!h) return SSCF_ERR_INVALID_ARG;
@@ -859,6 +938,43 @@ int sscf_build_fock(sscf_ctx* h) {
     if (!h) return SSCF_ERR_INVALID_ARG;
     Ctx& c = h->c;
     PK("build_fock", launch_build_h(&c, c.prm.eps));
+    return SSCF_OK;
+}
+
+int sscf_set_fock_blocks(sscf_ctx* h, const double* X) {
+    if (!h || !X) return SSCF_ERR_INVALID_ARG;
+    Ctx& c = h->c;
+    const size_t n = (size_t)c.n_mp * 36;
+    for (size_t i = 0; i < n; ++i)
+        if (!std::isfinite(X[i])) return SSCF_ERR_NONFINITE;
+    // the same threshold as the DFTB build: off-diagonal |X_mn| < eps -> 0
+    std::vector<double> v(X, X + n);
+    for (int m = 0; m < c.n_mol; ++m)
+        for (int e = c.h_mp_ptr[m]; e < c.h_mp_ptr[m + 1]; ++e)
+            for (int u = 0; u < 36; ++u) {
+                const bool diag = c.h_mp_col[e] == m && u / 6 == u % 6;
+                double& x = v[(size_t)e * 36 + u];
+                if (!diag && std::fabs(x) < c.prm.eps) x = 0.0;
+            }
+    drop_graph(c);
+    CK(cudaStreamSynchronize(c.stream));
+    if (c.prec == SSCF_FP64) {
+        CK(cudaMemcpy(c.d_Hb, v.data(), n * 8, cudaMemcpyHostToDevice));
+    } else {
+        std::vector<float> f(v.begin(), v.end());
+        CK(cudaMemcpy(c.d_Hb, f.data(), n * 4, cudaMemcpyHostToDevice));
+    }
+    return SSCF_OK;
+}
+
+int sscf_get_density_blocks(sscf_ctx* h, double* P) {
+    if (!h || !P) return SSCF_ERR_INVALID_ARG;
+    Ctx& c = h->c;
+    if (!c.have_guess) return SSCF_ERR_STATE;
+    if (!c.d_P) CKS(dalloc(&c, &c.d_P, (size_t)c.n_mp * 36));
+    PK("density", launch_density(&c, c.d_P));
+    CK(cudaStreamSynchronize(c.stream));
+    CK(cudaMemcpy(P, c.d_P, (size_t)c.n_mp * 36 * 8, cudaMemcpyDeviceToHost));
     return SSCF_OK;
 }
 
@@ -946,7 +1062,7 @@ int sscf_orthonormalise(sscf_ctx* h, int which, int max_pass, int* passes_out, d
     if (!h || (which != SSCF_ORTHO_ALL && which != SSCF_ORTHO_OCC) || max_pass < 1) return SSCF_ERR_INVALID_ARG;
     Ctx& c = h->c;
     if (!c.have_guess) return SSCF_ERR_STATE;
-    const double tol = c.prm.eps / 100.0;
+    const double tol = ortho_target(c, c.prm.eps);
     int k = 0;
     double eta = 0.0;
     for (k = 1; k <= max_pass; ++k) {
@@ -1008,7 +1124,7 @@ static int step_device(Ctx& c) {
     CK(cudaMemsetAsync(c.d_sc, 0, offsetof(DeviceScalars, hist), c.stream));
     PK("build_fock", launch_build_h(&c, c.prm.eps));
     CKS(rotate_sweep_async(c));
-    if (c.prm.ortho_every) CKS(ortho_pass_async(c, SSCF_ORTHO_OCC, c.prm.eps / 100.0));
+    if (c.prm.ortho_every) CKS(ortho_pass_async(c, SSCF_ORTHO_OCC, ortho_target(c, c.prm.eps)));
     CKS(density_async(c, true));
     CK(launch_count_tiles(&c, c.d_sc->tiles));
     return SSCF_OK;
@@ -1183,6 +1299,10 @@ int sscf_run(sscf_ctx* h, sscf_step_info* info) {
     c.prm.eps = eps_u;
     c.prm.dq_tol = dq_u;
     c.prm.e_tol = e_u;
+    // mixed precision: the SCC stages orthonormalised to max(eps / 100, 32 u_fp32);
+    // the MOs are widened to FP64 and the occupied ones polished to eps / 100
+    // before the final charges and energy (the context stays FP64)
+    if (c.prec == SSCF_MIXED) CKS(sscf_set_precision(h, SSCF_FP64));
     CKS(sscf_orthonormalise(h, SSCF_ORTHO_OCC, 200, nullptr, nullptr));
     double E = 0.0;
     CK(cudaMemsetAsync(c.d_sc, 0, sizeof(unsigned), c.stream));

@@ -376,7 +376,7 @@ __global__ void __launch_bounds__(kDensWarps * 32, kDensMinBlocks)
 k_density(int n_occ_tiles, int map_n, const int* __restrict__ mol_ot0, int cap, const int* __restrict__ c_nt,
           const int* __restrict__ c_tile, const T* __restrict__ c_val, const int* __restrict__ mp_ptr,
           const int* __restrict__ mp_col, const double* __restrict__ H0b, const double* __restrict__ Sb,
-          double* __restrict__ q, double* __restrict__ e_mol) {
+          double* __restrict__ q, double* __restrict__ e_mol, double* __restrict__ P_out) {
     // slot of every occupied tile of m's cluster in row m, or -1 (map_n = largest cluster);
     // then, in mixed precision, the FP64 sums of each lane's 36 products (flushed
     // from FP32 every kDensFlush tiles), kept in shared memory to save registers
@@ -482,6 +482,7 @@ k_density(int n_occ_tiles, int map_n, const int* __restrict__ mol_ot0, int cap, 
             double v = 0.0;
             for (int j = 0; j < 32; ++j) v += row[(j + lane) & 31];
             const double P = 2.0 * v;
+            if (P_out) P_out[(size_t)e * 36 + u] = P;
             const int k = u / 6;   // AO of m: O s, p, p, p, then H1 s, H2 s
             const double pq = P * Sb[(size_t)e * 36 + u];
             qa[0] += k < 4 ? pq : 0.0;
@@ -632,7 +633,7 @@ cudaError_t launch_transform_ortho(Ctx* c, int w) {
     return transform_t<float>(c, c->d_ort_tp_ptr[w], c->d_ort_tp_b[w], c->d_ort_tp_out[w], c->d_sig);
 }
 
-cudaError_t launch_density(Ctx* c) {
+cudaError_t launch_density(Ctx* c, double* P_out) {
     c->n_launch += 1;
     cudaError_t e = ensure_attrs();
     if (e != cudaSuccess) return e;
@@ -642,11 +643,11 @@ cudaError_t launch_density(Ctx* c) {
     if (c->prec == SSCF_FP64)
         k_density<double><<<c->n_mol, kDensWarps * 32, smem, c->stream>>>(c->n_occ_tiles, c->max_cl_otiles, c->d_mol_ot0, c->cap, c->d_c_nt[b], c->d_c_tile[b],
                                                               (const double*)c->d_c_val[b], c->d_mp_ptr,
-                                                              c->d_mp_col, c->d_H0b, c->d_Sb, c->d_q, c->d_e_mol);
+                                                              c->d_mp_col, c->d_H0b, c->d_Sb, c->d_q, c->d_e_mol, P_out);
     else
         k_density<float><<<c->n_mol, kDensWarps * 32, smem, c->stream>>>(c->n_occ_tiles, c->max_cl_otiles, c->d_mol_ot0, c->cap, c->d_c_nt[b], c->d_c_tile[b],
                                                              (const float*)c->d_c_val[b], c->d_mp_ptr, c->d_mp_col,
-                                                             c->d_H0b, c->d_Sb, c->d_q, c->d_e_mol);
+                                                             c->d_H0b, c->d_Sb, c->d_q, c->d_e_mol, P_out);
     return cudaGetLastError();
 }
 

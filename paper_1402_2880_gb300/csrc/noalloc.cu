@@ -7,6 +7,8 @@
 // at most k_max of the largest, ties at the cut kept) on arrays they already
 // own. Its working memory is a file-scope __device__ array: every GPU that
 // loads the library holds it (kNoallocScratchBytes) until the process exits.
+#include <cuda.h>
+
 #include <algorithm>
 #include <mutex>
 
@@ -31,6 +33,7 @@ static_assert(kNoallocScratchBytes == 16 * 1024 * 1024 + 288 * 8, "scratch size 
 
 std::mutex g_setup_mutex;
 void* g_scratch_ptr[64] = {nullptr};
+CUcontext g_scratch_ctx[64] = {nullptr};   // context the address was looked up in
 
 __device__ __forceinline__ unsigned long long key_of(double v) {
     return (unsigned long long)__double_as_longlong(v);
@@ -99,23 +102,47 @@ __global__ void k_na_mark(const double* __restrict__ f, long long n, double tau,
     if ((threadIdx.x & 31) == 0 && kept) atomicAdd(&s[kKept], kept);
 }
 
+// The CUDA context current on this thread (driver entry point through the
+// runtime, so the library needs no link to the driver library); NULL when
+// none is current yet or the lookup is unavailable.
+CUcontext current_context() {
+    using GetCurrentFn = CUresult (*)(CUcontext*);
+    static GetCurrentFn fn = [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess) {
+            cudaGetLastError();
+            p = nullptr;
+        }
+        return (GetCurrentFn)p;
+    }();
+    CUcontext c = nullptr;
+    if (!fn || fn(&c) != CUDA_SUCCESS) return nullptr;
+    return c;
+}
+
 // Set-up, once per device, with that device current: the device address of
 // the scratch array (in host code its name is only a stand-in, not a device
-// address).
+// address). The address belongs to the device's context: after a reset of
+// that context (cudaDeviceReset) the module is loaded again, so the address is
+// looked up again whenever the current context is not the one it came from.
 int scratch_for_current_device(unsigned long long** out) {
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
         cudaGetLastError();
         return SSCF_ERR_CUDA;
     }
+    CUcontext cur = current_context();
     std::lock_guard<std::mutex> lock(g_setup_mutex);
-    if (!g_scratch_ptr[dev]) {
+    if (!g_scratch_ptr[dev] || cur == nullptr || cur != g_scratch_ctx[dev]) {
         void* p = nullptr;
         if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || p == nullptr) {
             cudaGetLastError();
             return SSCF_ERR_CUDA;
         }
         g_scratch_ptr[dev] = p;
+        g_scratch_ctx[dev] = current_context();   // current now: the lookup made it so
     }
     *out = (unsigned long long*)g_scratch_ptr[dev];
     return SSCF_OK;

@@ -227,6 +227,9 @@ struct Ctx {
     double* d_dq = nullptr;
     double* d_Q = nullptr;
     double* d_e_mol = nullptr;    // n_mol band-energy partials
+    double* d_P = nullptr;        // n_mp * 36: density blocks (allocated by the first sscf_get_density_blocks)
+    unsigned char* d_stage = nullptr;   // staging of sscf_set_C_tiles (grown as needed)
+    size_t stage_bytes = 0;
     double* d_red = nullptr;      // reduction scratch (n_mol + 1024)
     double* d_grad = nullptr;     // 3 n_atoms: dE/dxyz
     double* d_par = nullptr;      // 8: dE/d(V0, S0)
@@ -259,6 +262,7 @@ struct Ctx {
 
 // ---- memory -----------------------------------------------------------------
 int dev_alloc(Ctx* c, void** p, size_t bytes);
+void dev_release(Ctx* c, void* p);   // frees one allocation of dev_alloc
 void dev_free_all(Ctx* c);
 
 template <typename P>
@@ -277,7 +281,7 @@ cudaError_t launch_colindex(Ctx* c);
 cudaError_t launch_xc(Ctx* c, bool use_h, int tile_lo, int tile_hi);
 cudaError_t launch_transform_rot(Ctx* c);
 cudaError_t launch_transform_ortho(Ctx* c, int which);
-cudaError_t launch_density(Ctx* c);
+cudaError_t launch_density(Ctx* c, double* P_out = nullptr);   // P blocks (n_mp x 36) too, if not NULL
 // schedules and sweeps
 cudaError_t launch_select_rot(Ctx* c);
 cudaError_t launch_ortho_prepare(Ctx* c, int which, double tol);

@@ -101,3 +101,30 @@ def test_capacity_overflow_keeps_state():
     assert np.array_equal(ctx.get_C(), C0)
     q1, dq1, Q1 = ctx.get_charges()
     assert np.array_equal(q1, q0) and np.array_equal(dq1, dq0) and np.array_equal(Q1, Q0)
+
+
+@pytest.mark.gpu
+def test_restart_refuses_bad_checkpoints_and_keeps_the_mos():
+    from gpu_common import context, water
+    from paper_1402_2880_gb300 import SscfError
+    ctx = context(water(32), precision=1)
+    ctx.set_thresholds(1e-5, 1e-4, 1e-8)
+    ctx.guess()
+    ctx.orthonormalise(0)
+    C0 = ctx.get_C()
+    nt, tiles, vals = ctx.get_C_tiles()
+    bad = vals.copy()
+    bad[5, 2, 3] = np.inf
+    with pytest.raises(SscfError) as e:
+        ctx.set_C_tiles(nt, tiles, bad)
+    assert e.value.status == -4
+    assert np.array_equal(ctx.get_C(), C0)
+    unsorted = tiles.copy()
+    unsorted[[0, 1]] = unsorted[[1, 0]]
+    with pytest.raises(SscfError) as e:
+        ctx.set_C_tiles(nt, unsorted, vals)
+    assert e.value.status == -1
+    assert np.array_equal(ctx.get_C(), C0)
+    ctx.step()
+    ctx.set_C_tiles(nt, tiles, vals)                 # restart from the checkpoint
+    assert np.array_equal(ctx.get_C(), C0)

@@ -4,12 +4,14 @@ For callers that cannot allocate device memory, sscf_select_pairs_noalloc
 applies the rotation-pair rule of a sweep to arrays they own, with its
 working memory in a file-scope device array. This file runs last: it checks
 two calls in a row against the pairs the regular entry point chose from the
-same F values, and that oversized inputs are refused.
+same F values and against the oracle's selection rule on those values, and
+that oversized inputs are refused.
 """
 import numpy as np
 import pytest
 
-from gpu_common import P, context, water
+from gpu_common import P, context, oracle_scf, water
+from oracle import sparse
 
 pytestmark = pytest.mark.gpu
 
@@ -47,6 +49,9 @@ def test_noalloc_selection_matches_rotate_sweep_twice():
         got, n_keep = _noalloc_keep(F, eps, k_max)
         assert n_keep == n_rot == int(want.sum())
         assert np.array_equal(got, want), f"call {call}"
+        st = oracle_scf(n).st
+        mask = st.group_nb[st.mo_group[:st.n_occ][:, None], st.mo_group[st.n_occ:][None, :]]
+        assert np.array_equal(got, sparse.select_pairs(F, mask, eps, k_max)), f"call {call}"
         capped.append(int(((np.abs(F) >= eps) & (F != 0)).sum()) > k_max)
     assert any(capped), "at least one call must exercise the top-k cap"
 
