@@ -231,6 +231,9 @@ def ortho_pass(C: np.ndarray, S: np.ndarray, st: Structure, which: str,
                tol: float, trunc: float, sigma: np.ndarray | None = None):
     """One pass of steps b-d; returns (eta, number of combinations).
 
+    A pass that finds eta below the target has found the MOs orthonormal: it
+    ends the orthonormalisation (step e) without normalising again.
+
     ``sigma`` (optional) supplies the overlaps of step b instead of computing
     them, so that steps c-d can be checked alone on given overlaps.
     """
@@ -240,12 +243,12 @@ def ortho_pass(C: np.ndarray, S: np.ndarray, st: Structure, which: str,
         sigma = Cm.T @ (S @ Cm)                  # step b: C^T S C
     sigma = np.where(overlap_mask(st, mos), sigma, 0.0)
     d = np.sqrt(np.diag(sigma))
-    C[:, mos] = Cm / d[None, :]                  # step c: normalise
     sig_n = sigma / np.outer(d, d)
     off = np.abs(sig_n - np.diag(np.diag(sig_n)))
     eta = float(off.max()) if off.size else 0.0
     if eta < tol:
-        return eta, 0
+        return eta, 0                            # converged: the pass changes nothing
+    C[:, mos] = Cm / d[None, :]                  # step c: normalise
     sel = overlap_mask(st, mos) & (np.abs(sig_n) >= 1e-3 * eta)
     np.fill_diagonal(sel, False)
     pa, pb = ortho_schedule(st, which, mos, sel)

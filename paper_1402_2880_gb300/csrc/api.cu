@@ -1045,6 +1045,7 @@ int sscf_autotune(sscf_ctx* h, int* tf_split_out) {
 
 static int ortho_pass_async(Ctx& c, int which, double tol) {
     const int w = which == SSCF_ORTHO_OCC ? 1 : 0;
+    c.ortho_tol = tol;
     PK("colindex", launch_colindex(&c));
     PK("xc_s", launch_xc(&c, false, 0, w == 1 ? c.n_occ_tiles : c.n_tiles));
     PK("transform_ss", launch_transform_ortho(&c, w));

@@ -408,7 +408,9 @@ struct SweepArgs {
     const int* pr_touch;     // tiles of each side a block's pairs touch: bits 0-2 side A, 3-5 side B
     const uint16_t* pr_ij;
     const void* pr_cs;
-    const double* dsc;       // combinations: divide the pass's MOs by d_i first
+    const double* dsc;       // combinations: divide the pass's MOs by d_i first ...
+    const double* cl_eta;    // ... in clusters whose eta is not below the pass's target
+    double tol;              // (below it the pass has converged and changes nothing)
     unsigned long long* upd; // counter of 2x2 row updates
     const int* cci_ptr;
     const int* cci_row;
@@ -576,12 +578,13 @@ __global__ void __launch_bounds__(256) k_closure(SweepArgs a) {
         a.out_nz[(size_t)r * a.cap + s] = map[lt(a.out_tile[(size_t)r * a.cap + s])] >= 0 ? 1 : 0;
     const T* inv = (const T*)a.in_val;
     T* outv = (T*)a.out_val;
+    const bool normalise = a.mode == 1 && !(a.cl_eta[k] < a.tol);
     for (int idx = threadIdx.x; idx < n1 * kTileVals; idx += blockDim.x) {
         const int s = idx / kTileVals, e = idx % kTileVals, col = e & 15;
         const int t = a.out_tile[(size_t)r * a.cap + s];
         const int os = map[lt(t)];
         T v = os >= 0 ? inv[((size_t)r * a.cap + os) * kTileVals + e] : (T)0;
-        if (a.mode == 1 && os >= 0 && (a.which == 0 || a.tile_kind[t] == 0) && col < a.tile_nmo[t])
+        if (normalise && os >= 0 && (a.which == 0 || a.tile_kind[t] == 0) && col < a.tile_nmo[t])
             v = v / (T)a.dsc[a.tile_mo0[t] + col];
         outv[((size_t)r * a.cap + s) * kTileVals + e] = v;
     }
@@ -1325,6 +1328,8 @@ static void fill_args(Ctx* c, SweepArgs& a, int mode, int which) {
     a.pr_ij = c->d_pr_ij;
     a.pr_cs = c->d_pr_cs;
     a.dsc = c->d_scale;
+    a.cl_eta = c->d_cl_eta;
+    a.tol = c->ortho_tol;
     a.upd = &c->d_sc->upd[mode == 0 ? 0 : 1];
     a.cci_ptr = c->d_cci_ptr;
     a.cci_row = c->d_cci_row;

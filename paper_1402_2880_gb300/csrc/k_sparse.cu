@@ -239,10 +239,38 @@ __global__ void k_xc(int tile_lo, int n_rows, int cap, int capY, const int* __re
 // ---------------------------------------------------------------------------
 constexpr int kTfWarps = 8;
 constexpr int kStage = 4;   // row blocks staged per warp at a time
+constexpr int kTcStride = 24;   // floats per staged AO row in the tensor-core path (bank-conflict-free fragments)
+constexpr int kTcRows = kStage * kAoPerMol;   // staged AO rows (K) per round: 24 = 3 k-steps of 8
+
+// x = hi + lo with hi, lo in TF32 (10 explicit mantissa bits each): hi by
+// round-to-nearest, lo the rounded remainder, so hi + lo carries ~21 bits.
+__device__ __forceinline__ void split_tf32(float x, uint32_t& hi, uint32_t& lo) {
+    uint32_t h, l;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(h) : "f"(x));
+    const float r = x - __uint_as_float(h);
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(l) : "f"(r));
+    hi = h;
+    lo = l;
+}
+
+// D (16x8, FP32) += A (16x8, TF32, row-major) x B (8x8, TF32, column-major)
+__device__ __forceinline__ void mma_tf32(float (&d)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
+        "{%0, %1, %2, %3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
 
 template <typename T> struct V4;
 template <> struct V4<float> { using type = float4; };
 template <> struct V4<double> { using type = double2; };
+
+// Staged values per warp: FP64 [kStage][2][96]; FP32 (tensor cores) C rows
+// then Y rows, kTcRows rows of kTcStride floats each.
+template <typename T> __host__ __device__ constexpr int tf_stage_vals() {
+    return std::is_same<T, float>::value ? 2 * kTcRows * kTcStride : kStage * 2 * kTileVals;
+}
 
 template <typename T>
 __global__ void __launch_bounds__(kTfWarps * 32)
@@ -252,8 +280,8 @@ k_transform(int n_split, int n_rows, const int* __restrict__ tile_row0, int cap,
             const int* __restrict__ cci_slot, const T* __restrict__ c_val, const int* __restrict__ y_n,
             const int* __restrict__ y_row, const T* __restrict__ y_val, T* __restrict__ out) {
     extern __shared__ __align__(16) unsigned char sraw[];
-    T* stage = (T*)sraw;                                        // [warps][kStage][2][96]
-    int* slot_of = (int*)(stage + (size_t)kTfWarps * kStage * 2 * kTileVals);   // n_rows (cluster-local)
+    T* stage = (T*)sraw;                                        // [warps][tf_stage_vals]
+    int* slot_of = (int*)(stage + (size_t)kTfWarps * tf_stage_vals<T>());   // n_rows (cluster-local)
     // CTA (a, s) takes the pairs of tile a with index = s (mod n_split)
     const int a = blockIdx.x / n_split, split = blockIdx.x % n_split;
     const int p0 = tp_ptr[a], p1 = tp_ptr[a + 1];
@@ -265,7 +293,110 @@ k_transform(int n_split, int n_rows, const int* __restrict__ tile_row0, int cap,
     for (int k = threadIdx.x; k < nc; k += blockDim.x) slot_of[cci_row[lo + k] - r0] = cci_slot[lo + k];
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    T* buf = stage + (size_t)warp * kStage * 2 * kTileVals;
+    T* buf = stage + (size_t)warp * tf_stage_vals<T>();
+    if constexpr (std::is_same<T, float>::value) {
+        // FP32 storage: the 16x16 block is two m16n8 tensor-core tiles, K = the
+        // staged AO rows (up to 4 matched row blocks = 24 rows = 3 k-steps of 8).
+        // Each product is split into TF32 hi + lo parts and summed as
+        // hi*hi + hi*lo + lo*hi (the lo*lo term is below FP32 rounding), into
+        // FP32 fragments flushed to FP64 every 32 of b's rows, as the FP64 path.
+        float* bc = buf;                          // [kTcRows][kTcStride]: C[r, a] rows
+        float* by = buf + kTcRows * kTcStride;    // [kTcRows][kTcStride]: Y[r, b] rows
+        const int gq = lane >> 2, tq = lane & 3;
+        for (int p = p0 + split + warp * n_split; p < p1; p += kTfWarps * n_split) {
+            const int b = tp_b[p];
+            const int nb = y_n[b];
+            const int* yr = y_row + (size_t)b * capY;
+            float acc[2][4];
+            double accd[2][4];
+#pragma unroll
+            for (int h = 0; h < 2; ++h)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    acc[h][q] = 0.f;
+                    accd[h][q] = 0.0;
+                }
+            for (int k0 = 0; k0 < nb; k0 += 32) {
+                const int k = k0 + lane;
+                const int sl = k < nb ? slot_of[yr[k] - r0] : -1;
+                unsigned m = __ballot_sync(0xffffffffu, sl >= 0);
+                while (m) {
+                    int rows[kStage];
+                    int nst = 0;
+#pragma unroll
+                    for (int g = 0; g < kStage; ++g) {
+                        rows[g] = -1;
+                        if (m) {
+                            rows[g] = __ffs(m) - 1;
+                            m &= m - 1;
+                            ++nst;
+                        }
+                    }
+                    // slot of a and position in b's list of every staged row block (warp-uniform)
+                    int ssv[kStage], kkv[kStage];
+#pragma unroll
+                    for (int g = 0; g < kStage; ++g) {
+                        const int src_lane = rows[g] < 0 ? 0 : rows[g];
+                        ssv[g] = __shfl_sync(0xffffffffu, sl, src_lane);
+                        kkv[g] = k0 + src_lane;
+                    }
+                    // stage: per row block 6 AO rows of C[r, a] and of Y[r, b], 16-byte pieces
+                    for (int v = lane; v < nst * 48; v += 32) {
+                        const int g = v / 48, rem = v - 48 * g, w = rem / 24, idx = rem - 24 * w;
+                        const int q = idx >> 2, part = idx & 3;
+                        int ss = 0, kk = 0;
+#pragma unroll
+                        for (int u = 0; u < kStage; ++u)
+                            if (u == g) {
+                                ss = ssv[u];
+                                kk = kkv[u];
+                            }
+                        const float4* src =
+                            w == 0 ? (const float4*)(c_val + ((size_t)yr[kk] * cap + ss) * kTileVals + q * 16) + part
+                                   : (const float4*)(y_val + ((size_t)b * capY + kk) * kTileVals + q * 16) + part;
+                        *(float4*)((w == 0 ? bc : by) + (g * kAoPerMol + q) * kTcStride + 4 * part) = *src;
+                    }
+                    __syncwarp();
+                    const int nkr = nst * kAoPerMol;
+                    for (int ks = 0; ks < nkr; ks += 8) {
+                        const int ka = ks + tq, kb = ks + tq + 4;
+                        const bool va = ka < nkr, vb = kb < nkr;
+                        uint32_t ah[4], al[4];
+                        split_tf32(va ? bc[ka * kTcStride + gq] : 0.f, ah[0], al[0]);
+                        split_tf32(va ? bc[ka * kTcStride + gq + 8] : 0.f, ah[1], al[1]);
+                        split_tf32(vb ? bc[kb * kTcStride + gq] : 0.f, ah[2], al[2]);
+                        split_tf32(vb ? bc[kb * kTcStride + gq + 8] : 0.f, ah[3], al[3]);
+#pragma unroll
+                        for (int h = 0; h < 2; ++h) {
+                            uint32_t bh[2], bl[2];
+                            split_tf32(va ? by[ka * kTcStride + 8 * h + gq] : 0.f, bh[0], bl[0]);
+                            split_tf32(vb ? by[kb * kTcStride + 8 * h + gq] : 0.f, bh[1], bl[1]);
+                            mma_tf32(acc[h], al, bh);
+                            mma_tf32(acc[h], ah, bl);
+                            mma_tf32(acc[h], ah, bh);
+                        }
+                    }
+                    __syncwarp();
+                }
+#pragma unroll
+                for (int h = 0; h < 2; ++h)
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        accd[h][q] += (double)acc[h][q];
+                        acc[h][q] = 0.f;
+                    }
+            }
+            T* o = out + (size_t)tp_out[p] * 256;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                o[gq * 16 + 8 * h + 2 * tq] = (T)accd[h][0];
+                o[gq * 16 + 8 * h + 2 * tq + 1] = (T)accd[h][1];
+                o[(gq + 8) * 16 + 8 * h + 2 * tq] = (T)accd[h][2];
+                o[(gq + 8) * 16 + 8 * h + 2 * tq + 1] = (T)accd[h][3];
+            }
+        }
+        return;
+    }
     const int i0 = 2 * (lane >> 2), j0 = 4 * (lane & 3);
     using A = typename Acc<T>::type;
     using VT = typename V4<T>::type;
@@ -592,7 +723,7 @@ cudaError_t launch_xc(Ctx* c, bool use_h, int tile_lo, int tile_hi) {
 
 template <typename T>
 static cudaError_t transform_t(Ctx* c, const int* ptr, const int* bl, const int* outl, void* out) {
-    const size_t smem = (size_t)kTfWarps * kStage * 2 * kTileVals * sizeof(T) + (size_t)c->max_cl_mol * 4;
+    const size_t smem = (size_t)kTfWarps * tf_stage_vals<T>() * sizeof(T) + (size_t)c->max_cl_mol * 4;
     k_transform<T><<<c->n_tiles * c->tf_split, kTfWarps * 32, smem, c->stream>>>(c->tf_split, c->max_cl_mol, c->d_tile_row0, c->cap, c->capY, ptr, bl, outl, c->d_cci_ptr,
                                                          c->d_cci_row, c->d_cci_slot, (const T*)c->d_c_val[c->cur],
                                                          c->d_y_n, c->d_y_row, (const T*)c->d_y_val, (T*)out);
@@ -603,7 +734,8 @@ cudaError_t launch_transform_rot(Ctx* c) {
     c->n_launch += 3;
     cudaError_t e = ensure_attrs();
     if (e != cudaSuccess) return e;
-    if ((size_t)kTfWarps * kStage * 2 * kTileVals * c->tsize + (size_t)c->max_cl_mol * 4 > 200 * 1024)
+    if ((size_t)kTfWarps * (c->prec == SSCF_FP64 ? tf_stage_vals<double>() * 8 : tf_stage_vals<float>() * 4) +
+            (size_t)c->max_cl_mol * 4 > 200 * 1024)
         return cudaErrorInvalidValue;
     if (c->prec == SSCF_FP64) {
         e = transform_t<double>(c, c->d_rot_tp_ptr, c->d_rot_tp_b, c->d_rot_tp_out, c->d_F);

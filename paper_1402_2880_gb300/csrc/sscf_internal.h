@@ -93,6 +93,7 @@ struct Ctx {
     double e_prev = 0.0;
     bool have_e_prev = false;
     int last_sched_kind = 0;   // 0 none, 1 rotations, 2 combinations
+    double ortho_tol = 0.0;    // target of the orthonormalisation pass being launched
     int last_ortho_which = 0;
 
     // host copies of the structure

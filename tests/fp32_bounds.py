@@ -64,13 +64,13 @@ def combinations(C: np.ndarray, sigma: np.ndarray, st, which: str, tol: float, t
     d = np.sqrt(np.diag(sig))
     X = C.copy()
     E = np.zeros_like(C)
-    X[:, mos] = C[:, mos] / d[None, :]
-    E[:, mos] = 3 * U * np.abs(X[:, mos])
     sig_n = sig / np.outer(d, d)
     off = np.abs(sig_n - np.diag(np.diag(sig_n)))
     eta = float(off.max()) if off.size else 0.0
     if eta < tol:
         return X, E
+    X[:, mos] = C[:, mos] / d[None, :]
+    E[:, mos] = 3 * U * np.abs(X[:, mos])
     sel = sparse.overlap_mask(st, mos) & (np.abs(sig_n) >= 1e-3 * eta)
     np.fill_diagonal(sel, False)
     pa, pb = sparse.ortho_schedule(st, which, mos, sel)

@@ -206,8 +206,9 @@ def test_scc_steps_follow_oracle(n):
 
 @pytest.mark.parametrize("n", [32, 216])
 def test_mixed_scc_steps_follow_oracle(n):
-    """Four mixed-precision SCC iterations against the FP64 oracle from the
-    same start (the oracle orthonormalises to the same floored target)."""
+    """Four mixed-precision SCC iterations against the FP64 oracle started
+    from the GPU's own MOs and charges (the oracle orthonormalises to the same
+    floored target)."""
     from oracle import sparse as osp
     s = water(n)
     sc = osp.SparseSCF(s, P, ortho_tol_min=2.0 ** -19)
@@ -216,8 +217,9 @@ def test_mixed_scc_steps_follow_oracle(n):
     ctx.set_thresholds(eps, 1e-4, 1e-8)
     ctx.guess()
     ctx.orthonormalise(0)
-    ctx.reset_charges()
-    st = sc.start(eps)
+    E0 = ctx.reset_charges()
+    q0, dq0, Q0 = ctx.get_charges()
+    st = osp.SparseState(C=ctx.get_C(), dq_in=dq0.copy(), Q_in=Q0.copy(), q_prev=q0.copy(), E_prev=E0)
     for k in range(4):
         info = ctx.step()
         ref = sc.step(st, eps)
