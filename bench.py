@@ -555,7 +555,9 @@ def main():
                                                                    if flushed else
                                                                    "more than twice the 129 MB L2: no flush")),
                    "prep": {"eps": args.prep_eps, "ortho_passes": prep_passes, "eta": prep_eta},
-                   "autotune": {"transform_ctas_per_tile": sorted({r["tuned"] for r in runs if r["tuned"]})}},
+                   "autotune": {"transform_ctas_per_tile": sorted({r["tuned"] % 16 for r in runs if r["tuned"]}),
+                                "transform_regs_cut_for_4_ctas": sorted({r["tuned"] >= 16 for r in runs
+                                                                         if r["tuned"]})}},
         "scf_iter_per_s": n_gpus * K / (t_max / 1e3),
         "cluster_iter_per_s": (max(args.clusters, 1) if args.clusters > 0 else n_gpus) * K / (t_max / 1e3),
         "clocks": clocks,

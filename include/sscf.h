@@ -96,6 +96,31 @@ typedef struct {
     int iteration;
 } sscf_step_info;
 
+/* Grouping ----------------------------------------------------------------- */
+
+/* MO groups for any geometry: constrained k-means of the molecules (Section
+ * "Defining neighbouring lists of atoms and MOs"), run on the GPU. Every
+ * molecule is one unit, placed at its first (oxygen) atom. Centres start on a
+ * grid over the bounding box with at least ceil(n_mol / n_link) points (the
+ * axis with the largest spacing refined first, extents below 1 bohr counted as
+ * 1 bohr, points at lo + (2i + 1) L / 2g). Each iteration links every molecule
+ * to a centre, at most n_link per centre: molecules propose to centres in
+ * increasing (distance^2, centre index) and a centre keeps the n_link
+ * proposals with the smallest (distance^2, molecule index) (deferred
+ * acceptance; the result does not depend on any processing order, so the
+ * paper's shuffle of the centres is not needed). Then every centre with
+ * members moves to their centroid (summed in increasing molecule index),
+ * until the average move of the centres is below tol (bohr) or after max_iter
+ * iterations; the links of the last centres are returned. Groups are the
+ * centres holding molecules, numbered in centre order.
+ *   n_atoms, xyz: as sscf_system (host; molecules O, H, H)
+ *   n_link: 1 .. 8 molecules per group
+ *   group_of_mol: host, n_atoms / 3, written; n_groups_out, iters_out may be NULL
+ * Device memory comes from the allocator of sscf_set_allocator, if set, and is
+ * freed before the call returns. Errors: INVALID_ARG, NONFINITE, OOM, CUDA. */
+int sscf_group_molecules(int n_atoms, const double* xyz, int n_link, int max_iter, double tol,
+                         void* cuda_stream, int* group_of_mol, int* n_groups_out, int* iters_out);
+
 /* Context ---------------------------------------------------------------- */
 
 /* Builds the structure of step I (atom and molecule neighbour lists within
@@ -199,10 +224,12 @@ int sscf_step(sscf_ctx* ctx, sscf_step_info* info);
 /* Launch-shape autotuner (no counterpart in the paper): on the current state
  * it builds H and Y = H C as a step would, times the occupied-virtual transform
  * (three launches after one warm-up, CUDA events on the context's stream) for
- * 1, 2, 4 and 8 CTAs sharing each occupied tile's pairs, and keeps the fastest
- * for later steps. Results of later calls do not depend on the choice (each
- * pair is summed the same way). Drops a captured CUDA graph. tf_split_out
- * (host, may be NULL) receives the choice. Errors: STATE before sscf_guess, CUDA. */
+ * 1, 2, 4 and 8 CTAs sharing each occupied tile's pairs, each with two
+ * register budgets of the kernel (uncut, or cut for four resident CTAs per
+ * SM), and keeps the fastest for later steps. Results of later calls do not
+ * depend on the choice (each pair is summed the same way). Drops a captured
+ * CUDA graph. tf_split_out (host, may be NULL) receives the CTAs per tile plus
+ * 16 if the cut register budget won. Errors: STATE before sscf_guess, CUDA. */
 int sscf_autotune(sscf_ctx* ctx, int* tf_split_out);
 
 /* CUDA graphs: when enabled, sscf_step captures its device work (all kernel
@@ -222,6 +249,16 @@ int sscf_enable_graph(sscf_ctx* ctx, int enable);
  * context stays FP64 afterwards. Returns NOT_CONVERGED with the state kept
  * if max_scc is reached. */
 int sscf_run(sscf_ctx* ctx, sscf_step_info* info);
+
+/* The user stage of sscf_run from the MOs already in the context (a
+ * checkpoint restored with sscf_set_C_tiles, for example the converged MOs of
+ * a nearby geometry, Section "Summary and future work": the MOs of one
+ * geometry are a good start for the next): full orthonormalisation at eps,
+ * charges of those MOs as the SCC input, SCC iterations until dq_max <= dq_tol
+ * and |dE| <= e_tol, the final occupied orthonormalisation (in FP64, as
+ * sscf_run). Errors: STATE before any MOs were set, NOT_CONVERGED (state
+ * kept), and those of the steps. */
+int sscf_run_from_current(sscf_ctx* ctx, sscf_step_info* info);
 
 /* Storage precision of a live context (no counterpart in the paper, whose
  * orthonormalisation is FP64 and C^T H C FP32 throughout): SSCF_FP64 widens

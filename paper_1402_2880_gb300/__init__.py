@@ -11,5 +11,6 @@ from ._lib import (  # noqa: F401
     SSCF_ORTHO_OCC,
     Context,
     SscfError,
+    group_molecules,
     load,
 )

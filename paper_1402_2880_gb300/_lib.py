@@ -36,6 +36,7 @@ EXPORTED = [
     "sscf_enable_graph", "sscf_get_C_rows", "sscf_get_blocks",
     "sscf_get_C_cols", "sscf_get_F_entries", "sscf_get_C_tiles", "sscf_set_C_tiles", "sscf_autotune",
     "sscf_set_precision", "sscf_set_fock_blocks", "sscf_get_density_blocks", "sscf_get_overlap_dense",
+    "sscf_group_molecules", "sscf_run_from_current",
 ]
 
 
@@ -103,6 +104,7 @@ def load() -> ctypes.CDLL:
         "sscf_reset_charges": (c_int, [c_vp, P(c_double)]),
         "sscf_step": (c_int, [c_vp, P(StepInfo)]),
         "sscf_run": (c_int, [c_vp, P(StepInfo)]),
+        "sscf_run_from_current": (c_int, [c_vp, P(StepInfo)]),
         "sscf_get_C_dense": (c_int, [c_vp, P(c_double)]),
         "sscf_set_C_dense": (c_int, [c_vp, P(c_double)]),
         "sscf_get_H_dense": (c_int, [c_vp, P(c_double), P(c_double), P(c_double)]),
@@ -124,6 +126,8 @@ def load() -> ctypes.CDLL:
         "sscf_set_precision": (c_int, [c_vp, c_int]),
         "sscf_set_fock_blocks": (c_int, [c_vp, P(c_double)]),
         "sscf_get_overlap_dense": (c_int, [c_vp, P(c_double), P(c_int)]),
+        "sscf_group_molecules": (c_int, [c_int, P(c_double), c_int, c_int, c_double, c_vp, P(c_int), P(c_int),
+                                         P(c_int)]),
         "sscf_get_density_blocks": (c_int, [c_vp, P(c_double)]),
         "sscf_get_C_tiles": (c_int, [c_vp, P(ctypes.c_int32), P(ctypes.c_int32), P(c_double), P(c_i64)]),
         "sscf_set_C_tiles": (c_int, [c_vp, P(ctypes.c_int32), P(ctypes.c_int32), P(c_double)]),
@@ -178,6 +182,20 @@ def select_pairs_noalloc(f_dev_ptr: int, n: int, tau: float, k_max: int, keep_de
                                          ctypes.c_void_p(keep_dev_ptr), ctypes.byref(kept),
                                          ctypes.c_void_p(stream or 0)), "sscf_select_pairs_noalloc")
     return kept.value
+
+
+def group_molecules(xyz, n_link: int = 8, max_iter: int = 100, tol: float = 1e-3, stream: int | None = None):
+    """MO groups of a water-like system (atoms O, H, H per molecule) by the
+    GPU's constrained k-means: (group_of_mol, n_groups, iterations)."""
+    lib = load()
+    x = np.ascontiguousarray(xyz, dtype=np.float64).reshape(-1)
+    n_atoms = x.size // 3
+    groups = np.empty(n_atoms // 3, dtype=np.int32)
+    ng, it = ctypes.c_int(), ctypes.c_int()
+    _check(lib.sscf_group_molecules(int(n_atoms), _ptr(x), int(n_link), int(max_iter), float(tol),
+                                    ctypes.c_void_p(stream or 0), _ptr(groups, ctypes.c_int), ctypes.byref(ng),
+                                    ctypes.byref(it)), "sscf_group_molecules")
+    return groups, ng.value, it.value
 
 
 class Context:
@@ -280,6 +298,16 @@ class Context:
         s = self.lib.sscf_run(self.h, ctypes.byref(info))
         if not (s == SSCF_OK or (allow_not_converged and s == -6)):
             _check(s, "sscf_run")
+        d = info.as_dict()
+        d["converged"] = s == SSCF_OK
+        return d
+
+    def run_from_current(self, allow_not_converged: bool = False) -> dict:
+        """The user-threshold SCF from the MOs already in the context (a restart)."""
+        info = StepInfo()
+        s = self.lib.sscf_run_from_current(self.h, ctypes.byref(info))
+        if not (s == SSCF_OK or (allow_not_converged and s == -6)):
+            _check(s, "sscf_run_from_current")
         d = info.as_dict()
         d["converged"] = s == SSCF_OK
         return d

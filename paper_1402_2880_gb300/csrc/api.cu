@@ -496,6 +496,25 @@ int dev_alloc(Ctx* c, void** p, size_t bytes) {
     return SSCF_OK;
 }
 
+void* raw_alloc(size_t bytes) {
+    bytes = std::max<size_t>(bytes, 16);
+    void* q = nullptr;
+    if (g_alloc) return g_alloc(bytes, g_alloc_user);
+    if (cudaMalloc(&q, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return q;
+}
+
+void raw_free(void* p) {
+    if (!p) return;
+    if (g_free)
+        g_free(p, g_alloc_user);
+    else
+        cudaFree(p);
+}
+
 void dev_release(Ctx* c, void* p) {
     if (!p) return;
     for (size_t i = 0; i < c->allocations.size(); ++i)
@@ -1016,30 +1035,34 @@ int sscf_autotune(sscf_ctx* h, int* tf_split_out) {
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
     const int cand[] = {1, 2, 4, 8};
-    int best = c.tf_split;
+    int best = c.tf_split, best_regs = c.tf_regs;
     float best_ms = 1e30f;
     cudaError_t err = cudaSuccess;
-    for (int s : cand) {
-        c.tf_split = s;
-        err = launch_transform_rot(&c);   // warm-up
-        if (err != cudaSuccess) break;
-        err = cudaEventRecord(e0, c.stream);
-        for (int r = 0; r < 3 && err == cudaSuccess; ++r) err = launch_transform_rot(&c);
-        if (err == cudaSuccess) err = cudaEventRecord(e1, c.stream);
-        if (err == cudaSuccess) err = cudaEventSynchronize(e1);
-        float ms = 0.f;
-        if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
-        if (err != cudaSuccess) break;
-        if (ms < best_ms) {
-            best_ms = ms;
-            best = s;
+    for (int regs = 0; regs < 2 && err == cudaSuccess; ++regs)
+        for (int s : cand) {
+            c.tf_split = s;
+            c.tf_regs = regs;
+            err = launch_transform_rot(&c);   // warm-up
+            if (err != cudaSuccess) break;
+            err = cudaEventRecord(e0, c.stream);
+            for (int r = 0; r < 3 && err == cudaSuccess; ++r) err = launch_transform_rot(&c);
+            if (err == cudaSuccess) err = cudaEventRecord(e1, c.stream);
+            if (err == cudaSuccess) err = cudaEventSynchronize(e1);
+            float ms = 0.f;
+            if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
+            if (err != cudaSuccess) break;
+            if (ms < best_ms) {
+                best_ms = ms;
+                best = s;
+                best_regs = regs;
+            }
         }
-    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     c.tf_split = best;
+    c.tf_regs = best_regs;
     if (err != cudaSuccess) return SSCF_ERR_CUDA;
-    if (tf_split_out) *tf_split_out = best;
+    if (tf_split_out) *tf_split_out = best + 16 * best_regs;
     return SSCF_OK;
 }
 
@@ -1263,21 +1286,26 @@ int sscf_profile_read(sscf_ctx* h, int max_entries, char* names, double* ms, int
     return SSCF_OK;
 }
 
-int sscf_run(sscf_ctx* h, sscf_step_info* info) {
-    if (!h) return SSCF_ERR_INVALID_ARG;
+// The two-stage SCF (Section "Sparsity and numerical accuracy"), or, from the
+// MOs already in the context, the user stage alone.
+static int run_impl(sscf_ctx* h, sscf_step_info* info, bool from_current) {
     Ctx& c = h->c;
     const double eps_u = c.prm.eps, dq_u = c.prm.dq_tol, e_u = c.prm.e_tol;
-    CKS(sscf_guess(h));
+    if (from_current) {
+        if (!c.have_guess) return SSCF_ERR_STATE;
+    } else {
+        CKS(sscf_guess(h));
+    }
     struct Stage {
         double eps, dq, e;
     } stages[2] = {{1e-3, 1e-1, INFINITY}, {eps_u, dq_u, e_u}};
     sscf_step_info last{};
     bool converged = false;
-    for (int s = 0; s < 2; ++s) {
+    for (int s = from_current ? 1 : 0; s < 2; ++s) {
         if (c.prm.eps != stages[s].eps) drop_graph(c);
         c.prm.eps = stages[s].eps;
         CKS(sscf_orthonormalise(h, SSCF_ORTHO_ALL, 200, nullptr, nullptr));
-        if (s == 0) CKS(sscf_reset_charges(h, nullptr));
+        if (s == 0 || from_current) CKS(sscf_reset_charges(h, nullptr));
         converged = false;
         std::vector<double> e_prev(c.n_clusters), e_now(c.n_clusters), dq_now(c.n_clusters);
         CKS(sscf_get_cluster_results(h, e_prev.data(), nullptr, nullptr));
@@ -1312,6 +1340,16 @@ int sscf_run(sscf_ctx* h, sscf_step_info* info) {
     last.energy = E;
     if (info) *info = last;
     return converged ? SSCF_OK : SSCF_ERR_NOT_CONVERGED;
+}
+
+int sscf_run(sscf_ctx* h, sscf_step_info* info) {
+    if (!h) return SSCF_ERR_INVALID_ARG;
+    return run_impl(h, info, false);
+}
+
+int sscf_run_from_current(sscf_ctx* h, sscf_step_info* info) {
+    if (!h) return SSCF_ERR_INVALID_ARG;
+    return run_impl(h, info, true);
 }
 
 }  // extern "C"

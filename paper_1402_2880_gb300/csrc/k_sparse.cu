@@ -272,8 +272,9 @@ template <typename T> __host__ __device__ constexpr int tf_stage_vals() {
     return std::is_same<T, float>::value ? 2 * kTcRows * kTcStride : kStage * 2 * kTileVals;
 }
 
-template <typename T>
-__global__ void __launch_bounds__(kTfWarps * 32)
+// MINB: resident CTAs per SM the register budget is cut for (1: no cut)
+template <typename T, int MINB>
+__global__ void __launch_bounds__(kTfWarps * 32, MINB)
 k_transform(int n_split, int n_rows, const int* __restrict__ tile_row0, int cap, int capY, const int* __restrict__ tp_ptr,
             const int* __restrict__ tp_b,
             const int* __restrict__ tp_out, const int* __restrict__ cci_ptr, const int* __restrict__ cci_row,
@@ -318,43 +319,42 @@ k_transform(int n_split, int n_rows, const int* __restrict__ tile_row0, int cap,
                 }
             for (int k0 = 0; k0 < nb; k0 += 32) {
                 const int k = k0 + lane;
-                const int sl = k < nb ? slot_of[yr[k] - r0] : -1;
+                const int rr = k < nb ? yr[k] : 0;
+                const int sl = k < nb ? slot_of[rr - r0] : -1;
                 unsigned m = __ballot_sync(0xffffffffu, sl >= 0);
                 while (m) {
-                    int rows[kStage];
-                    int nst = 0;
+                    // up to kStage matched row blocks: their row, a's slot and b's position
+                    int nst = 0, rowv[kStage], ssv[kStage], kkv[kStage];
 #pragma unroll
                     for (int g = 0; g < kStage; ++g) {
-                        rows[g] = -1;
+                        const int src_lane = m ? __ffs(m) - 1 : 0;
                         if (m) {
-                            rows[g] = __ffs(m) - 1;
                             m &= m - 1;
                             ++nst;
                         }
-                    }
-                    // slot of a and position in b's list of every staged row block (warp-uniform)
-                    int ssv[kStage], kkv[kStage];
-#pragma unroll
-                    for (int g = 0; g < kStage; ++g) {
-                        const int src_lane = rows[g] < 0 ? 0 : rows[g];
+                        rowv[g] = __shfl_sync(0xffffffffu, rr, src_lane);
                         ssv[g] = __shfl_sync(0xffffffffu, sl, src_lane);
                         kkv[g] = k0 + src_lane;
                     }
-                    // stage: per row block 6 AO rows of C[r, a] and of Y[r, b], 16-byte pieces
-                    for (int v = lane; v < nst * 48; v += 32) {
-                        const int g = v / 48, rem = v - 48 * g, w = rem / 24, idx = rem - 24 * w;
-                        const int q = idx >> 2, part = idx & 3;
-                        int ss = 0, kk = 0;
+                    // stage: lane q*4 + part (< 24) copies 16 bytes of AO row q of
+                    // C[r, a] and of Y[r, b] for every staged row block, loads first
+                    if (lane < 24) {
+                        const int q = lane >> 2, part = lane & 3;
+                        float4 cv[kStage], yv[kStage];
 #pragma unroll
-                        for (int u = 0; u < kStage; ++u)
-                            if (u == g) {
-                                ss = ssv[u];
-                                kk = kkv[u];
+                        for (int g = 0; g < kStage; ++g)
+                            if (g < nst) {
+                                cv[g] = *((const float4*)(c_val + ((size_t)rowv[g] * cap + ssv[g]) * kTileVals +
+                                                          q * 16) + part);
+                                yv[g] = *((const float4*)(y_val + ((size_t)b * capY + kkv[g]) * kTileVals + q * 16) +
+                                          part);
                             }
-                        const float4* src =
-                            w == 0 ? (const float4*)(c_val + ((size_t)yr[kk] * cap + ss) * kTileVals + q * 16) + part
-                                   : (const float4*)(y_val + ((size_t)b * capY + kk) * kTileVals + q * 16) + part;
-                        *(float4*)((w == 0 ? bc : by) + (g * kAoPerMol + q) * kTcStride + 4 * part) = *src;
+#pragma unroll
+                        for (int g = 0; g < kStage; ++g)
+                            if (g < nst) {
+                                *(float4*)(bc + (g * kAoPerMol + q) * kTcStride + 4 * part) = cv[g];
+                                *(float4*)(by + (g * kAoPerMol + q) * kTcStride + 4 * part) = yv[g];
+                            }
                     }
                     __syncwarp();
                     const int nkr = nst * kAoPerMol;
@@ -683,7 +683,9 @@ static cudaError_t set_attrs() {
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(k_xc<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(k_transform<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    e = cudaFuncSetAttribute(k_transform<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k_transform<T, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(k_density<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     return e;
@@ -724,9 +726,10 @@ cudaError_t launch_xc(Ctx* c, bool use_h, int tile_lo, int tile_hi) {
 template <typename T>
 static cudaError_t transform_t(Ctx* c, const int* ptr, const int* bl, const int* outl, void* out) {
     const size_t smem = (size_t)kTfWarps * tf_stage_vals<T>() * sizeof(T) + (size_t)c->max_cl_mol * 4;
-    k_transform<T><<<c->n_tiles * c->tf_split, kTfWarps * 32, smem, c->stream>>>(c->tf_split, c->max_cl_mol, c->d_tile_row0, c->cap, c->capY, ptr, bl, outl, c->d_cci_ptr,
-                                                         c->d_cci_row, c->d_cci_slot, (const T*)c->d_c_val[c->cur],
-                                                         c->d_y_n, c->d_y_row, (const T*)c->d_y_val, (T*)out);
+    auto kern = c->tf_regs == 1 ? k_transform<T, 4> : k_transform<T, 1>;
+    kern<<<c->n_tiles * c->tf_split, kTfWarps * 32, smem, c->stream>>>(
+        c->tf_split, c->max_cl_mol, c->d_tile_row0, c->cap, c->capY, ptr, bl, outl, c->d_cci_ptr, c->d_cci_row,
+        c->d_cci_slot, (const T*)c->d_c_val[c->cur], c->d_y_n, c->d_y_row, (const T*)c->d_y_val, (T*)out);
     return cudaGetLastError();
 }
 

@@ -86,6 +86,7 @@ struct Ctx {
     int apply_variant = 0;   // 0 specialised sweep kernels where they apply, 1 generic only,
                              // 2 specialised with one CTA per block
     int tf_split = 4;        // CTAs sharing one occupied tile's pairs in the transform (sscf_autotune)
+    int tf_regs = 0;         // transform register budget: 0 uncut, 1 cut for 4 CTAs per SM (sscf_autotune)
     int n_sm = 152;          // multiprocessors of the context's device
     bool have_guess = false;
     int iteration = 0;
@@ -264,6 +265,8 @@ struct Ctx {
 // ---- memory -----------------------------------------------------------------
 int dev_alloc(Ctx* c, void** p, size_t bytes);
 void dev_release(Ctx* c, void* p);   // frees one allocation of dev_alloc
+void* raw_alloc(size_t bytes);       // device memory outside a context (the allocator hook if set); NULL on failure
+void raw_free(void* p);
 void dev_free_all(Ctx* c);
 
 template <typename P>

@@ -45,7 +45,7 @@ def test_full_block_kernel_matches_generic(n):
 
 
 def test_autotune_keeps_results():
-    """sscf_autotune only chooses a launch shape: the steps after it equal
+    """sscf_autotune only chooses a launch shape and a register budget: the steps after it equal
     the steps of an untuned context bit for bit."""
     s = water(216)
     runs = []
@@ -58,7 +58,7 @@ def test_autotune_keeps_results():
         ctx.reset_charges()
         ctx.step()
         if tune:
-            assert ctx.autotune() in (1, 2, 4, 8)
+            assert ctx.autotune() % 16 in (1, 2, 4, 8)
         infos = [ctx.step() for _ in range(2)]
         runs.append((ctx.get_C(), infos))
     assert np.array_equal(runs[0][0], runs[1][0])
