@@ -78,6 +78,18 @@ typedef struct {
                                 1: the generic kernel for every block,
                                 2: the specialised kernels with one CTA per block
                                 (all three give the same results; 1 and 2 are for tests) */
+    int closure_mode;        /* structural fill of a sweep (same results either way):
+                                0: once per sweep, every row given every tile its
+                                   units are connected to through the sweep's active
+                                   blocks (fewest launches; rows can grow to the whole
+                                   cluster, so cap_tiles defaults to that);
+                                1: once per colour, a row given the partner units of
+                                   that colour's active blocks for the units it holds
+                                   nonzero values in, and zero tiles dropped at the end
+                                   of the sweep (rows hold their real fill plus one
+                                   colour's insertions; for clusters whose dense rows
+                                   do not fit). In mode 1 a CAPACITY error leaves the
+                                   MOs partly swept: restart from a checkpoint. */
 } sscf_params;
 
 typedef struct {

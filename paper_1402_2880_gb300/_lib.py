@@ -59,7 +59,7 @@ class Params(ctypes.Structure):
                 ("e_tol", ctypes.c_double), ("group_cut", ctypes.c_double), ("rot_cap_factor", ctypes.c_double),
                 ("mix_beta", ctypes.c_double), ("max_scc", ctypes.c_int), ("precision", ctypes.c_int),
                 ("ortho_every", ctypes.c_int), ("cap_tiles", ctypes.c_int), ("cap_y", ctypes.c_int),
-                ("apply_variant", ctypes.c_int)]
+                ("apply_variant", ctypes.c_int), ("closure_mode", ctypes.c_int)]
 
 
 class StepInfo(ctypes.Structure):
@@ -154,7 +154,7 @@ def _check(status: int, what: str):
 
 
 def make_params(p: dict, precision: int = SSCF_FP64, ortho_every: int = 1, cap_tiles: int = 0, cap_y: int = 0,
-                apply_variant: int = 0) -> Params:
+                apply_variant: int = 0, closure_mode: int = 0) -> Params:
     q = Params()
     q.onsite[:] = [p["onsite_O_s"], p["onsite_O_p"], p["onsite_H_s"]]
     q.V0[:] = list(p["V0"])
@@ -165,7 +165,7 @@ def make_params(p: dict, precision: int = SSCF_FP64, ortho_every: int = 1, cap_t
     q.eps, q.dq_tol, q.e_tol = p["eps_mo"], p["dq_tol"], p["e_tol"]
     q.group_cut, q.rot_cap_factor, q.mix_beta = p["group_cut"], p["rot_cap_factor"], p["mix_beta"]
     q.max_scc, q.precision, q.ortho_every, q.cap_tiles = int(p["max_scc"]), precision, ortho_every, cap_tiles
-    q.cap_y, q.apply_variant = cap_y, apply_variant
+    q.cap_y, q.apply_variant, q.closure_mode = cap_y, apply_variant, closure_mode
     return q
 
 
@@ -203,7 +203,7 @@ class Context:
 
     def __init__(self, species, xyz, group_of_mol, params: dict, precision: int = SSCF_FP64,
                  stream: int | None = None, ortho_every: int = 1, cap_tiles: int = 0, cluster_of_mol=None,
-                 cap_y: int = 0, apply_variant: int = 0):
+                 cap_y: int = 0, apply_variant: int = 0, closure_mode: int = 0):
         self.lib = load()
         self._species = np.ascontiguousarray(species, dtype=np.int32)
         self._xyz = np.ascontiguousarray(xyz, dtype=np.float64).reshape(-1)
@@ -212,7 +212,7 @@ class Context:
         sysc = System(n_atoms=int(self._species.size), species=_ptr(self._species, ctypes.c_int),
                       xyz=_ptr(self._xyz), group_of_mol=_ptr(self._groups, ctypes.c_int),
                       cluster_of_mol=_ptr(self._clusters, ctypes.c_int))
-        self.params = make_params(params, precision, ortho_every, cap_tiles, cap_y, apply_variant)
+        self.params = make_params(params, precision, ortho_every, cap_tiles, cap_y, apply_variant, closure_mode)
         h = ctypes.c_void_p()
         _check(self.lib.sscf_create(ctypes.byref(sysc), ctypes.byref(self.params),
                                     ctypes.c_void_p(stream or 0), ctypes.byref(h)), "sscf_create")

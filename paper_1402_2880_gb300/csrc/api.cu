@@ -575,6 +575,7 @@ int sscf_create(const sscf_system* sys, const sscf_params* prm, void* cuda_strea
     if (sys->n_atoms <= 0 || sys->n_atoms % 3 != 0) return SSCF_ERR_INVALID_ARG;
     if (prm->precision != SSCF_FP64 && prm->precision != SSCF_MIXED) return SSCF_ERR_INVALID_ARG;
     if (prm->apply_variant < 0 || prm->apply_variant > 2) return SSCF_ERR_INVALID_ARG;
+    if (prm->closure_mode < 0 || prm->closure_mode > 1) return SSCF_ERR_INVALID_ARG;
     if (prm->cap_tiles < 0 || prm->cap_y < 0) return SSCF_ERR_INVALID_ARG;
     if (!(prm->r_cut > 0) || !(prm->r_decay > 0) || !(prm->group_cut > 0) || !(prm->eps >= 0) ||
         !(prm->U[0] > 0) || !(prm->U[1] > 0) || !(prm->rot_cap_factor > 0))
@@ -669,6 +670,7 @@ int sscf_create(const sscf_system* sys, const sscf_params* prm, void* cuda_strea
             c.n_sm = nsm;
     }
     c.apply_variant = prm->apply_variant;
+    c.per_colour = prm->closure_mode == 1;
     // uploads
 #define UP(d, v)                        \
     do {                                \
@@ -1002,9 +1004,17 @@ static int rotate_sweep_async(Ctx& c) {
     PK("xc_h", launch_xc(&c, true, 0, c.n_tiles));
     PK("transform_ov", launch_transform_rot(&c));
     PK("select_rot", launch_select_rot(&c));
-    PK("closure", launch_closure(&c, 0, 0));
-    PK("colindex", launch_colindex(&c));
-    PK("apply_rot", launch_apply(&c, 0, 0));
+    if (c.per_colour) {
+        for (int col = 0; col < c.n_colours; ++col) {
+            PK("closure", launch_closure(&c, 0, 0, col, col == 0));
+            PK("colindex", launch_colindex(&c));
+            PK("apply_rot", launch_apply(&c, 0, 0, col, col + 1));
+        }
+    } else {
+        PK("closure", launch_closure(&c, 0, 0));
+        PK("colindex", launch_colindex(&c));
+        PK("apply_rot", launch_apply(&c, 0, 0));
+    }
     PK("compact", launch_compact(&c));
     c.last_sched_kind = 1;
     return SSCF_OK;
@@ -1073,9 +1083,17 @@ static int ortho_pass_async(Ctx& c, int which, double tol) {
     PK("xc_s", launch_xc(&c, false, 0, w == 1 ? c.n_occ_tiles : c.n_tiles));
     PK("transform_ss", launch_transform_ortho(&c, w));
     PK("ortho_prepare", launch_ortho_prepare(&c, w, tol));
-    PK("closure", launch_closure(&c, 1, w));
-    PK("colindex", launch_colindex(&c));
-    PK("apply_ortho", launch_apply(&c, 1, w));
+    if (c.per_colour) {
+        for (int col = 0; col < c.n_colours; ++col) {
+            PK("closure", launch_closure(&c, 1, w, col, col == 0));
+            PK("colindex", launch_colindex(&c));
+            PK("apply_ortho", launch_apply(&c, 1, w, col, col + 1));
+        }
+    } else {
+        PK("closure", launch_closure(&c, 1, w));
+        PK("colindex", launch_colindex(&c));
+        PK("apply_ortho", launch_apply(&c, 1, w));
+    }
     PK("compact", launch_compact(&c));
     c.last_sched_kind = 2;
     c.last_ortho_which = w;

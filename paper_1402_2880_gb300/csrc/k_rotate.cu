@@ -381,7 +381,7 @@ __global__ void k_ortho_lists(int w, double tol, const int* __restrict__ oblk, c
 struct SweepArgs {
     int mode;        // 0 rotations (A occupied | B virtual), 1 combinations
     int which;       // combinations: 0 all MOs, 1 occupied MOs
-    int n_tiles, n_occ_tiles, n_groups, cap, n_blk, max_cl_groups;
+    int n_tiles, n_occ_tiles, n_groups, cap, n_blk, max_cl_groups, n_clusters;
     double trunc;
     float trunc_f;   // smallest float >= trunc: |x| < trunc <=> |x| < trunc_f for every float x
     const int* blk;          // blocks of the pass by colour
@@ -422,6 +422,8 @@ struct SweepArgs {
     int* out_tile;
     void* out_val;
     unsigned char* out_nz;   // flags of out: 0 = the tile is all zero (written by the closure, kept by the sweep)
+    const unsigned char* in_nz;   // closure: flags of the input (NULL: every listed tile may be nonzero)
+    int normalise_pass;      // closure in mode 1: divide by d_i (the first closure of a pass)
     unsigned* err;
 };
 
@@ -486,9 +488,58 @@ __global__ void __launch_bounds__(1024) k_closure_labels(SweepArgs a, int* __res
     for (int u = threadIdx.x; u < nu; u += blockDim.x) unit_lab[2 * g0 + u] = slab[u];
 }
 
+// Labels of one colour's closure. The active blocks of one colour form a
+// matching on the units (no unit in two of them), so the component of a unit
+// is the unit itself or the pair of one block: no transitive chain. In passes
+// over all MOs the occupied and virtual tiles of a group form one unit.
+// First every unit is its own label (the group's for virtual units in that
+// case), then every active block of the colour links its two units.
+__device__ __forceinline__ int cluster_of_group(const SweepArgs& a, int g) {
+    int lo = 0, hi = a.n_clusters - 1;   // the last cluster whose first group is <= g
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (a.cl_g0[mid] <= g) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+__global__ void k_colour_labels_init(SweepArgs a, int* __restrict__ unit_lab) {
+    const int gu = blockIdx.x * blockDim.x + threadIdx.x;   // 2 g0 + u over all clusters
+    if (gu >= 2 * a.n_groups) return;
+    const int cl = cluster_of_group(a, gu >> 1);
+    const int g0 = a.cl_g0[cl], ng = a.cl_g0[cl + 1] - g0;
+    const int u = gu - 2 * g0;
+    const bool groups = a.mode == 1 && a.which == 0;
+    unit_lab[gu] = groups && u >= ng ? u - ng : u;
+}
+
+__global__ void k_colour_labels_link(SweepArgs a, int p0, int n_blk, int* __restrict__ unit_lab) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n_blk) return;
+    const int e = a.blk[p0 + j];
+    if (a.pr_n[e] == 0) return;
+    const int A = a.gnb_row[e], B = a.gnb_col[e];
+    const int cl = cluster_of_group(a, A);
+    const int g0 = a.cl_g0[cl], ng = a.cl_g0[cl + 1] - g0;
+    const bool groups = a.mode == 1 && a.which == 0;
+    const int u = A - g0;
+    const int v = (a.mode == 0 ? ng : 0) + (B - g0);
+    if (groups) {
+        const int l = min(A, B) - g0;
+        unit_lab[2 * g0 + (A - g0)] = l;
+        unit_lab[2 * g0 + ng + (A - g0)] = l;
+        unit_lab[2 * g0 + (B - g0)] = l;
+        unit_lab[2 * g0 + ng + (B - g0)] = l;
+    } else {
+        unit_lab[2 * g0 + max(u, v)] = min(u, v);
+    }
+}
+
 template <typename T>
 __global__ void __launch_bounds__(256) k_closure(SweepArgs a) {
     extern __shared__ __align__(16) unsigned char smraw[];
+    if (*a.err & (kErrCapacity | kErrSortSize)) return;   // an earlier kernel of the step overflowed
     // everything a row block touches belongs to its own cluster: group bits and
     // the tile map are indexed inside the cluster's ranges
     const int r = blockIdx.x;
@@ -511,6 +562,8 @@ __global__ void __launch_bounds__(256) k_closure(SweepArgs a) {
     for (int s = threadIdx.x; s < n0; s += blockDim.x) {
         const int t = a.in_tile[(size_t)r * a.cap + s];
         map[lt(t)] = (short)s;
+        // a tile flagged all-zero holds its place but cannot create fill
+        if (a.in_nz && !a.in_nz[(size_t)r * a.cap + s]) continue;
         const int g = a.tile_group[t] - g0;
         const unsigned bit = 1u << (g & 31);
         if (a.mode == 1 && a.which == 0) {
@@ -574,11 +627,13 @@ __global__ void __launch_bounds__(256) k_closure(SweepArgs a) {
     __syncthreads();
     // tiles copied from the input survived the last compaction (or come from the
     // guess or a restart) and may be nonzero; inserted tiles are zero
-    for (int s = threadIdx.x; s < n1; s += blockDim.x)
-        a.out_nz[(size_t)r * a.cap + s] = map[lt(a.out_tile[(size_t)r * a.cap + s])] >= 0 ? 1 : 0;
+    for (int s = threadIdx.x; s < n1; s += blockDim.x) {
+        const int os = map[lt(a.out_tile[(size_t)r * a.cap + s])];
+        a.out_nz[(size_t)r * a.cap + s] = os < 0 ? 0 : (a.in_nz ? a.in_nz[(size_t)r * a.cap + os] : 1);
+    }
     const T* inv = (const T*)a.in_val;
     T* outv = (T*)a.out_val;
-    const bool normalise = a.mode == 1 && !(a.cl_eta[k] < a.tol);
+    const bool normalise = a.mode == 1 && a.normalise_pass && !(a.cl_eta[k] < a.tol);
     for (int idx = threadIdx.x; idx < n1 * kTileVals; idx += blockDim.x) {
         const int s = idx / kTileVals, e = idx % kTileVals, col = e & 15;
         const int t = a.out_tile[(size_t)r * a.cap + s];
@@ -669,6 +724,7 @@ __global__ void __launch_bounds__(apply_threads<T>()) k_apply_colour(SweepArgs a
     __shared__ int s_slot[CH][NT];
     // side A occupies panel tiles [0, kSideA), side B [kSideA, NT)
     constexpr int kSideA = MODE == 0 ? 2 : NT / 2;
+    if (*a.err & (kErrCapacity | kErrSortSize)) return;
     const int e = a.blk[p0 + blockIdx.y];
     const int np = a.pr_n[e];
     if (np == 0) return;
@@ -932,6 +988,7 @@ __global__ void __launch_bounds__(kFullThreads, kFullMinCtas[MODE]) k_apply_full
     float* panel = (float*)smraw;                           // [NB B columns][kFullNR rows]
     Coef* coef = (Coef*)(panel + NB * kFullNR);             // [32 levels][32 i]
     __shared__ unsigned s_mask[32];
+    if (*a.err & (kErrCapacity | kErrSortSize)) return;
     const int e = a.blk[p0 + blockIdx.y];
     const int np = a.pr_n[e];
     if (np == 0) return;
@@ -1299,6 +1356,9 @@ static void fill_args(Ctx* c, SweepArgs& a, int mode, int which) {
     a.n_occ_tiles = c->n_occ_tiles;
     a.n_groups = c->n_groups;
     a.max_cl_groups = c->max_cl_groups;
+    a.n_clusters = c->n_clusters;
+    a.in_nz = nullptr;
+    a.normalise_pass = 1;
     a.mol_cluster = c->d_mol_cluster;
     a.cl_g0 = c->d_cl_g0;
     a.cl_ot0 = c->d_cl_ot0;
@@ -1337,8 +1397,11 @@ static void fill_args(Ctx* c, SweepArgs& a, int mode, int which) {
     a.err = &c->d_sc->err;
 }
 
+// colour < 0: the closure of a whole sweep (components over all active
+// blocks); colour >= 0: the closure of that colour alone, on the flags of the
+// current buffer unless it is the first of the pass.
 template <typename T>
-static cudaError_t closure_t(Ctx* c, int mode, int which) {
+static cudaError_t closure_t(Ctx* c, int mode, int which, int colour, bool first) {
     SweepArgs a;
     fill_args<T>(c, a, mode, which);
     const int in = c->cur, out = 1 - c->cur;
@@ -1350,22 +1413,31 @@ static cudaError_t closure_t(Ctx* c, int mode, int which) {
     a.out_val = c->d_c_val[out];
     a.out_nz = c->d_c_nz[out];
     a.unit_lab = c->d_unit_lab;
+    a.in_nz = first ? nullptr : c->d_c_nz[in];
+    a.normalise_pass = first ? 1 : 0;
     const size_t smem = closure_smem_bytes(c);
     if (smem > (size_t)kMaxDynSmem) return cudaErrorInvalidValue;
     cudaError_t e = cudaFuncSetAttribute(k_closure<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    const size_t lsmem = (size_t)2 * c->max_cl_groups * 4;
-    if (lsmem > (size_t)kMaxDynSmem) return cudaErrorInvalidValue;
-    e = cudaFuncSetAttribute(k_closure_labels, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lsmem);
-    if (e != cudaSuccess) return e;
-    k_closure_labels<<<c->n_clusters, 1024, lsmem, c->stream>>>(a, c->d_unit_lab);
+    if (colour < 0) {
+        const size_t lsmem = (size_t)2 * c->max_cl_groups * 4;
+        if (lsmem > (size_t)kMaxDynSmem) return cudaErrorInvalidValue;
+        e = cudaFuncSetAttribute(k_closure_labels, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lsmem);
+        if (e != cudaSuccess) return e;
+        k_closure_labels<<<c->n_clusters, 1024, lsmem, c->stream>>>(a, c->d_unit_lab);
+    } else {
+        const std::vector<int>& ptr = mode == 0 ? c->h_colour_ptr : c->h_ocolour_ptr;
+        const int nb = ptr[colour + 1] - ptr[colour];
+        k_colour_labels_init<<<(2 * c->n_groups + 255) / 256, 256, 0, c->stream>>>(a, c->d_unit_lab);
+        if (nb > 0) k_colour_labels_link<<<(nb + 127) / 128, 128, 0, c->stream>>>(a, ptr[colour], nb, c->d_unit_lab);
+    }
     k_closure<T><<<c->n_mol, 256, smem, c->stream>>>(a);
     c->cur = out;
     return cudaGetLastError();
 }
 
 template <typename T, int MODE, int NT, int PCAP>
-static cudaError_t apply_mode_t(Ctx* c, int which) {
+static cudaError_t apply_mode_t(Ctx* c, int which, int col_lo, int col_hi) {
     SweepArgs a;
     fill_args<T>(c, a, MODE, which);
     a.in_nt = a.out_nt = c->d_c_nt[c->cur];
@@ -1397,7 +1469,7 @@ static cudaError_t apply_mode_t(Ctx* c, int which) {
         full_occ[MODE] = std::max(full_occ[MODE], 1);
     }
     const int chunks = (c->n_mol + kFullCH - 1) / kFullCH;
-    for (int col = 0; col < c->n_colours; ++col) {
+    for (int col = col_lo; col < col_hi; ++col) {
         const int nf = full ? nfull[col] : 0;
         if (nf > 0) {
             // variant 2: one CTA takes all row chunks of its block (the longest
@@ -1422,19 +1494,22 @@ static cudaError_t apply_mode_t(Ctx* c, int which) {
 // tiles, 32 x 16 pairs; occupied passes 2 + 2 tiles, 32 x 32 pairs; passes over
 // all MOs 3 + 3 tiles, 48 x 48 pairs
 template <typename T>
-static cudaError_t apply_t(Ctx* c, int mode, int which) {
-    if (mode == 0) return apply_mode_t<T, 0, 3, kRotCap>(c, which);
-    if (which == 1) return apply_mode_t<T, 1, 4, 32 * 32>(c, which);
-    return apply_mode_t<T, 1, 6, kOrthoCap>(c, which);
+static cudaError_t apply_t(Ctx* c, int mode, int which, int col_lo, int col_hi) {
+    if (mode == 0) return apply_mode_t<T, 0, 3, kRotCap>(c, which, col_lo, col_hi);
+    if (which == 1) return apply_mode_t<T, 1, 4, 32 * 32>(c, which, col_lo, col_hi);
+    return apply_mode_t<T, 1, 6, kOrthoCap>(c, which, col_lo, col_hi);
 }
 
-cudaError_t launch_closure(Ctx* c, int mode, int which) {
-    c->n_launch += 2;
-    return c->prec == SSCF_FP64 ? closure_t<double>(c, mode, which) : closure_t<float>(c, mode, which);
+cudaError_t launch_closure(Ctx* c, int mode, int which, int colour, bool first) {
+    c->n_launch += colour < 0 ? 2 : 3;
+    return c->prec == SSCF_FP64 ? closure_t<double>(c, mode, which, colour, first)
+                                : closure_t<float>(c, mode, which, colour, first);
 }
 
-cudaError_t launch_apply(Ctx* c, int mode, int which) {
-    return c->prec == SSCF_FP64 ? apply_t<double>(c, mode, which) : apply_t<float>(c, mode, which);
+cudaError_t launch_apply(Ctx* c, int mode, int which, int col_lo, int col_hi) {
+    if (col_hi < 0) col_hi = c->n_colours;
+    return c->prec == SSCF_FP64 ? apply_t<double>(c, mode, which, col_lo, col_hi)
+                                : apply_t<float>(c, mode, which, col_lo, col_hi);
 }
 
 cudaError_t launch_compact(Ctx* c) {

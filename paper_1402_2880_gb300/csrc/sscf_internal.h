@@ -83,6 +83,7 @@ struct Ctx {
     int n_gnb = 0;       // group-graph entries (directed, including (A, A))
     int cap = 0;         // tiles per row block of C
     int capY = 0;        // row blocks per tile of Y
+    bool per_colour = false; // closure per colour (bounded fill) instead of per sweep
     int apply_variant = 0;   // 0 specialised sweep kernels where they apply, 1 generic only,
                              // 2 specialised with one CTA per block
     int tf_split = 4;        // CTAs sharing one occupied tile's pairs in the transform (sscf_autotune)
@@ -289,9 +290,11 @@ cudaError_t launch_density(Ctx* c, double* P_out = nullptr);   // P blocks (n_mp
 // schedules and sweeps
 cudaError_t launch_select_rot(Ctx* c);
 cudaError_t launch_ortho_prepare(Ctx* c, int which, double tol);
-cudaError_t launch_closure(Ctx* c, int mode, int which); // structural fill; cur <- other
+// structural fill of a whole sweep (colour < 0) or of one colour; cur <- other
+cudaError_t launch_closure(Ctx* c, int mode, int which, int colour = -1, bool first = true);
 size_t closure_smem_bytes(const Ctx* c);
-cudaError_t launch_apply(Ctx* c, int mode, int which);   // mode 0 rotations, 1 combinations; in place
+// mode 0 rotations, 1 combinations, colours [col_lo, col_hi) (col_hi < 0: all); in place
+cudaError_t launch_apply(Ctx* c, int mode, int which, int col_lo = 0, int col_hi = -1);
 cudaError_t launch_compact(Ctx* c);                      // drop all-zero tiles; cur <- other
 // charges
 cudaError_t launch_charges_finish(Ctx* c, bool mix);
