@@ -248,8 +248,16 @@ int sscf_autotune(sscf_ctx* ctx, int* tf_split_out);
  * launches of one SCC iteration) into a graph at the first call and replays
  * it afterwards: one launch per iteration. The graph is rebuilt when eps
  * changes or the C buffers swapped parity (sscf_set_C_dense, sscf_guess).
- * Needs a non-NULL stream (SSCF_ERR_INVALID_ARG otherwise); per-launcher
- * profiling does not see replayed launches. */
+ * sscf_run and sscf_run_from_current then run each SCC stage as one graph
+ * launch: a conditional while node repeats one captured SCC iteration and a
+ * one-block kernel that applies the stage's convergence test on the device
+ * (every cluster's max |q - q_prev| and |E - E_prev|), so no host round trip
+ * separates the iterations; it stops at convergence, at max_scc iterations or
+ * when a kernel reports an error, with the same results as the host loop.
+ * (A stage whose captured iteration would not end in the C buffer it starts
+ * from, possible with closure_mode 1, runs the host loop instead.) Needs a
+ * non-NULL stream (SSCF_ERR_INVALID_ARG otherwise); per-launcher profiling
+ * does not see replayed launches. */
 int sscf_enable_graph(sscf_ctx* ctx, int enable);
 
 /* Loose stage (eps 1e-3, dq 1e-1), full orthonormalisation, user stage until

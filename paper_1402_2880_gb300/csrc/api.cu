@@ -448,6 +448,38 @@ __global__ void k_convert(size_t n, const S* __restrict__ in, D* __restrict__ ou
         out[i] = (D)in[i];
 }
 
+// Convergence test of one SCC iteration inside a graph-resident stage (the
+// test of sscf_run's host loop: every cluster with max |q - q_prev| <= dq_tol
+// and |E - E_prev| <= e_tol). Sets the condition of the stage's while node:
+// another iteration unless all clusters converged, the iteration limit is
+// reached, a kernel of the iteration set an error bit, or an energy is not
+// finite. One block.
+__global__ void k_scc_loop_test(int n_clusters, const double* __restrict__ cl_E, double* __restrict__ cl_Eprev,
+                                const double* __restrict__ cl_dq, double dq_tol, double e_tol, int max_iter,
+                                int* __restrict__ loop, const unsigned* __restrict__ err,
+                                cudaGraphConditionalHandle handle) {
+    __shared__ int s_ok, s_bad;
+    if (threadIdx.x == 0) {
+        s_ok = 1;
+        s_bad = 0;
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < n_clusters; k += blockDim.x) {
+        const double e = cl_E[k];
+        if (!isfinite(e)) s_bad = 1;
+        if (!(cl_dq[k] <= dq_tol && fabs(e - cl_Eprev[k]) <= e_tol)) s_ok = 0;
+        cl_Eprev[k] = e;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const int it = loop[0] + 1;
+        loop[0] = it;
+        loop[1] = s_ok;
+        const bool stop = s_ok || it >= max_iter || s_bad || (*err & (kErrCapacity | kErrSortSize | kErrNonFinite));
+        cudaGraphSetConditional(handle, stop ? 0u : 1u);
+    }
+}
+
 void drop_graph(Ctx& c) {
     if (c.graph_exec) cudaGraphExecDestroy(c.graph_exec);
     if (c.graph) cudaGraphDestroy(c.graph);
@@ -836,6 +868,8 @@ int sscf_create(const sscf_system* sys, const sscf_params* prm, void* cuda_strea
     AL(c.d_cl_hist, (size_t)c.n_clusters * 256 * 8);
     AL(c.d_cl_eta, (size_t)c.n_clusters * 8);
     AL(c.d_cl_dq, (size_t)c.n_clusters * 8);
+    AL(c.d_cl_Eprev, (size_t)c.n_clusters * 8);
+    AL(c.d_loop, 16);
     AL(c.d_grad, (size_t)c.n_atoms * 3 * 8);
     AL(c.d_par, 8 * 8);
     AL(c.d_gmol, (size_t)c.n_mol * 9 * 8);
@@ -1304,6 +1338,108 @@ int sscf_profile_read(sscf_ctx* h, int max_entries, char* names, double* ms, int
     return SSCF_OK;
 }
 
+// One SCC stage as a single graph launch: an init part (iteration counter,
+// previous energies) and a while node whose body is one SCC iteration
+// (step_device, captured) followed by k_scc_loop_test. No host round trip
+// between iterations. Returns STATE, with nothing launched, when the captured
+// iteration does not end in the C buffer it starts from (it could not repeat).
+static int stage_in_graph(Ctx& c, double dq_tol, double e_tol, int max_iter, bool* converged,
+                          sscf_step_info* last) {
+    if (!c.stream) return SSCF_ERR_STATE;
+    drop_graph(c);
+    const bool prof = c.prof;
+    c.prof = false;
+    const int cur0 = c.cur;
+    const long long l0 = c.n_launch;
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaGraphConditionalHandle handle;
+    int st = SSCF_OK;
+    long long body_launches = 0;
+    auto fail = [&](int s_) {
+        cudaGetLastError();
+        if (exec) cudaGraphExecDestroy(exec);
+        if (g) cudaGraphDestroy(g);
+        c.prof = prof;
+        c.cur = cur0;
+        c.n_launch = l0;
+        return s_;
+    };
+    if (cudaGraphCreate(&g, 0) != cudaSuccess) return fail(SSCF_ERR_CUDA);
+    if (cudaGraphConditionalHandleCreate(&handle, g, 1, cudaGraphCondAssignDefault) != cudaSuccess)
+        return fail(SSCF_ERR_CUDA);
+    // init: counter and convergence flag to zero, previous energies = current ones
+    if (cudaStreamBeginCaptureToGraph(c.stream, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) !=
+        cudaSuccess)
+        return fail(SSCF_ERR_CUDA);
+    cudaError_t e1 = cudaMemsetAsync(c.d_loop, 0, 16, c.stream);
+    cudaError_t e2 = cudaMemcpyAsync(c.d_cl_Eprev, c.d_cl_E, (size_t)c.n_clusters * 8, cudaMemcpyDeviceToDevice,
+                                     c.stream);
+    cudaGraph_t gg = nullptr;
+    if (cudaStreamEndCapture(c.stream, &gg) != cudaSuccess || e1 != cudaSuccess || e2 != cudaSuccess)
+        return fail(SSCF_ERR_CUDA);
+    size_t n_nodes = 0;
+    if (cudaGraphGetNodes(g, nullptr, &n_nodes) != cudaSuccess) return fail(SSCF_ERR_CUDA);
+    std::vector<cudaGraphNode_t> deps(n_nodes);
+    if (n_nodes && cudaGraphGetNodes(g, deps.data(), &n_nodes) != cudaSuccess) return fail(SSCF_ERR_CUDA);
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = handle;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t cond;
+    if (cudaGraphAddNode(&cond, g, deps.data(), nullptr, n_nodes, &cp) != cudaSuccess) return fail(SSCF_ERR_CUDA);
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    // body: one SCC iteration and the convergence test
+    if (cudaStreamBeginCaptureToGraph(c.stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) !=
+        cudaSuccess)
+        return fail(SSCF_ERR_CUDA);
+    st = step_device(c);
+    if (st == SSCF_OK) {
+        k_scc_loop_test<<<1, 256, 0, c.stream>>>(c.n_clusters, c.d_cl_E, c.d_cl_Eprev, c.d_cl_dq, dq_tol, e_tol,
+                                                 max_iter, c.d_loop, &c.d_sc->err, handle);
+        c.n_launch += 1;
+        if (cudaGetLastError() != cudaSuccess) st = SSCF_ERR_CUDA;
+    }
+    cudaGraph_t gb = nullptr;
+    const cudaError_t ce = cudaStreamEndCapture(c.stream, &gb);
+    body_launches = c.n_launch - l0;
+    if (st != SSCF_OK) return fail(st);
+    if (ce != cudaSuccess) return fail(SSCF_ERR_CUDA);
+    if (c.cur != cur0) return fail(SSCF_ERR_STATE);
+    if (cudaGraphInstantiate(&exec, g, 0) != cudaSuccess) return fail(SSCF_ERR_CUDA);
+    if (cudaGraphLaunch(exec, c.stream) != cudaSuccess) return fail(SSCF_ERR_CUDA);
+    int loop[2] = {0, 0};
+    if (cudaMemcpyAsync(loop, c.d_loop, 8, cudaMemcpyDeviceToHost, c.stream) != cudaSuccess) return fail(SSCF_ERR_CUDA);
+    st = sync_scalars(c);
+    cudaGraphExecDestroy(exec);
+    cudaGraphDestroy(g);
+    c.prof = prof;
+    c.n_launch = l0 + (long long)loop[0] * body_launches;
+    if (st != SSCF_OK) return st;
+    c.iteration += loop[0];
+    if (last) {
+        last->energy = c.h_sc->energy;
+        last->dq_max = c.h_sc->dq_max;
+        last->dE = c.have_e_prev ? c.h_sc->energy - c.e_prev : c.h_sc->energy;
+        last->max_fov = c.h_sc->max_fov;
+        last->eta = c.h_sc->eta;
+        last->n_rot = (int64_t)c.h_sc->n_rot;
+        last->n_combo = (int64_t)c.h_sc->n_combo;
+        last->nnz_c = (int64_t)c.h_sc->tiles[0] * kTileVals;
+        last->nnz_occ = (int64_t)c.h_sc->tiles[1] * kTileVals;
+        last->launches = (int64_t)body_launches;
+        last->upd_rot = (int64_t)c.h_sc->upd[0];
+        last->upd_combo = (int64_t)c.h_sc->upd[1];
+        last->iteration = c.iteration;
+    }
+    if (!std::isfinite(c.h_sc->energy)) return SSCF_ERR_NONFINITE;
+    c.e_prev = c.h_sc->energy;
+    c.have_e_prev = true;
+    *converged = loop[1] != 0;
+    return SSCF_OK;
+}
+
 // The two-stage SCF (Section "Sparsity and numerical accuracy"), or, from the
 // MOs already in the context, the user stage alone.
 static int run_impl(sscf_ctx* h, sscf_step_info* info, bool from_current) {
@@ -1325,6 +1461,14 @@ static int run_impl(sscf_ctx* h, sscf_step_info* info, bool from_current) {
         CKS(sscf_orthonormalise(h, SSCF_ORTHO_ALL, 200, nullptr, nullptr));
         if (s == 0 || from_current) CKS(sscf_reset_charges(h, nullptr));
         converged = false;
+        if (c.use_graph && c.prm.max_scc > 0) {
+            int st = stage_in_graph(c, stages[s].dq, stages[s].e, c.prm.max_scc, &converged, &last);
+            if (st != SSCF_ERR_STATE) {
+                CKS(st);
+                continue;
+            }
+            // the captured iteration does not end in the buffer it starts from: host loop
+        }
         std::vector<double> e_prev(c.n_clusters), e_now(c.n_clusters), dq_now(c.n_clusters);
         CKS(sscf_get_cluster_results(h, e_prev.data(), nullptr, nullptr));
         for (int it = 0; it < c.prm.max_scc; ++it) {

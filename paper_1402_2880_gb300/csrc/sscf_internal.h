@@ -165,6 +165,8 @@ struct Ctx {
     double* d_cl_eta = nullptr;       // per-cluster largest normalised overlap
     double* d_cl_E = nullptr;         // per-cluster energy of the last charge update
     double* d_cl_dq = nullptr;        // per-cluster max |q - q_prev|
+    double* d_cl_Eprev = nullptr;     // per-cluster energy of the previous iteration (graph-resident stages)
+    int* d_loop = nullptr;            // graph-resident stage: iterations, converged
     int* d_tile_kind = nullptr;
     int* d_tile_loc0 = nullptr;
     int* d_tile_nmo = nullptr;

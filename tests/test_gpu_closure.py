@@ -43,17 +43,35 @@ def test_per_colour_closure_gives_the_same_mos(n, precision):
 
 
 def test_per_colour_closure_fits_where_the_sweep_closure_overflows():
+    """4096 molecules after the guess and the loose full orthonormalisation
+    (eps 1e-3, the bench's input state), then one SCC iteration: the MOs are
+    local, so rows hold a few hundred of the 1536 tiles. With 640 tiles per row
+    the per-sweep closure overflows on the first pass (it gives a row every
+    tile of the cluster); the per-colour closure runs, and its checkpoint of C
+    equals the dense-row reference tile for tile."""
     from paper_1402_2880_gb300 import SscfError
-    n = 512
-    ref_ctx, ref = _trajectory(n, 1, 0)                       # dense rows: reference
-    nt, _, _ = ref_ctx.get_C_tiles()
-    n_tiles = ref_ctx.n_tiles
-    cap = int(0.75 * n_tiles)
-    print(f"{n_tiles} tiles, rows hold at most {nt.max()} after three iterations; capacity {cap}")
-    assert nt.max() < cap                                      # the real fill fits
+    s = water(4096)
+
+    def prep(closure_mode, cap_tiles):
+        ctx = context(s, precision=1, closure_mode=closure_mode, cap_tiles=cap_tiles)
+        ctx.set_thresholds(1e-3, 1e-2, 1e-8)
+        ctx.guess()
+        ctx.orthonormalise(0)
+        first = ctx.get_C_tiles()
+        ctx.set_thresholds(1e-5, 1e-4, 1e-6)
+        ctx.reset_charges()
+        info = ctx.step()
+        return first, ctx.get_C_tiles(), info
+
+    ref_first, ref_after, ref_info = prep(0, 0)
+    cap = 640
+    print(f"rows hold at most {ref_first[0].max()} tiles after the orthonormalisation and "
+          f"{ref_after[0].max()} after one iteration; capacity {cap}")
+    assert ref_after[0].max() < cap
     with pytest.raises(SscfError) as e:
-        _trajectory(n, 1, 0, cap_tiles=cap)
-    assert e.value.status == -5                                # the sweep closure needs whole rows
-    _, got = _trajectory(n, 1, 1, cap_tiles=cap)
-    assert np.array_equal(got[1], ref[1]) and np.array_equal(got[-1], ref[-1])
-    assert got[3:-1] == ref[3:-1]
+        prep(0, cap)
+    assert e.value.status == -5
+    got_first, got_after, got_info = prep(1, cap)
+    for a, b in ((got_first, ref_first), (got_after, ref_after)):
+        assert all(np.array_equal(x, y) for x, y in zip(a, b))
+    assert got_info["energy"] == ref_info["energy"]
