@@ -14,6 +14,8 @@ dense       oracle A: the definition of the result, an SCC loop around a dense
             generalised eigensolve (the paper's LAPACK DSYGVD reference).
 sparse      oracle B: the paper's sparse SCF algorithm (steps I-V) written out
             step by step on dense FP64 arrays holding explicit zeros.
+adjoint     analytic SCC energy gradients (forces, Slater-Koster prefactors).
+kmeans      the constrained k-means grouping of the molecules into MO groups.
 
 Parity status: every function is pinned by tests in ``tests/test_oracle_*``;
 none is "parity unpinned".

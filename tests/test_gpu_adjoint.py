@@ -60,12 +60,27 @@ def test_autograd_function_backward():
     assert np.allclose(xyz.grad.numpy(), 2.0 * g, rtol=0, atol=1e-9 * np.abs(g).max())
     assert np.allclose(V0.grad.numpy(), 2.0 * gp[:4], rtol=1e-9, atol=0)
     assert np.allclose(S0.grad.numpy(), 2.0 * gp[4:], rtol=1e-9, atol=0)
-    # one finite-difference check through the function itself (FP64 path)
+    # finite differences through the function itself (FP64 path) on a smooth,
+    # tightly converged energy: cut-off 1e-9, charges to 1e-10 e, energy to
+    # 1e-12 Ha (an SCF error of 1e-12 Ha is 5e-9 Ha/bohr at h = 1e-4 bohr);
+    # no atom pair of the displaced atom within 2h of the 10-bohr hard cut-off
+    from paper_1402_2880_gb300 import Context
+    from synth import default_params
+    pt = default_params(eps_mo=1e-9, dq_tol=1e-10, e_tol=1e-12)
+    x0 = xyz.detach()
     h = 1e-4
-    k = int(np.argmax(np.abs(g[:, 0])))
-    xp = xyz.detach().clone()
-    xm = xyz.detach().clone()
-    xp[k, 0] += h
-    xm[k, 0] -= h
-    fd = (scc_energy(s, xp, V0.detach(), S0.detach(), P) - scc_energy(s, xm, V0.detach(), S0.detach(), P)) / (2 * h)
-    assert abs(float(fd) - g[k, 0]) < 1e-4 * np.abs(g).max()
+    d = np.sqrt(((s.xyz[:, None, :] - s.xyz[None, :, :]) ** 2).sum(-1))
+    c = Context.from_system(s, pt)
+    assert c.run()["converged"]
+    g_t, _ = c.gradients()
+    c.close()
+    gmax = np.abs(g_t).max()
+    for k in np.argsort(-np.abs(g_t).ravel())[:3]:
+        a, ax = divmod(int(k), 3)
+        assert np.abs(d[a] - 10.0).min() > 2 * h
+        xp = x0.clone()
+        xm = x0.clone()
+        xp[a, ax] += h
+        xm[a, ax] -= h
+        fd = (scc_energy(s, xp, V0.detach(), S0.detach(), pt) - scc_energy(s, xm, V0.detach(), S0.detach(), pt)) / (2 * h)
+        assert abs(float(fd) - g_t[a, ax]) < 1e-5 * gmax
