@@ -308,16 +308,13 @@ k_transform(int n_split, int n_rows, const int* __restrict__ tile_row0, int cap,
             const int b = tp_b[p];
             const int nb = y_n[b];
             const int* yr = y_row + (size_t)b * capY;
-            // hi*hi and the two correction terms in separate fragments: two
-            // independent MMA chains per n-tile instead of one chain of three
-            float acc[2][4], cor[2][4];
+            float acc[2][4];
             double accd[2][4];
 #pragma unroll
             for (int h = 0; h < 2; ++h)
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
                     acc[h][q] = 0.f;
-                    cor[h][q] = 0.f;
                     accd[h][q] = 0.0;
                 }
             for (int k0 = 0; k0 < nb; k0 += 32) {
@@ -374,9 +371,9 @@ k_transform(int n_split, int n_rows, const int* __restrict__ tile_row0, int cap,
                             uint32_t bh[2], bl[2];
                             split_tf32(va ? by[ka * kTcStride + 8 * h + gq] : 0.f, bh[0], bl[0]);
                             split_tf32(vb ? by[kb * kTcStride + 8 * h + gq] : 0.f, bh[1], bl[1]);
-                            mma_tf32(cor[h], al, bh);
+                            mma_tf32(acc[h], al, bh);
+                            mma_tf32(acc[h], ah, bl);
                             mma_tf32(acc[h], ah, bh);
-                            mma_tf32(cor[h], ah, bl);
                         }
                     }
                     __syncwarp();
@@ -385,9 +382,8 @@ k_transform(int n_split, int n_rows, const int* __restrict__ tile_row0, int cap,
                 for (int h = 0; h < 2; ++h)
 #pragma unroll
                     for (int q = 0; q < 4; ++q) {
-                        accd[h][q] += (double)cor[h][q] + (double)acc[h][q];
+                        accd[h][q] += (double)acc[h][q];
                         acc[h][q] = 0.f;
-                        cor[h][q] = 0.f;
                     }
             }
             T* o = out + (size_t)tp_out[p] * 256;
