@@ -74,6 +74,7 @@ def parse():
     ap.add_argument("--no-autotune", action="store_true", help="keep the default transform launch shape")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 path on the same checkpoint")
     ap.add_argument("--no-accuracy", action="store_true", help="skip the converged 32-molecule accuracy check")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (very large single clusters)")
     return ap.parse_args()
 
 
@@ -384,20 +385,22 @@ def main():
         ctx.profile(False)
         # end to end through the C-ABI: the checkpoint (C and charges) in from
         # page-locked host memory, one SCC iteration, the charges out, every step
-        pin_ck = tuple(pinned_copy(a) for a in ck[0])
-        pin_q = [pinned_copy(a) for a in ck[1]]
-        pin_out = [pinned_copy(a) for a in ck[1]]
-        h2d = sum(a.nbytes for a in pin_ck) + sum(a.nbytes for a in pin_q)
-        d2h = sum(a.nbytes for a in pin_out)
-        torch.cuda.synchronize(dev)
-        t0 = time.perf_counter()
-        for _ in range(K):
-            ctx.set_C_tiles(*pin_ck)
-            ctx.set_charges(*pin_q)
-            ctx.step()
-            ctx.get_charges(out=pin_out)
-        torch.cuda.synchronize(dev)
-        e2e_dt = time.perf_counter() - t0
+        e2e_dt, h2d, d2h = None, 0, 0
+        if not args.no_e2e:
+            pin_ck = tuple(pinned_copy(a) for a in ck[0])
+            pin_q = [pinned_copy(a) for a in ck[1]]
+            pin_out = [pinned_copy(a) for a in ck[1]]
+            h2d = sum(a.nbytes for a in pin_ck) + sum(a.nbytes for a in pin_q)
+            d2h = sum(a.nbytes for a in pin_out)
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            for _ in range(K):
+                ctx.set_C_tiles(*pin_ck)
+                ctx.set_charges(*pin_q)
+                ctx.step()
+                ctx.get_charges(out=pin_out)
+            torch.cuda.synchronize(dev)
+            e2e_dt = time.perf_counter() - t0
         n_mo = ctx.n_mo
         ctx.close()
         fp64 = None
@@ -435,8 +438,10 @@ def main():
     ms = sum(r["ms"] for r in runs)
     job_atoms, t_max = aggregate(n_atoms_local, ms, dist, dev)
     value = job_atoms * K / (t_max / 1e3)
-    _, e2e_t = aggregate(n_atoms_local, sum(r["e2e_dt"] for r in runs), dist, dev)
-    e2e_value = job_atoms * K / e2e_t
+    e2e_value = None
+    if not args.no_e2e:
+        _, e2e_t = aggregate(n_atoms_local, sum(r["e2e_dt"] for r in runs), dist, dev)
+        e2e_value = job_atoms * K / e2e_t
     infos = [inf for r in runs for inf in r["infos"]]
     prof = {}
     for r in runs:
@@ -565,7 +570,7 @@ def main():
         "scf_iter_per_s": n_gpus * K / (t_max / 1e3),
         "cluster_iter_per_s": (max(args.clusters, 1) if args.clusters > 0 else n_gpus) * K / (t_max / 1e3),
         "clocks": clocks,
-        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": sum(r["h2d"] for r in runs),
+        "e2e": None if e2e_value is None else {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": sum(r["h2d"] for r in runs),
                 "d2h_bytes_per_step": sum(r["d2h"] for r in runs),
                 "what": "per step through the C-ABI: sscf_set_C_tiles (checkpoint of C, FP64 tiles) and "
                         "sscf_set_charges from page-locked host memory, sscf_step, sscf_get_charges"},

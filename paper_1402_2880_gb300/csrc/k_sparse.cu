@@ -118,18 +118,25 @@ __global__ void k_xc(int tile_lo, int n_rows, int cap, int capY, const int* __re
                      int* __restrict__ y_row, T* __restrict__ y_val, unsigned* __restrict__ err) {
     // row maps are local to the tile's cluster: row r -> r - r0, n_rows = largest cluster
     extern __shared__ int sm[];
-    int* rowpos = sm;                             // n_rows: index into the tile's column list or -1
-    unsigned* bits = (unsigned*)(sm + n_rows);    // n_rows bits
-    int* wpre = (int*)(bits + (n_rows + 31) / 32);  // prefix of popcounts per word
+    const int nw = (n_rows + 31) / 32;
+    unsigned* bits = (unsigned*)sm;               // n_rows bits
+    int* wpre = (int*)(bits + nw);                // prefix of popcounts per word
+    short* rowpos = (short*)(wpre + nw);          // n_rows: index into the tile's column list or -1
     __shared__ int s_total;
     const int t = tile_lo + blockIdx.x;
     const int r0 = tile_row0[t];
     const int lo = cci_ptr[t], nc = cci_ptr[t + 1] - lo;
-    const int nw = (n_rows + 31) / 32;
+    if (nc > 32767) {   // the 16-bit row map cannot index this column
+        if (threadIdx.x == 0) {
+            atomicOr(err, kErrCapacity);
+            y_n[t] = 0;
+        }
+        return;
+    }
     for (int i = threadIdx.x; i < n_rows; i += blockDim.x) rowpos[i] = -1;
     for (int i = threadIdx.x; i < nw; i += blockDim.x) bits[i] = 0u;
     __syncthreads();
-    for (int k = threadIdx.x; k < nc; k += blockDim.x) rowpos[cci_row[lo + k] - r0] = k;
+    for (int k = threadIdx.x; k < nc; k += blockDim.x) rowpos[cci_row[lo + k] - r0] = (short)k;
     for (int k = threadIdx.x; k < nc; k += blockDim.x) {
         int r = cci_row[lo + k];
         for (int e = mp_ptr[r]; e < mp_ptr[r + 1]; ++e) {
@@ -282,7 +289,7 @@ k_transform(int n_split, int n_rows, const int* __restrict__ tile_row0, int cap,
             const int* __restrict__ y_row, const T* __restrict__ y_val, T* __restrict__ out) {
     extern __shared__ __align__(16) unsigned char sraw[];
     T* stage = (T*)sraw;                                        // [warps][tf_stage_vals]
-    int* slot_of = (int*)(stage + (size_t)kTfWarps * tf_stage_vals<T>());   // n_rows (cluster-local)
+    short* slot_of = (short*)(stage + (size_t)kTfWarps * tf_stage_vals<T>());   // n_rows (cluster-local)
     // CTA (a, s) takes the pairs of tile a with index = s (mod n_split)
     const int a = blockIdx.x / n_split, split = blockIdx.x % n_split;
     const int p0 = tp_ptr[a], p1 = tp_ptr[a + 1];
@@ -291,7 +298,7 @@ k_transform(int n_split, int n_rows, const int* __restrict__ tile_row0, int cap,
     const int lo = cci_ptr[a], nc = cci_ptr[a + 1] - lo;
     for (int i = threadIdx.x; i < n_rows; i += blockDim.x) slot_of[i] = -1;
     __syncthreads();
-    for (int k = threadIdx.x; k < nc; k += blockDim.x) slot_of[cci_row[lo + k] - r0] = cci_slot[lo + k];
+    for (int k = threadIdx.x; k < nc; k += blockDim.x) slot_of[cci_row[lo + k] - r0] = (short)cci_slot[lo + k];
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     T* buf = stage + (size_t)warp * tf_stage_vals<T>();
@@ -708,7 +715,7 @@ cudaError_t launch_xc(Ctx* c, bool use_h, int tile_lo, int tile_hi) {
     const int n = tile_hi - tile_lo;
     if (n <= 0) return cudaSuccess;
     const int nr = c->max_cl_mol;
-    const size_t smem = (size_t)nr * 4 + (size_t)((nr + 31) / 32) * 8 + 64;
+    const size_t smem = (size_t)((nr + 31) / 32) * 8 + (size_t)nr * 2 + 64;
     if (smem > 200 * 1024) return cudaErrorInvalidValue;
     if (c->prec == SSCF_FP64)
         k_xc<double><<<n, 256, smem, c->stream>>>(tile_lo, nr, c->cap, c->capY, c->d_tile_row0, c->d_cci_ptr, c->d_cci_row,
@@ -725,7 +732,7 @@ cudaError_t launch_xc(Ctx* c, bool use_h, int tile_lo, int tile_hi) {
 
 template <typename T>
 static cudaError_t transform_t(Ctx* c, const int* ptr, const int* bl, const int* outl, void* out) {
-    const size_t smem = (size_t)kTfWarps * tf_stage_vals<T>() * sizeof(T) + (size_t)c->max_cl_mol * 4;
+    const size_t smem = (size_t)kTfWarps * tf_stage_vals<T>() * sizeof(T) + (size_t)c->max_cl_mol * 2;
     auto kern = c->tf_regs == 1 ? k_transform<T, 4> : k_transform<T, 1>;
     kern<<<c->n_tiles * c->tf_split, kTfWarps * 32, smem, c->stream>>>(
         c->tf_split, c->max_cl_mol, c->d_tile_row0, c->cap, c->capY, ptr, bl, outl, c->d_cci_ptr, c->d_cci_row,
@@ -738,7 +745,7 @@ cudaError_t launch_transform_rot(Ctx* c) {
     cudaError_t e = ensure_attrs();
     if (e != cudaSuccess) return e;
     if ((size_t)kTfWarps * (c->prec == SSCF_FP64 ? tf_stage_vals<double>() * 8 : tf_stage_vals<float>() * 4) +
-            (size_t)c->max_cl_mol * 4 > 200 * 1024)
+            (size_t)c->max_cl_mol * 2 > 200 * 1024)
         return cudaErrorInvalidValue;
     if (c->prec == SSCF_FP64) {
         e = transform_t<double>(c, c->d_rot_tp_ptr, c->d_rot_tp_b, c->d_rot_tp_out, c->d_F);

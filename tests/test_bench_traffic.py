@@ -77,3 +77,13 @@ def test_shared_header_edit_drops_the_record(tmp_path):
         assert key in src
         return src.replace(key, "constexpr int kOrthoCap = 48 * 49;", 1)
     assert bench.measured_traffic("apply_ortho", WORKLOAD, root=_tree(tmp_path, edit_header=edit)) is None
+
+
+def test_committed_record_is_well_formed():
+    rec = os.path.join(ROOT, "profiles", "dram_traffic_apply_ortho_water4096_mixed.md")
+    with open(rec) as f:
+        line = next(l for l in f if l.startswith("traffic: apply_ortho "))
+    fields = dict(kv.split("=", 1) for kv in line.split()[2:])
+    assert float(fields["bytes_per_call"]) > 1e9
+    assert len(fields["kernel_code_sha256"]) == 64
+    assert fields["workload"].startswith("n_mol:4096,eps:1e-05,precision:mixed,clusters:1,replayed_iteration:")
