@@ -68,8 +68,8 @@ def parse():
                     help="batched workload: clusters per context, contexts run one after another (0: all in one)")
     ap.add_argument("--cap-tiles", type=int, default=0, help="tiles per row of C (0: the largest cluster's tiles)")
     ap.add_argument("--cap-y", type=int, default=0, help="row blocks per tile of Y (0: the largest cluster)")
-    ap.add_argument("--closure-mode", type=int, default=0, choices=[0, 1],
-                    help="0: structural fill once per sweep; 1: once per colour (bounded rows, large clusters)")
+    ap.add_argument("--closure-mode", type=int, default=0,
+                    help="0: structural fill once per sweep; k >= 1: once per k colours (bounded rows, large clusters)")
     ap.add_argument("--graph", action="store_true", help="replay each SCC iteration as one CUDA graph")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default transform launch shape")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 path on the same checkpoint")
@@ -555,7 +555,7 @@ def main():
                                + (", CUDA graph" if args.graph else ""),
                    "n_mol": n_mol_local, "eps": args.eps, "precision": args.precision, "clusters": max(args.clusters, 1),
                    "replayed_iteration": args.warmup + 1,
-                   "closure": "per colour" if args.closure_mode == 1 else "per sweep",
+                   "closure": f"per {args.closure_mode} colours" if args.closure_mode > 0 else "per sweep",
                    "cap_tiles": args.cap_tiles, "cap_y": args.cap_y,
                    "nnz_per_mo": nnz_c / n_mo_local,
                    "parallelism": ("clusters sharded over ranks" if args.clusters > 0 else "replicas")

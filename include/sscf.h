@@ -83,13 +83,16 @@ typedef struct {
                                    units are connected to through the sweep's active
                                    blocks (fewest launches; rows can grow to the whole
                                    cluster, so cap_tiles defaults to that);
-                                1: once per colour, a row given the partner units of
-                                   that colour's active blocks for the units it holds
-                                   nonzero values in, and zero tiles dropped at the end
-                                   of the sweep (rows hold their real fill plus one
-                                   colour's insertions; for clusters whose dense rows
-                                   do not fit). In mode 1 a CAPACITY error leaves the
-                                   MOs partly swept: restart from a checkpoint. */
+                                k >= 1: once per window of k colours, a row given the
+                                   tiles its units are connected to through the active
+                                   blocks of those colours, counting only the units it
+                                   holds nonzero values in; zero tiles are dropped at
+                                   the end of the sweep. Rows hold their real fill plus
+                                   one window's insertions (k = 1: the partner of each
+                                   unit), for clusters whose dense rows do not fit; a
+                                   larger k copies C fewer times. With k >= 1 a
+                                   CAPACITY error leaves the MOs partly swept: restart
+                                   from a checkpoint. */
 } sscf_params;
 
 typedef struct {

@@ -607,7 +607,7 @@ int sscf_create(const sscf_system* sys, const sscf_params* prm, void* cuda_strea
     if (sys->n_atoms <= 0 || sys->n_atoms % 3 != 0) return SSCF_ERR_INVALID_ARG;
     if (prm->precision != SSCF_FP64 && prm->precision != SSCF_MIXED) return SSCF_ERR_INVALID_ARG;
     if (prm->apply_variant < 0 || prm->apply_variant > 2) return SSCF_ERR_INVALID_ARG;
-    if (prm->closure_mode < 0 || prm->closure_mode > 1) return SSCF_ERR_INVALID_ARG;
+    if (prm->closure_mode < 0) return SSCF_ERR_INVALID_ARG;
     if (prm->cap_tiles < 0 || prm->cap_y < 0) return SSCF_ERR_INVALID_ARG;
     if (!(prm->r_cut > 0) || !(prm->r_decay > 0) || !(prm->group_cut > 0) || !(prm->eps >= 0) ||
         !(prm->U[0] > 0) || !(prm->U[1] > 0) || !(prm->rot_cap_factor > 0))
@@ -702,7 +702,7 @@ int sscf_create(const sscf_system* sys, const sscf_params* prm, void* cuda_strea
             c.n_sm = nsm;
     }
     c.apply_variant = prm->apply_variant;
-    c.per_colour = prm->closure_mode == 1;
+    c.closure_window = prm->closure_mode;
     // uploads
 #define UP(d, v)                        \
     do {                                \
@@ -794,6 +794,7 @@ int sscf_create(const sscf_system* sys, const sscf_params* prm, void* cuda_strea
     UP(c.d_gnb_ptr, c.h_gnb_ptr);
     UP(c.d_gnb_row, c.h_gnb_row);
     UP(c.d_gnb_col, c.h_gnb_col);
+    UP(c.d_gnb_colour, c.h_gnb_colour);
     UP(c.d_colour_ptr, c.h_colour_ptr);
     UP(c.d_colour_blk, c.h_colour_blk);
     UP(c.d_ocolour_ptr, c.h_ocolour_ptr);
@@ -1038,11 +1039,12 @@ static int rotate_sweep_async(Ctx& c) {
     PK("xc_h", launch_xc(&c, true, 0, c.n_tiles));
     PK("transform_ov", launch_transform_rot(&c));
     PK("select_rot", launch_select_rot(&c));
-    if (c.per_colour) {
-        for (int col = 0; col < c.n_colours; ++col) {
-            PK("closure", launch_closure(&c, 0, 0, col, col == 0));
+    if (c.closure_window > 0) {
+        for (int col = 0; col < c.n_colours; col += c.closure_window) {
+            const int hi = std::min(col + c.closure_window, c.n_colours);
+            PK("closure", launch_closure(&c, 0, 0, col, hi, col == 0));
             PK("colindex", launch_colindex(&c));
-            PK("apply_rot", launch_apply(&c, 0, 0, col, col + 1));
+            PK("apply_rot", launch_apply(&c, 0, 0, col, hi));
         }
     } else {
         PK("closure", launch_closure(&c, 0, 0));
@@ -1117,11 +1119,12 @@ static int ortho_pass_async(Ctx& c, int which, double tol) {
     PK("xc_s", launch_xc(&c, false, 0, w == 1 ? c.n_occ_tiles : c.n_tiles));
     PK("transform_ss", launch_transform_ortho(&c, w));
     PK("ortho_prepare", launch_ortho_prepare(&c, w, tol));
-    if (c.per_colour) {
-        for (int col = 0; col < c.n_colours; ++col) {
-            PK("closure", launch_closure(&c, 1, w, col, col == 0));
+    if (c.closure_window > 0) {
+        for (int col = 0; col < c.n_colours; col += c.closure_window) {
+            const int hi = std::min(col + c.closure_window, c.n_colours);
+            PK("closure", launch_closure(&c, 1, w, col, hi, col == 0));
             PK("colindex", launch_colindex(&c));
-            PK("apply_ortho", launch_apply(&c, 1, w, col, col + 1));
+            PK("apply_ortho", launch_apply(&c, 1, w, col, hi));
         }
     } else {
         PK("closure", launch_closure(&c, 1, w));

@@ -392,6 +392,8 @@ struct SweepArgs {
     const int* clblk_ptr;    // closure: blocks of the pass by cluster
     const int* clblk;
     const int* unit_lab;     // closure: component label of every unit (2 per group), cluster-local
+    const int* gnb_colour;   // closure: colour of every block ...
+    int col_lo, col_hi;      // ... only blocks of colours [col_lo, col_hi) link units
     const int* gnb_row;
     const int* gnb_col;
     const int* group_nmol;
@@ -468,6 +470,8 @@ __global__ void __launch_bounds__(1024) k_closure_labels(SweepArgs a, int* __res
             if (j < jb1 - jb0) {
                 const int e = a.clblk[jb0 + j];
                 if (a.pr_n[e] == 0) continue;
+                const int col = a.gnb_colour[e];
+                if (col < a.col_lo || col >= a.col_hi) continue;
                 u = a.gnb_row[e] - g0;
                 v = a.mode == 0 ? ng + (a.gnb_col[e] - g0) : a.gnb_col[e] - g0;
             } else {
@@ -486,54 +490,6 @@ __global__ void __launch_bounds__(1024) k_closure_labels(SweepArgs a, int* __res
         if (!any) break;
     }
     for (int u = threadIdx.x; u < nu; u += blockDim.x) unit_lab[2 * g0 + u] = slab[u];
-}
-
-// Labels of one colour's closure. The active blocks of one colour form a
-// matching on the units (no unit in two of them), so the component of a unit
-// is the unit itself or the pair of one block: no transitive chain. In passes
-// over all MOs the occupied and virtual tiles of a group form one unit.
-// First every unit is its own label (the group's for virtual units in that
-// case), then every active block of the colour links its two units.
-__device__ __forceinline__ int cluster_of_group(const SweepArgs& a, int g) {
-    int lo = 0, hi = a.n_clusters - 1;   // the last cluster whose first group is <= g
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (a.cl_g0[mid] <= g) lo = mid;
-        else hi = mid - 1;
-    }
-    return lo;
-}
-
-__global__ void k_colour_labels_init(SweepArgs a, int* __restrict__ unit_lab) {
-    const int gu = blockIdx.x * blockDim.x + threadIdx.x;   // 2 g0 + u over all clusters
-    if (gu >= 2 * a.n_groups) return;
-    const int cl = cluster_of_group(a, gu >> 1);
-    const int g0 = a.cl_g0[cl], ng = a.cl_g0[cl + 1] - g0;
-    const int u = gu - 2 * g0;
-    const bool groups = a.mode == 1 && a.which == 0;
-    unit_lab[gu] = groups && u >= ng ? u - ng : u;
-}
-
-__global__ void k_colour_labels_link(SweepArgs a, int p0, int n_blk, int* __restrict__ unit_lab) {
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= n_blk) return;
-    const int e = a.blk[p0 + j];
-    if (a.pr_n[e] == 0) return;
-    const int A = a.gnb_row[e], B = a.gnb_col[e];
-    const int cl = cluster_of_group(a, A);
-    const int g0 = a.cl_g0[cl], ng = a.cl_g0[cl + 1] - g0;
-    const bool groups = a.mode == 1 && a.which == 0;
-    const int u = A - g0;
-    const int v = (a.mode == 0 ? ng : 0) + (B - g0);
-    if (groups) {
-        const int l = min(A, B) - g0;
-        unit_lab[2 * g0 + (A - g0)] = l;
-        unit_lab[2 * g0 + ng + (A - g0)] = l;
-        unit_lab[2 * g0 + (B - g0)] = l;
-        unit_lab[2 * g0 + ng + (B - g0)] = l;
-    } else {
-        unit_lab[2 * g0 + max(u, v)] = min(u, v);
-    }
 }
 
 template <typename T>
@@ -937,6 +893,7 @@ __global__ void __launch_bounds__(apply_threads<T>()) k_apply_colour(SweepArgs a
 // that the level loop runs in full warps.
 constexpr int kFullDenseMin = 12;                 // pairs in a level from which MODE 1 runs it without branches
 constexpr int kFullBatch = 8;                     // slots loaded ahead in a branch-free level (multiple of 4)
+constexpr int kFusedBatch = 4;                    // slots loaded ahead when two levels share a pass (even)
 constexpr int kFullMinCtas[2] = {6, 5};          // resident CTAs per SM the register budget is cut for
 constexpr int kFullWaves[2] = {16, 4};            // resident-CTA multiples per launch (fewer: more row chunks per CTA to collect from)
 constexpr int kFullCH = 32;                       // row blocks per CTA
@@ -947,9 +904,9 @@ template <> struct FullShape<0> {   // rotations: B = one virtual tile, coeffici
     static constexpr int nb = 16;
     using Coef = float4;
 };
-template <> struct FullShape<1> {   // combinations: B = two occupied tiles, coefficient -c
+template <> struct FullShape<1> {   // combinations: B = two occupied tiles, (-c, truncation threshold)
     static constexpr int nb = 32;
-    using Coef = float;
+    using Coef = float2;
 };
 template <int MODE> __host__ __device__ constexpr size_t full_apply_smem() {
     return (size_t)FullShape<MODE>::nb * kFullNR * 4 + (size_t)32 * 32 * sizeof(typename FullShape<MODE>::Coef);
@@ -1006,7 +963,7 @@ __global__ void __launch_bounds__(kFullThreads, kFullMinCtas[MODE]) k_apply_full
     }
     for (int i = threadIdx.x; i < 32 * 32; i += blockDim.x) {
         if constexpr (MODE == 0) coef[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-        else coef[i] = 0.f;
+        else coef[i] = make_float2(0.f, 0.f);
     }
     if (threadIdx.x < 32) s_mask[threadIdx.x] = 0u;
     __syncthreads();
@@ -1020,7 +977,7 @@ __global__ void __launch_bounds__(kFullThreads, kFullMinCtas[MODE]) k_apply_full
             const float sn = cs[2 * q + 1];
             coef[lv * 32 + il] = make_float4(c, c, sn, sn);
         } else {
-            coef[lv * 32 + il] = -c;   // a slot without a pair keeps c = 0
+            coef[lv * 32 + il] = make_float2(-c, a.trunc_f);   // a slot without a pair keeps (0, 0)
         }
         atomicOr(&s_mask[lv], 1u << il);
     }
@@ -1092,26 +1049,81 @@ __global__ void __launch_bounds__(kFullThreads, kFullMinCtas[MODE]) k_apply_full
             const Coef* cl = coef + lv * 32;
             if constexpr (MODE == 1) {
                 if (__popc(m) >= kFullDenseMin) {
-                    // most slots of the level hold a pair: run all 32 without a
-                    // branch; an empty slot (c = 0, threshold 0) leaves both of
-                    // its values as they are. kFullBatch loads in flight before
-                    // their updates.
+                    // Most slots of the level hold a pair: all 32 run without a
+                    // branch; a slot without a pair (c = 0, threshold 0) leaves
+                    // both of its values as they are. Each slot reads (c, t) from
+                    // the table, two slots per 16-byte load.
+                    if (lv + 1 < 32 && __popc(s_mask[lv + 1]) >= kFullDenseMin) {
+                        // Two dense levels in one pass over the slots. Slot i of
+                        // level lv+1 pairs x_i with y_(lv+1-i), the value slot i-1
+                        // has just updated at level lv: it stays in a register for
+                        // its second update and is stored once. Slot 0's level-lv+1
+                        // partner, y_(lv+1), is last updated at level lv by slot 31,
+                        // so that update comes after the pass. Every value sees its
+                        // updates in level order, as in the one-level pass.
+                        const float4* ca4 = (const float4*)cl;
+                        const float4* cb4 = (const float4*)(cl + 32);
+                        float2 yprev = make_float2(0.f, 0.f);
+#pragma unroll
+                        for (int i0 = 0; i0 < 32; i0 += kFusedBatch) {
+                            float2 yv[kFusedBatch];
+                            float4 ca[kFusedBatch / 2], cb[kFusedBatch / 2];
+#pragma unroll
+                            for (int u = 0; u < kFusedBatch / 2; ++u) {
+                                ca[u] = ca4[i0 / 2 + u];
+                                cb[u] = cb4[i0 / 2 + u];
+                            }
+#pragma unroll
+                            for (int u = 0; u < kFusedBatch; ++u)
+                                yv[u] = *(const float2*)(ps + ((lv - i0 - u) & 31) * kFullNR);
+#pragma unroll
+                            for (int u = 0; u < kFusedBatch; ++u) {
+                                const int i = i0 + u;
+                                const float c0 = (u & 1) ? ca[u / 2].z : ca[u / 2].x;
+                                const float t0 = (u & 1) ? ca[u / 2].w : ca[u / 2].y;
+                                const float2 cc0 = make_float2(c0, c0);
+                                const float2 xn = __ffma2_rn(cc0, yv[u], x[i]);
+                                const float2 yn = __ffma2_rn(cc0, x[i], yv[u]);
+                                x[i] = trunc2_mul(xn, t0);
+                                const float2 ynew = trunc2_mul(yn, t0);
+                                if (i > 0) {
+                                    const float c1 = (u & 1) ? cb[u / 2].z : cb[u / 2].x;
+                                    const float t1 = (u & 1) ? cb[u / 2].w : cb[u / 2].y;
+                                    const float2 cc1 = make_float2(c1, c1);
+                                    const float2 xn1 = __ffma2_rn(cc1, yprev, x[i]);
+                                    const float2 yn1 = __ffma2_rn(cc1, x[i], yprev);
+                                    x[i] = trunc2_mul(xn1, t1);
+                                    *(float2*)(ps + ((lv + 1 - i) & 31) * kFullNR) = trunc2_mul(yn1, t1);
+                                }
+                                yprev = ynew;
+                            }
+                        }
+                        {   // slot 0 of level lv+1 with y_(lv+1)
+                            const float2 ct = cl[32];
+                            const float2 cc1 = make_float2(ct.x, ct.x);
+                            const float2 xn1 = __ffma2_rn(cc1, yprev, x[0]);
+                            const float2 yn1 = __ffma2_rn(cc1, x[0], yprev);
+                            x[0] = trunc2_mul(xn1, ct.y);
+                            *(float2*)(ps + ((lv + 1) & 31) * kFullNR) = trunc2_mul(yn1, ct.y);
+                        }
+                        ++lv;
+                        continue;
+                    }
                     const float4* cl4 = (const float4*)cl;
 #pragma unroll
                     for (int i0 = 0; i0 < 32; i0 += kFullBatch) {
                         float2 yv[kFullBatch];
-                        float4 cv[kFullBatch / 4];
+                        float4 cv[kFullBatch / 2];
 #pragma unroll
-                        for (int u = 0; u < kFullBatch / 4; ++u) cv[u] = cl4[i0 / 4 + u];
+                        for (int u = 0; u < kFullBatch / 2; ++u) cv[u] = cl4[i0 / 2 + u];
 #pragma unroll
                         for (int u = 0; u < kFullBatch; ++u)
                             yv[u] = *(const float2*)(ps + ((lv - i0 - u) & 31) * kFullNR);
 #pragma unroll
                         for (int u = 0; u < kFullBatch; ++u) {
                             const int i = i0 + u;
-                            const float4 c4 = cv[u / 4];
-                            const float c = (u & 3) == 0 ? c4.x : (u & 3) == 1 ? c4.y : (u & 3) == 2 ? c4.z : c4.w;
-                            const float t = (m >> i & 1u) ? tf : 0.f;
+                            const float c = (u & 1) ? cv[u / 2].z : cv[u / 2].x;
+                            const float t = (u & 1) ? cv[u / 2].w : cv[u / 2].y;
                             const float2 cc = make_float2(c, c);
                             const float2 xn = __ffma2_rn(cc, yv[u], x[i]);
                             const float2 yn = __ffma2_rn(cc, x[i], yv[u]);
@@ -1134,7 +1146,7 @@ __global__ void __launch_bounds__(kFullThreads, kFullMinCtas[MODE]) k_apply_full
                         xn = __ffma2_rn(cc, x[i], __fmul2_rn(make_float2(c4.z, c4.w), y));
                         yn = __ffma2_rn(cc, y, __fmul2_rn(make_float2(-c4.z, -c4.w), x[i]));
                     } else {
-                        const float2 cc = make_float2(c4, c4);
+                        const float2 cc = make_float2(c4.x, c4.x);
                         xn = __ffma2_rn(cc, y, x[i]);
                         yn = __ffma2_rn(cc, x[i], y);
                     }
@@ -1359,6 +1371,9 @@ static void fill_args(Ctx* c, SweepArgs& a, int mode, int which) {
     a.n_clusters = c->n_clusters;
     a.in_nz = nullptr;
     a.normalise_pass = 1;
+    a.gnb_colour = c->d_gnb_colour;
+    a.col_lo = 0;
+    a.col_hi = c->n_colours;
     a.mol_cluster = c->d_mol_cluster;
     a.cl_g0 = c->d_cl_g0;
     a.cl_ot0 = c->d_cl_ot0;
@@ -1397,11 +1412,11 @@ static void fill_args(Ctx* c, SweepArgs& a, int mode, int which) {
     a.err = &c->d_sc->err;
 }
 
-// colour < 0: the closure of a whole sweep (components over all active
-// blocks); colour >= 0: the closure of that colour alone, on the flags of the
-// current buffer unless it is the first of the pass.
+// The closure of the sweep's colours [col_lo, col_hi) (components over the
+// active blocks of those colours); unless it is the first of the pass, a unit
+// whose tiles in a row are all flagged zero does not count as held there.
 template <typename T>
-static cudaError_t closure_t(Ctx* c, int mode, int which, int colour, bool first) {
+static cudaError_t closure_t(Ctx* c, int mode, int which, int col_lo, int col_hi, bool first) {
     SweepArgs a;
     fill_args<T>(c, a, mode, which);
     const int in = c->cur, out = 1 - c->cur;
@@ -1415,22 +1430,17 @@ static cudaError_t closure_t(Ctx* c, int mode, int which, int colour, bool first
     a.unit_lab = c->d_unit_lab;
     a.in_nz = first ? nullptr : c->d_c_nz[in];
     a.normalise_pass = first ? 1 : 0;
+    a.col_lo = col_lo;
+    a.col_hi = col_hi;
     const size_t smem = closure_smem_bytes(c);
     if (smem > (size_t)kMaxDynSmem) return cudaErrorInvalidValue;
     cudaError_t e = cudaFuncSetAttribute(k_closure<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    if (colour < 0) {
-        const size_t lsmem = (size_t)2 * c->max_cl_groups * 4;
-        if (lsmem > (size_t)kMaxDynSmem) return cudaErrorInvalidValue;
-        e = cudaFuncSetAttribute(k_closure_labels, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lsmem);
-        if (e != cudaSuccess) return e;
-        k_closure_labels<<<c->n_clusters, 1024, lsmem, c->stream>>>(a, c->d_unit_lab);
-    } else {
-        const std::vector<int>& ptr = mode == 0 ? c->h_colour_ptr : c->h_ocolour_ptr;
-        const int nb = ptr[colour + 1] - ptr[colour];
-        k_colour_labels_init<<<(2 * c->n_groups + 255) / 256, 256, 0, c->stream>>>(a, c->d_unit_lab);
-        if (nb > 0) k_colour_labels_link<<<(nb + 127) / 128, 128, 0, c->stream>>>(a, ptr[colour], nb, c->d_unit_lab);
-    }
+    const size_t lsmem = (size_t)2 * c->max_cl_groups * 4;
+    if (lsmem > (size_t)kMaxDynSmem) return cudaErrorInvalidValue;
+    e = cudaFuncSetAttribute(k_closure_labels, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lsmem);
+    if (e != cudaSuccess) return e;
+    k_closure_labels<<<c->n_clusters, 1024, lsmem, c->stream>>>(a, c->d_unit_lab);
     k_closure<T><<<c->n_mol, 256, smem, c->stream>>>(a);
     c->cur = out;
     return cudaGetLastError();
@@ -1500,10 +1510,11 @@ static cudaError_t apply_t(Ctx* c, int mode, int which, int col_lo, int col_hi) 
     return apply_mode_t<T, 1, 6, kOrthoCap>(c, which, col_lo, col_hi);
 }
 
-cudaError_t launch_closure(Ctx* c, int mode, int which, int colour, bool first) {
-    c->n_launch += colour < 0 ? 2 : 3;
-    return c->prec == SSCF_FP64 ? closure_t<double>(c, mode, which, colour, first)
-                                : closure_t<float>(c, mode, which, colour, first);
+cudaError_t launch_closure(Ctx* c, int mode, int which, int col_lo, int col_hi, bool first) {
+    c->n_launch += 2;
+    if (col_hi < 0) col_hi = c->n_colours;
+    return c->prec == SSCF_FP64 ? closure_t<double>(c, mode, which, col_lo, col_hi, first)
+                                : closure_t<float>(c, mode, which, col_lo, col_hi, first);
 }
 
 cudaError_t launch_apply(Ctx* c, int mode, int which, int col_lo, int col_hi) {

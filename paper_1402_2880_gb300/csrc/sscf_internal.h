@@ -83,7 +83,7 @@ struct Ctx {
     int n_gnb = 0;       // group-graph entries (directed, including (A, A))
     int cap = 0;         // tiles per row block of C
     int capY = 0;        // row blocks per tile of Y
-    bool per_colour = false; // closure per colour (bounded fill) instead of per sweep
+    int closure_window = 0;  // colours per closure (bounded fill); 0: one closure per sweep
     int apply_variant = 0;   // 0 specialised sweep kernels where they apply, 1 generic only,
                              // 2 specialised with one CTA per block
     int tf_split = 4;        // CTAs sharing one occupied tile's pairs in the transform (sscf_autotune)
@@ -174,6 +174,7 @@ struct Ctx {
     int* d_gnb_ptr = nullptr;
     int* d_gnb_row = nullptr;
     int* d_gnb_col = nullptr;
+    int* d_gnb_colour = nullptr;
     int* d_colour_ptr = nullptr;
     int* d_colour_blk = nullptr;
     int* d_ocolour_ptr = nullptr;
@@ -292,8 +293,8 @@ cudaError_t launch_density(Ctx* c, double* P_out = nullptr);   // P blocks (n_mp
 // schedules and sweeps
 cudaError_t launch_select_rot(Ctx* c);
 cudaError_t launch_ortho_prepare(Ctx* c, int which, double tol);
-// structural fill of a whole sweep (colour < 0) or of one colour; cur <- other
-cudaError_t launch_closure(Ctx* c, int mode, int which, int colour = -1, bool first = true);
+// structural fill of the sweep's colours [col_lo, col_hi) (col_hi < 0: all); cur <- other
+cudaError_t launch_closure(Ctx* c, int mode, int which, int col_lo = 0, int col_hi = -1, bool first = true);
 size_t closure_smem_bytes(const Ctx* c);
 // mode 0 rotations, 1 combinations, colours [col_lo, col_hi) (col_hi < 0: all); in place
 cudaError_t launch_apply(Ctx* c, int mode, int which, int col_lo = 0, int col_hi = -1);

@@ -1,12 +1,13 @@
-"""The per-colour closure (closure_mode = 1) against the per-sweep closure.
+"""Windowed closures (closure_mode = k >= 1) against the per-sweep closure.
 
 Both place tiles before the 2x2 updates of a sweep and neither changes a
-value, so C, the pair lists and every energy must agree bit for bit. The
-per-colour closure gives a row only the partner units of one colour's active
-blocks for the units it holds nonzero values in, so rows hold their real fill
-plus one colour's insertions: with a row capacity far below the cluster's
-tile count it still runs the passes that the per-sweep closure (which gives a
-row every tile its units are connected to) refuses with SSCF_ERR_CAPACITY.
+value, so C, the pair lists and every energy must agree bit for bit. A
+window of k colours gives a row only the tiles its units are connected to
+through those colours' active blocks, counting only units it holds nonzero
+values in, so rows hold their real fill plus one window's insertions: with a
+row capacity far below the cluster's tile count it still runs the passes that
+the per-sweep closure (which gives a row every tile its units are connected
+to) refuses with SSCF_ERR_CAPACITY. Windows of 1 and 8 colours are checked.
 """
 import numpy as np
 import pytest
@@ -31,10 +32,10 @@ def _trajectory(n, precision, closure_mode, cap_tiles=0):
     return ctx, out
 
 
-@pytest.mark.parametrize("n,precision", [(100, 0), (216, 1)])
-def test_per_colour_closure_gives_the_same_mos(n, precision):
+@pytest.mark.parametrize("n,precision,window", [(100, 0, 1), (216, 1, 1), (216, 1, 8)])
+def test_windowed_closure_gives_the_same_mos(n, precision, window):
     _, a = _trajectory(n, precision, 0)
-    _, b = _trajectory(n, precision, 1)
+    _, b = _trajectory(n, precision, window)
     assert a[0] == b[0]
     assert np.array_equal(a[1], b[1])
     assert a[2] == b[2]
@@ -71,7 +72,8 @@ def test_per_colour_closure_fits_where_the_sweep_closure_overflows():
     with pytest.raises(SscfError) as e:
         prep(0, cap)
     assert e.value.status == -5
-    got_first, got_after, got_info = prep(1, cap)
-    for a, b in ((got_first, ref_first), (got_after, ref_after)):
-        assert all(np.array_equal(x, y) for x, y in zip(a, b))
-    assert got_info["energy"] == ref_info["energy"]
+    for window in (1, 8):
+        got_first, got_after, got_info = prep(window, cap)
+        for a, b in ((got_first, ref_first), (got_after, ref_after)):
+            assert all(np.array_equal(x, y) for x, y in zip(a, b))
+        assert got_info["energy"] == ref_info["energy"]
