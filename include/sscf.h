@@ -90,7 +90,9 @@ typedef struct {
                                    the end of the sweep. Rows hold their real fill plus
                                    one window's insertions (k = 1: the partner of each
                                    unit), for clusters whose dense rows do not fit; a
-                                   larger k copies C fewer times. With k >= 1 a
+                                   larger k copies C fewer times but, with many active
+                                   blocks, links units across much of the cluster
+                                   within the window (k = 1 bounds it). With k >= 1 a
                                    CAPACITY error leaves the MOs partly swept: restart
                                    from a checkpoint. */
 } sscf_params;
