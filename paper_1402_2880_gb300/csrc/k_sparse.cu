@@ -681,7 +681,7 @@ cudaError_t launch_colindex(Ctx* c) {
     return cudaGetLastError();
 }
 
-static bool g_attr_done = false;
+static bool g_attr_done[64] = {false};   // per device: function attributes are set per device
 
 template <typename T>
 static cudaError_t set_attrs() {
@@ -699,11 +699,14 @@ static cudaError_t set_attrs() {
 }
 
 static cudaError_t ensure_attrs() {
-    if (g_attr_done) return cudaSuccess;
-    cudaError_t e = set_attrs<double>();
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev >= 0 && dev < 64 && g_attr_done[dev]) return cudaSuccess;
+    e = set_attrs<double>();
     if (e != cudaSuccess) return e;
     e = set_attrs<float>();
-    if (e == cudaSuccess) g_attr_done = true;
+    if (e == cudaSuccess && dev >= 0 && dev < 64) g_attr_done[dev] = true;
     return e;
 }
 
