@@ -843,6 +843,8 @@ int sscf_create(const sscf_system* sys, const sscf_params* prm, void* cuda_strea
     AL(c.d_cci_cnt, (size_t)c.n_tiles * 4);
     AL(c.d_cci_row, (size_t)c.n_mol * c.cap * 4);
     AL(c.d_cci_slot, (size_t)c.n_mol * c.cap * 4);
+    AL(c.d_c_cnz, (size_t)c.n_mol * c.cap);
+    AL(c.d_blk_info, (size_t)std::max(c.n_gnb, 1) * 8 * 4);
     AL(c.d_y_n, (size_t)c.n_tiles * 4);
     AL(c.d_y_row, (size_t)c.n_tiles * c.capY * 4);
     AL(c.d_y_val, (size_t)c.n_tiles * c.capY * kTileVals * ts);

@@ -424,6 +424,8 @@ struct SweepArgs {
     int* out_tile;
     void* out_val;
     unsigned char* out_nz;   // flags of out: 0 = the tile is all zero (written by the closure, kept by the sweep)
+    unsigned char* col_nz;   // sweeps: the same flags in column-index order (entry p of cci_row / cci_slot)
+    const int4* blk_info;    // FP32 sweeps: per block in colour order, (e, pairs, touch, rows), (pa, pb, rows of B, 0)
     const unsigned char* in_nz;   // closure: flags of the input (NULL: every listed tile may be nonzero)
     int normalise_pass;      // closure in mode 1: divide by d_i (the first closure of a pass)
     unsigned* err;
@@ -602,6 +604,37 @@ __global__ void __launch_bounds__(256) k_closure(SweepArgs a) {
 }
 
 
+// The tile flags of the sweep's input in column-index order: entry p of tile
+// t's list (row cci_row[p], slot cci_slot[p]) gets the flag of that tile in
+// that row. The sweep kernels then test a block's rows for work with
+// contiguous reads of its tiles' column lists, with no dependence on the slot
+// loads, and raise both copies of a flag together. One CTA per tile.
+__global__ void __launch_bounds__(256) k_flags_by_column(int cap, const int* __restrict__ cci_ptr,
+                                                         const int* __restrict__ cci_row,
+                                                         const int* __restrict__ cci_slot,
+                                                         const unsigned char* __restrict__ nz,
+                                                         unsigned char* __restrict__ col_nz) {
+    const int t = blockIdx.x;
+    const int lo = cci_ptr[t], hi = cci_ptr[t + 1];
+    for (int p = lo + threadIdx.x; p < hi; p += blockDim.x) col_nz[p] = nz[(size_t)cci_row[p] * cap + cci_slot[p]];
+}
+
+// What a CTA of k_apply_full needs to start on block q of the pass (colour
+// order), gathered once per sweep so that it costs one load instead of a
+// chain of dependent ones: the block, its pair count and touched tiles, and
+// the column lists of the first tile of each side.
+template <int MODE>
+__global__ void k_block_info(SweepArgs a, int n, int4* __restrict__ info) {
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= n) return;
+    const int e = a.blk[q];
+    const int A = a.gnb_row[e], B = a.gnb_col[e];
+    const int ta0 = a.group_ot0[A], tb0 = MODE == 0 ? a.group_vt0[B] : a.group_ot0[B];
+    const int pa = a.cci_ptr[ta0], pb = a.cci_ptr[tb0];
+    info[2 * q] = make_int4(e, a.pr_n[e], a.pr_touch[e], a.cci_ptr[ta0 + 1] - pa);
+    info[2 * q + 1] = make_int4(pa, pb, a.cci_ptr[tb0 + 1] - pb, 0);
+}
+
 // side tiles of a block: up to 3 per side, as (first tile of a run, offset)
 struct Side {
     int n;           // tiles on the side
@@ -678,6 +711,7 @@ __global__ void __launch_bounds__(apply_threads<T>()) k_apply_colour(SweepArgs a
     __shared__ int s_lvl[kMaxSub + 1];
     __shared__ int s_row[CH];
     __shared__ int s_slot[CH][NT];
+    __shared__ int s_cp[NT];   // start of each panel tile's column list (-1: not held)
     // side A occupies panel tiles [0, kSideA), side B [kSideA, NT)
     constexpr int kSideA = MODE == 0 ? 2 : NT / 2;
     if (*a.err & (kErrCapacity | kErrSortSize)) return;
@@ -714,6 +748,19 @@ __global__ void __launch_bounds__(apply_threads<T>()) k_apply_colour(SweepArgs a
             if (i < NT - kSideA)
                 s_slot[t][kSideA + i] = same ? -1 : (i < sb.nrun0 ? bo + i : (i < sb.n ? bv + (i - sb.nrun0) : -1));
         }
+    }
+    if (threadIdx.x < NT) {
+        const int p = threadIdx.x;
+        int tile = -1;
+        if (p < kSideA) {
+            if (p < sa.nrun0) tile = sa.run0 + p;
+            else if (p < sa.n) tile = sa.run1 + (p - sa.nrun0);
+        } else if (!same) {
+            const int i = p - kSideA;
+            if (i < sb.nrun0) tile = sb.run0 + i;
+            else if (i < sb.n) tile = sb.run1 + (i - sb.nrun0);
+        }
+        s_cp[p] = tile >= 0 ? a.cci_ptr[tile] : -1;
     }
     const int* lvl = a.pr_lvl + (size_t)e * (kMaxSub + 1);
     for (int i = threadIdx.x; i <= kMaxSub; i += blockDim.x) s_lvl[i] = lvl[i];
@@ -869,7 +916,10 @@ __global__ void __launch_bounds__(apply_threads<T>()) k_apply_colour(SweepArgs a
             e2[col] = srcp[col * NRP];
             any |= e2[col] != (T)0;
         }
-        if (any) a.out_nz[(size_t)s_row[rb] * a.cap + sl] = 1;   // the tile may be nonzero now
+        if (any) {   // the tile may be nonzero now
+            a.out_nz[(size_t)s_row[rb] * a.cap + sl] = 1;
+            a.col_nz[s_cp[p] + k0 + rb] = 1;
+        }
         V* dst = (V*)(val + ((size_t)s_row[rb] * a.cap + sl) * kTileVals + kr * 16);
 #pragma unroll
         for (int v = 0; v < kVPer; ++v) dst[v] = out[v];
@@ -946,25 +996,22 @@ __global__ void __launch_bounds__(kFullThreads, kFullMinCtas[MODE]) k_apply_full
     Coef* coef = (Coef*)(panel + NB * kFullNR);             // [32 levels][32 i]
     __shared__ unsigned s_mask[32];
     if (*a.err & (kErrCapacity | kErrSortSize)) return;
-    const int e = a.blk[p0 + blockIdx.y];
-    const int np = a.pr_n[e];
+    const int4 i0 = a.blk_info[2 * (p0 + blockIdx.y)], i1 = a.blk_info[2 * (p0 + blockIdx.y) + 1];
+    const int e = i0.x, np = i0.y, touch = i0.z, n_rows = i0.w;
+    const int pa = i1.x, pb = i1.y;
     if (np == 0) return;
-    const int A = a.gnb_row[e], B = a.gnb_col[e];
-    const int ta0 = a.group_ot0[A], tb0 = MODE == 0 ? a.group_vt0[B] : a.group_ot0[B];
-    const int pa = a.cci_ptr[ta0], n_rows = a.cci_ptr[ta0 + 1] - pa;
-    const int pb = a.cci_ptr[tb0];
     // CTA x takes row chunks x, x + gridDim.x, ... of the block, so its
     // coefficient table serves several chunks
     const int k_first = blockIdx.x * kFullCH;
     if (k_first >= n_rows) return;
-    if (a.cci_ptr[tb0 + 1] - pb != n_rows) {
+    if (i1.z != n_rows) {
         if (threadIdx.x == 0) atomicOr(a.err, kErrCapacity);
         return;
     }
-    for (int i = threadIdx.x; i < 32 * 32; i += blockDim.x) {
-        if constexpr (MODE == 0) coef[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-        else coef[i] = make_float2(0.f, 0.f);
-    }
+    // rotations read only the slots that hold a pair (the mask's bits); the
+    // dense levels of occupied passes read every slot, so those start at zero
+    if constexpr (MODE == 1)
+        for (int i = threadIdx.x; i < 32 * 32; i += blockDim.x) coef[i] = make_float2(0.f, 0.f);
     if (threadIdx.x < 32) s_mask[threadIdx.x] = 0u;
     __syncthreads();
     const float* cs = (const float*)a.pr_cs + (size_t)e * kOrthoCap * 2;
@@ -982,26 +1029,31 @@ __global__ void __launch_bounds__(kFullThreads, kFullMinCtas[MODE]) k_apply_full
         atomicOr(&s_mask[lv], 1u << il);
     }
     __syncthreads();
-    // tiles no selected pair touches keep their values: neither loaded nor stored
-    const int touch = a.pr_touch[e];
+    // tiles no selected pair touches (touch bits clear) keep their values:
+    // neither loaded nor stored
     float* val = (float*)a.out_val;   // in place
+    // The side tiles of a unit are consecutive tile ids with equal column
+    // lists, so side tile t's list starts t * n_rows after the first one's.
     // Each row chunk first tells, per row pair, whether it has work: a row pair
     // whose touched tiles are all flagged zero stays zero under the block's
     // updates (x - c y and c x + s y of zeros, truncation keeps zeros), and so
     // does a flagged row pair of zeros that runs through them. The row pairs
     // with work are appended to a shared list; once it holds a CTA's worth,
     // every thread takes one, loads both sides and runs the updates, so that the
-    // level loop runs in full warps. The rest runs at the end.
+    // level loop runs in full warps. The rest runs at the end. The flags are
+    // read in column-index order (contiguous for consecutive rows of the
+    // block), together with the rows and slots the run needs.
     __shared__ int s_list[2 * kFullThreads];   // row pairs with work, not yet run
+    __shared__ int s_lrow[2 * kFullThreads];   // their row block and the slots of both sides there
+    __shared__ int s_lsa[2 * kFullThreads];
+    __shared__ int s_lsb[2 * kFullThreads];
     __shared__ int s_wcnt[kFullThreads / 32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int rb = threadIdx.x / 3;   // own row block (of the chunk)
     // the updates of one row pair with work: entry = (row block in the block's
     // row list) * 3 + pair
-    auto run = [&](const int ent) {
+    auto run = [&](const int ent, const int row, const int slA, const int slB) {
         const int kr = ent / 3, k2s = 2 * (ent - 3 * kr);
-        const int row = a.cci_row[pa + kr];
-        const int slA = a.cci_slot[pa + kr], slB = a.cci_slot[pb + kr];
         const size_t baseA = ((size_t)row * a.cap + slA) * kTileVals + k2s * kTileW;
         const size_t baseB = ((size_t)row * a.cap + slB) * kTileVals + k2s * kTileW;
         // the B side goes to the thread's own panel rows (consecutive threads,
@@ -1172,7 +1224,10 @@ __global__ void __launch_bounds__(kFullThreads, kFullMinCtas[MODE]) k_apply_full
                 any |= a0.x != 0.f || a0.y != 0.f || a1.x != 0.f || a1.y != 0.f || a2.x != 0.f ||
                        a2.y != 0.f || a3.x != 0.f || a3.y != 0.f;
             }
-            if (any) f[slA + t] = 1;
+            if (any) {
+                f[slA + t] = 1;
+                a.col_nz[pa + t * n_rows + kr] = 1;
+            }
         }
 #pragma unroll
         for (int t = 0; t < NB / 16; ++t) {
@@ -1190,7 +1245,10 @@ __global__ void __launch_bounds__(kFullThreads, kFullMinCtas[MODE]) k_apply_full
                 any |= b0.x != 0.f || b0.y != 0.f || b1.x != 0.f || b1.y != 0.f || b2.x != 0.f ||
                        b2.y != 0.f || b3.x != 0.f || b3.y != 0.f;
             }
-            if (any) f[slB + t] = 1;
+            if (any) {
+                f[slB + t] = 1;
+                a.col_nz[pb + t * n_rows + kr] = 1;
+            }
         }
     };
     int n_acc = 0;   // entries in s_list (the same in every thread)
@@ -1200,14 +1258,16 @@ __global__ void __launch_bounds__(kFullThreads, kFullMinCtas[MODE]) k_apply_full
         // unchanged and skipped included
         if (threadIdx.x == 0) atomicAdd(a.upd, (unsigned long long)np * (unsigned long long)(nk * 6));
         bool work = false;
+        int row = 0, slA = 0, slB = 0;
         if (rb < nk) {
-            const int row = a.cci_row[pa + k0 + rb];
-            const int slA = a.cci_slot[pa + k0 + rb], slB = a.cci_slot[pb + k0 + rb];
-            const unsigned char* f = a.out_nz + (size_t)row * a.cap;
+            const int k = k0 + rb;
+            row = a.cci_row[pa + k];
+            slA = a.cci_slot[pa + k];
+            slB = a.cci_slot[pb + k];
 #pragma unroll
-            for (int t = 0; t < 2; ++t) work |= (touch >> t & 1) && f[slA + t];
+            for (int t = 0; t < 2; ++t) work |= (touch >> t & 1) && a.col_nz[pa + t * n_rows + k];
 #pragma unroll
-            for (int t = 0; t < NB / 16; ++t) work |= (touch >> (3 + t) & 1) && f[slB + t];
+            for (int t = 0; t < NB / 16; ++t) work |= (touch >> (3 + t) & 1) && a.col_nz[pb + t * n_rows + k];
         }
         // pack the row pairs with work to the first threads
         const unsigned bal = __ballot_sync(0xffffffffu, work);
@@ -1219,19 +1279,32 @@ __global__ void __launch_bounds__(kFullThreads, kFullMinCtas[MODE]) k_apply_full
             before += w < warp ? s_wcnt[w] : 0;
             n_work += s_wcnt[w];
         }
-        if (work) s_list[n_acc + before + __popc(bal & ((1u << lane) - 1u))] = 3 * k0 + threadIdx.x;
+        if (work) {
+            const int i = n_acc + before + __popc(bal & ((1u << lane) - 1u));
+            s_list[i] = 3 * k0 + threadIdx.x;
+            s_lrow[i] = row;
+            s_lsa[i] = slA;
+            s_lsb[i] = slB;
+        }
         n_acc += n_work;
         __syncthreads();
         if (n_acc >= kFullThreads) {
-            const int ent = s_list[threadIdx.x];
+            const int ent = s_list[threadIdx.x], erow = s_lrow[threadIdx.x];
+            const int esa = s_lsa[threadIdx.x], esb = s_lsb[threadIdx.x];
             __syncthreads();   // entries read: move the rest (fewer than a CTA's worth) to the front
-            for (int i = threadIdx.x; i < n_acc - kFullThreads; i += blockDim.x) s_list[i] = s_list[kFullThreads + i];
+            for (int i = threadIdx.x; i < n_acc - kFullThreads; i += blockDim.x) {
+                s_list[i] = s_list[kFullThreads + i];
+                s_lrow[i] = s_lrow[kFullThreads + i];
+                s_lsa[i] = s_lsa[kFullThreads + i];
+                s_lsb[i] = s_lsb[kFullThreads + i];
+            }
             n_acc -= kFullThreads;
-            run(ent);
+            run(ent, erow, esa, esb);
             __syncthreads();   // the list is rewritten by the next chunk
         }
     }   // row chunks
-    if ((int)threadIdx.x < n_acc) run(s_list[threadIdx.x]);
+    if ((int)threadIdx.x < n_acc)
+        run(s_list[threadIdx.x], s_lrow[threadIdx.x], s_lsa[threadIdx.x], s_lsb[threadIdx.x]);
 }
 
 // drop tiles whose 6x16 values are all zero; in -> out
@@ -1454,6 +1527,7 @@ static cudaError_t apply_mode_t(Ctx* c, int which, int col_lo, int col_hi) {
     a.in_tile = a.out_tile = c->d_c_tile[c->cur];
     a.in_val = a.out_val = c->d_c_val[c->cur];
     a.out_nz = c->d_c_nz[c->cur];
+    a.col_nz = c->d_c_cnz;
     const size_t smem = (size_t)NT * 16 * apply_nrp<T>() * sizeof(T) + (size_t)2 * PCAP * sizeof(T) + (size_t)PCAP * 4;
     cudaError_t e = cudaFuncSetAttribute(k_apply_colour<T, MODE, NT, PCAP>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -1479,6 +1553,14 @@ static cudaError_t apply_mode_t(Ctx* c, int which, int col_lo, int col_hi) {
         full_occ[MODE] = std::max(full_occ[MODE], 1);
     }
     const int chunks = (c->n_mol + kFullCH - 1) / kFullCH;
+    k_flags_by_column<<<c->n_tiles, 256, 0, c->stream>>>(c->cap, c->d_cci_ptr, c->d_cci_row, c->d_cci_slot,
+                                                         a.out_nz, a.col_nz);
+    c->n_launch += 1;
+    if (full && a.n_blk > 0) {
+        a.blk_info = (const int4*)c->d_blk_info;
+        k_block_info<MODE><<<(a.n_blk + 127) / 128, 128, 0, c->stream>>>(a, a.n_blk, (int4*)c->d_blk_info);
+        c->n_launch += 1;
+    }
     for (int col = col_lo; col < col_hi; ++col) {
         const int nf = full ? nfull[col] : 0;
         if (nf > 0) {

@@ -185,6 +185,8 @@ struct Ctx {
     int* d_c_tile[2] = {nullptr, nullptr};
     void* d_c_val[2] = {nullptr, nullptr};
     unsigned char* d_c_nz[2] = {nullptr, nullptr};   // per (row block, slot): 0 = tile known all-zero during a sweep
+    unsigned char* d_c_cnz = nullptr;   // the current sweep's flags in column-index order
+    int* d_blk_info = nullptr;          // per block of a sweep in colour order: 8 ints the FP32 sweep kernel starts from
     int cur = 0;
     int* d_cci_ptr = nullptr;     // n_tiles + 1
     int* d_cci_cnt = nullptr;     // n_tiles
