@@ -110,6 +110,7 @@ __global__ void k_ci_sort(const int* __restrict__ ptr, int* __restrict__ row, in
 // through the molecule-pair pattern, then one warp per output row block sums
 // X[r, n] (6x6) C[n, t] (6x16) over the pattern neighbours n holding t.
 // ---------------------------------------------------------------------------
+constexpr int kXcBatch = 4;   // matched neighbours whose loads are in flight together
 template <typename T>
 __global__ void k_xc(int tile_lo, int n_rows, int cap, int capY, const int* __restrict__ tile_row0,
                      const int* __restrict__ cci_ptr, const int* __restrict__ cci_row,
@@ -194,17 +195,17 @@ __global__ void k_xc(int tile_lo, int n_rows, int cap, int capY, const int* __re
             }
             unsigned mm = __ballot_sync(0xffffffffu, sl >= 0);
             while (mm) {
-                // two matched neighbours per round: both loads in flight, sums in order
-                int src[2];
+                // kXcBatch matched neighbours per round: their loads in flight together, sums in order
+                int src[kXcBatch];
 #pragma unroll
-                for (int u = 0; u < 2; ++u) {
+                for (int u = 0; u < kXcBatch; ++u) {
                     src[u] = mm ? __ffs(mm) - 1 : -1;
                     if (mm) mm &= mm - 1;
                 }
-                A c6[2][6];
-                const T* xb[2];
+                A c6[kXcBatch][6];
+                const T* xb[kXcBatch];
 #pragma unroll
-                for (int u = 0; u < 2; ++u) {
+                for (int u = 0; u < kXcBatch; ++u) {
                     const int sv = src[u] < 0 ? 0 : src[u];
                     const int n = __shfl_sync(0xffffffffu, nl, sv);
                     const int ss = __shfl_sync(0xffffffffu, sl, sv);
@@ -216,13 +217,27 @@ __global__ void k_xc(int tile_lo, int n_rows, int cap, int capY, const int* __re
                     }
                 }
 #pragma unroll
-                for (int u = 0; u < 2; ++u) {
+                for (int u = 0; u < kXcBatch; ++u) {
                     if (src[u] < 0) continue;
+                    // the lane's three rows of the 6x6 block, two values per load
+                    // (rows start 6 values apart: 8-byte aligned for FP32, 16 for FP64)
+                    using V2 = typename std::conditional<sizeof(T) == 4, float2, double2>::type;
+                    A xr[3][6];
+#pragma unroll
+                    for (int rr = 0; rr < 3; ++rr) {
+                        const V2* x2 = (const V2*)(xb[u] + (q0 + 2 * rr) * 6);
+#pragma unroll
+                        for (int h = 0; h < 3; ++h) {
+                            const V2 v = x2[h];
+                            xr[rr][2 * h] = (A)v.x;
+                            xr[rr][2 * h + 1] = (A)v.y;
+                        }
+                    }
 #pragma unroll
                     for (int q = 0; q < 6; ++q) {
-                        acc0 += (A)xb[u][(q0)*6 + q] * c6[u][q];
-                        acc1 += (A)xb[u][(q0 + 2) * 6 + q] * c6[u][q];
-                        acc2 += (A)xb[u][(q0 + 4) * 6 + q] * c6[u][q];
+                        acc0 += xr[0][q] * c6[u][q];
+                        acc1 += xr[1][q] * c6[u][q];
+                        acc2 += xr[2][q] * c6[u][q];
                     }
                 }
             }
