@@ -1252,59 +1252,69 @@ __global__ void __launch_bounds__(kFullThreads, kFullMinCtas[MODE]) k_apply_full
         }
     };
     int n_acc = 0;   // entries in s_list (the same in every thread)
-    for (int k0 = k_first; k0 < n_rows; k0 += gridDim.x * kFullCH) {
-        const int nk = min(kFullCH, n_rows - k0);
-        // the counter holds the 2x2 row updates the algorithm defines, rows proven
-        // unchanged and skipped included
-        if (threadIdx.x == 0) atomicAdd(a.upd, (unsigned long long)np * (unsigned long long)(nk * 6));
-        bool work = false;
-        int row = 0, slA = 0, slB = 0;
-        if (rb < nk) {
-            const int k = k0 + rb;
-            row = a.cci_row[pa + k];
-            slA = a.cci_slot[pa + k];
-            slB = a.cci_slot[pb + k];
+    int k0 = k_first;
+    // one call site of the update code (it is large): collect row pairs until
+    // a CTA's worth is listed or the block's rows run out, then run them
+    for (;;) {
+        while (n_acc < kFullThreads && k0 < n_rows) {
+            const int nk = min(kFullCH, n_rows - k0);
+            // the counter holds the 2x2 row updates the algorithm defines, rows proven
+            // unchanged and skipped included
+            if (threadIdx.x == 0) atomicAdd(a.upd, (unsigned long long)np * (unsigned long long)(nk * 6));
+            bool work = false;
+            int row = 0, slA = 0, slB = 0;
+            if (rb < nk) {
+                const int k = k0 + rb;
+                row = a.cci_row[pa + k];
+                slA = a.cci_slot[pa + k];
+                slB = a.cci_slot[pb + k];
 #pragma unroll
-            for (int t = 0; t < 2; ++t) work |= (touch >> t & 1) && a.col_nz[pa + t * n_rows + k];
+                for (int t = 0; t < 2; ++t) work |= (touch >> t & 1) && a.col_nz[pa + t * n_rows + k];
 #pragma unroll
-            for (int t = 0; t < NB / 16; ++t) work |= (touch >> (3 + t) & 1) && a.col_nz[pb + t * n_rows + k];
-        }
-        // pack the row pairs with work to the first threads
-        const unsigned bal = __ballot_sync(0xffffffffu, work);
-        if (lane == 0) s_wcnt[warp] = __popc(bal);
-        __syncthreads();
-        int before = 0, n_work = 0;
-#pragma unroll
-        for (int w = 0; w < kFullThreads / 32; ++w) {
-            before += w < warp ? s_wcnt[w] : 0;
-            n_work += s_wcnt[w];
-        }
-        if (work) {
-            const int i = n_acc + before + __popc(bal & ((1u << lane) - 1u));
-            s_list[i] = 3 * k0 + threadIdx.x;
-            s_lrow[i] = row;
-            s_lsa[i] = slA;
-            s_lsb[i] = slB;
-        }
-        n_acc += n_work;
-        __syncthreads();
-        if (n_acc >= kFullThreads) {
-            const int ent = s_list[threadIdx.x], erow = s_lrow[threadIdx.x];
-            const int esa = s_lsa[threadIdx.x], esb = s_lsb[threadIdx.x];
-            __syncthreads();   // entries read: move the rest (fewer than a CTA's worth) to the front
-            for (int i = threadIdx.x; i < n_acc - kFullThreads; i += blockDim.x) {
-                s_list[i] = s_list[kFullThreads + i];
-                s_lrow[i] = s_lrow[kFullThreads + i];
-                s_lsa[i] = s_lsa[kFullThreads + i];
-                s_lsb[i] = s_lsb[kFullThreads + i];
+                for (int t = 0; t < NB / 16; ++t) work |= (touch >> (3 + t) & 1) && a.col_nz[pb + t * n_rows + k];
             }
-            n_acc -= kFullThreads;
-            run(ent, erow, esa, esb);
-            __syncthreads();   // the list is rewritten by the next chunk
+            // pack the row pairs with work to the first threads
+            const unsigned bal = __ballot_sync(0xffffffffu, work);
+            if (lane == 0) s_wcnt[warp] = __popc(bal);
+            __syncthreads();
+            int before = 0, n_work = 0;
+#pragma unroll
+            for (int w = 0; w < kFullThreads / 32; ++w) {
+                before += w < warp ? s_wcnt[w] : 0;
+                n_work += s_wcnt[w];
+            }
+            if (work) {
+                const int i = n_acc + before + __popc(bal & ((1u << lane) - 1u));
+                s_list[i] = 3 * k0 + threadIdx.x;
+                s_lrow[i] = row;
+                s_lsa[i] = slA;
+                s_lsb[i] = slB;
+            }
+            n_acc += n_work;
+            k0 += gridDim.x * kFullCH;
+            __syncthreads();
         }
-    }   // row chunks
-    if ((int)threadIdx.x < n_acc)
-        run(s_list[threadIdx.x], s_lrow[threadIdx.x], s_lsa[threadIdx.x], s_lsb[threadIdx.x]);
+        if (n_acc == 0) break;
+        const int take = min(n_acc, kFullThreads);
+        const bool mine = (int)threadIdx.x < take;
+        int ent = 0, erow = 0, esa = 0, esb = 0;
+        if (mine) {
+            ent = s_list[threadIdx.x];
+            erow = s_lrow[threadIdx.x];
+            esa = s_lsa[threadIdx.x];
+            esb = s_lsb[threadIdx.x];
+        }
+        __syncthreads();   // entries read: move the rest (fewer than a CTA's worth) to the front
+        for (int i = threadIdx.x; i < n_acc - take; i += blockDim.x) {
+            s_list[i] = s_list[take + i];
+            s_lrow[i] = s_lrow[take + i];
+            s_lsa[i] = s_lsa[take + i];
+            s_lsb[i] = s_lsb[take + i];
+        }
+        n_acc -= take;
+        if (mine) run(ent, erow, esa, esb);
+        __syncthreads();   // the list is rewritten by the next chunk
+    }
 }
 
 // drop tiles whose 6x16 values are all zero; in -> out
