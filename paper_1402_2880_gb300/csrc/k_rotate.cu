@@ -77,16 +77,40 @@ __global__ void k_rot_stats(int n_gnb, const int* __restrict__ gnb_row, const in
 }
 
 // one radix-select pass over the candidate keys (8 bits, most significant
-// first) of every cluster whose candidates exceed its cap
+// first) of every cluster whose candidates exceed its cap. A CTA takes a
+// contiguous range of blocks (clusters are contiguous in block order) and
+// counts in shared memory, adding its nonzero bins to the cluster's global
+// histogram when the cluster changes and at the end: the early passes put
+// most keys in a few bins, which global atomics per key would serialise on.
 template <typename T>
-__global__ void k_rot_hist(int shift, int n_gnb, const int* __restrict__ gnb_row, const int* __restrict__ gnb_col,
-                           const int* __restrict__ group_nmol, const int* __restrict__ group_nvt,
-                           const int* __restrict__ group_cl, const int* __restrict__ blk_tp0,
-                           const T* __restrict__ F, double tau, const ClSel* __restrict__ cl,
-                           unsigned long long* __restrict__ hist) {
-    for (int e = blockIdx.x; e < n_gnb; e += gridDim.x) {
+__global__ void __launch_bounds__(256) k_rot_hist(int shift, int n_gnb, const int* __restrict__ gnb_row,
+                                                  const int* __restrict__ gnb_col,
+                                                  const int* __restrict__ group_nmol, const int* __restrict__ group_nvt,
+                                                  const int* __restrict__ group_cl, const int* __restrict__ blk_tp0,
+                                                  const T* __restrict__ F, double tau,
+                                                  const ClSel* __restrict__ cl, unsigned long long* __restrict__ hist) {
+    __shared__ unsigned s_h[256];
+    const int per = (n_gnb + gridDim.x - 1) / gridDim.x;
+    const int e_lo = blockIdx.x * per, e_hi = min(n_gnb, e_lo + per);
+    for (int i = threadIdx.x; i < 256; i += blockDim.x) s_h[i] = 0u;
+    int cur = -1;   // cluster whose counts s_h holds (the same in every thread)
+    auto flush = [&]() {
+        __syncthreads();
+        for (int i = threadIdx.x; i < 256; i += blockDim.x)
+            if (s_h[i]) {
+                atomicAdd(&hist[(size_t)cur * 256 + i], (unsigned long long)s_h[i]);
+                s_h[i] = 0u;
+            }
+        __syncthreads();
+    };
+    __syncthreads();
+    for (int e = e_lo; e < e_hi; ++e) {
         const int A = gnb_row[e], B = gnb_col[e];
         const int c = group_cl[A];
+        if (c != cur) {
+            if (cur >= 0) flush();
+            cur = c;
+        }
         const ClSel s = cl[c];
         if (s.cand <= s.kmax) continue;
         const int no = 4 * group_nmol[A], nv = 2 * group_nmol[B], nvt = group_nvt[B];
@@ -97,9 +121,10 @@ __global__ void k_rot_hist(int shift, int n_gnb, const int* __restrict__ gnb_row
             if (!(f >= tau && f > 0.0)) continue;
             const unsigned long long k = dkey(f);
             if ((k & s.mask) != s.prefix) continue;
-            atomicAdd(&hist[(size_t)c * 256 + ((k >> shift) & 255ull)], 1ull);
+            atomicAdd(&s_h[(k >> shift) & 255ull], 1u);
         }
     }
+    if (cur >= 0) flush();
 }
 
 // one thread per cluster: pick the bin holding the kmax-th largest key
