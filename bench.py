@@ -75,6 +75,9 @@ def parse():
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 path on the same checkpoint")
     ap.add_argument("--no-accuracy", action="store_true", help="skip the converged 32-molecule accuracy check")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (very large single clusters)")
+    ap.add_argument("--no-batch", action="store_true",
+                    help="skip the batch leg (the first wave of the 256-cluster batch, graph-replayed steps)")
+    ap.add_argument("--batch-clusters", type=int, default=32, help="clusters in the batch leg")
     return ap.parse_args()
 
 
@@ -327,10 +330,11 @@ def main():
     K = args.steps
     flush = None
 
-    def timed_steps(ctx, ck, n_steps, flushing):
+    def timed_steps(ctx, ck, n_steps, flushing, on=None):
         """n_steps replays of the checkpointed iteration: restore (untimed), then one
         sscf_step between CUDA events on the context's stream; returns (ms, infos)."""
         nonlocal flush
+        st = stream if on is None else on
         if flushing and flush is None:
             flush = torch.empty(64 << 20, dtype=torch.float32, device=dev)
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
@@ -340,11 +344,11 @@ def main():
             ctx.set_C_tiles(*ck[0])
             ctx.set_charges(*ck[1])
             if flushing:
-                with torch.cuda.stream(stream):
+                with torch.cuda.stream(st):
                     flush.zero_()
-            ev[k][0].record(stream)
+            ev[k][0].record(st)
             infos.append(ctx.step())
-            ev[k][1].record(stream)
+            ev[k][1].record(st)
         torch.cuda.synchronize(dev)
         return sum(a.elapsed_time(b_) for a, b_ in ev), infos
 
@@ -538,6 +542,53 @@ def main():
     if not args.no_accuracy:
         accuracy = accuracy_config1(p)
 
+    def batch_leg(n_clusters: int, n_steps: int = 2, warmup: int = 3):
+        """The first n_clusters of the 256-cluster batch (sizes U[200, 3000], seed 7)
+        in one context, mixed, eps 1e-5: every SCC iteration of all of them is one
+        CUDA-graph replay on a side stream; iteration warmup + 1 replayed from a
+        checkpoint n_steps times between CUDA events, as the main leg."""
+        from synth import cluster_sizes, concat_clusters
+        sizes = cluster_sizes()[:n_clusters]
+        sb = concat_clusters([lattice_water(int(nm), seed=k) for k, nm in enumerate(sizes)])
+        st = torch.cuda.Stream(dev)
+        ctx = Context.from_system(sb, p, precision=SSCF_MIXED, stream=st.cuda_stream)
+        ctx.set_thresholds(args.prep_eps, 10 * args.prep_eps, 1e-8)
+        ctx.guess()
+        ctx.orthonormalise(SSCF_ORTHO_ALL, max_pass=args.prep_passes)
+        ctx.set_thresholds(1e-5, 1e-4, 1e-6)
+        ctx.reset_charges()
+        for w in range(warmup):
+            if w == 1:
+                ctx.autotune()
+                ctx.enable_graph(True)
+            ctx.step()
+        torch.cuda.synchronize(dev)
+        ckb = (ctx.get_C_tiles(), ctx.get_charges())
+        ctx.set_C_tiles(*ckb[0])
+        ctx.set_charges(*ckb[1])
+        ctx.step()   # untimed replay
+        samp = ClockSampler(local_rank)
+        samp.start()
+        msb, infb = timed_steps(ctx, ckb, n_steps, False, on=st)
+        clk = samp.stop()
+        n_mo_b = ctx.n_mo
+        ctx.close()
+        t = msb / n_steps / 1e3
+        return {"workload": f"the first {n_clusters} clusters of the 256-cluster batch ({sb.n_mol} molecules, "
+                            f"{sb.n_atoms} atoms) in one context, mixed, eps 1e-05; each SCC iteration of all "
+                            f"of them is one CUDA-graph replay; iteration {warmup + 1} replayed {n_steps} times "
+                            "from a checkpoint",
+                "clusters": n_clusters, "n_mol": sb.n_mol, "n_atoms": sb.n_atoms,
+                "ms_per_step": msb / n_steps, "cluster_iter_per_s": n_clusters / t,
+                "atom_iter_per_s": sb.n_atoms / t, "graph": True,
+                "nnz_per_mo": float(np.mean([inf["nnz_c"] for inf in infb])) / n_mo_b,
+                "same_iteration_every_step": len({round(inf["energy"], 9) for inf in infb}) == 1,
+                "clocks": clk}
+
+    batch = None
+    if not args.no_batch and args.clusters == 0 and args.precision == "mixed":
+        batch = batch_leg(args.batch_clusters)
+
     launches = int(round(mean("launches")))
     fp64 = runs[0]["fp64"]
     line = {
@@ -581,6 +632,7 @@ def main():
         "fp64": fp64,
         "mixed_speedup_vs_fp64": (fp64["ms_per_step"] / (t_max / K)) if fp64 else None,
         "accuracy": accuracy,
+        "batch": batch,
         "state": {"energy": infos[-1]["energy"], "dq_max": infos[-1]["dq_max"], "n_rot": n_rot,
                   "n_combo": n_combo, "nnz_per_mo": nnz_c / n_mo_local,
                   "same_iteration_every_step": all(r["same_iteration"] for r in runs)},
