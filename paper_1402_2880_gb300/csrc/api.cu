@@ -689,8 +689,10 @@ int sscf_create(const sscf_system* sys, const sscf_params* prm, void* cuda_strea
     c.cap = std::max(c.cap, 2);
     c.max_cl_groups = 0;
     for (int k = 0; k < c.n_clusters; ++k) c.max_cl_groups = std::max(c.max_cl_groups, c.h_cl_g0[k + 1] - c.h_cl_g0[k]);
-    // the closure keeps the old slot of every tile of the row's cluster as a 16-bit value in shared memory
-    if (c.cap > 32767 || closure_smem_bytes(&c) > (size_t)kMaxDynSmem) {
+    // the closure keeps a row's tile list and 16-bit slots in shared memory, and
+    // labels every unit of a cluster in one CTA
+    if (c.cap > 32767 || closure_smem_bytes(&c) > (size_t)kMaxDynSmem ||
+        closure_labels_smem_bytes(&c) > (size_t)kMaxDynSmem) {
         delete h;
         return SSCF_ERR_INVALID_ARG;
     }
@@ -837,7 +839,12 @@ int sscf_create(const sscf_system* sys, const sscf_params* prm, void* cuda_strea
         AL(c.d_c_tile[b], (size_t)c.n_mol * c.cap * 4);
         AL(c.d_c_val[b], (size_t)c.n_mol * c.cap * kTileVals * ts);
         AL(c.d_c_nz[b], (size_t)c.n_mol * c.cap);
-        if (b == 0) AL(c.d_unit_lab, (size_t)2 * c.n_groups * 4);
+        if (b == 0) {
+            AL(c.d_unit_lab, (size_t)2 * c.n_groups * 4);
+            AL(c.d_lab_start, (size_t)2 * c.n_groups * 4);
+            AL(c.d_lab_cnt, (size_t)2 * c.n_groups * 4);
+            AL(c.d_lab_mem, (size_t)2 * c.n_groups * 4);
+        }
     }
     AL(c.d_cci_ptr, (size_t)(c.n_tiles + 1) * 4);
     AL(c.d_cci_cnt, (size_t)c.n_tiles * 4);

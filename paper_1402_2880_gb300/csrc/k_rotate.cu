@@ -417,6 +417,9 @@ struct SweepArgs {
     const int* clblk_ptr;    // closure: blocks of the pass by cluster
     const int* clblk;
     const int* unit_lab;     // closure: component label of every unit (2 per group), cluster-local
+    int* lab_start;          // closure: per label, first entry of its members in lab_mem, and their count
+    int* lab_cnt;
+    int* lab_mem;            // closure: the units of every component, in increasing order
     const int* gnb_colour;   // closure: colour of every block ...
     int col_lo, col_hi;      // ... only blocks of colours [col_lo, col_hi) link units
     const int* gnb_row;
@@ -517,76 +520,144 @@ __global__ void __launch_bounds__(1024) k_closure_labels(SweepArgs a, int* __res
         if (!any) break;
     }
     for (int u = threadIdx.x; u < nu; u += blockDim.x) unit_lab[2 * g0 + u] = slab[u];
+    // The members of every component in increasing unit order (CSR by label):
+    // counts, an exclusive scan, then one warp places the units in order, the
+    // lanes of a group of 32 with equal labels taking consecutive entries.
+    int* cnt = slab + nu;
+    for (int u = threadIdx.x; u < nu; u += blockDim.x) cnt[u] = 0;
+    __syncthreads();
+    for (int u = threadIdx.x; u < nu; u += blockDim.x) atomicAdd(&cnt[slab[u]], 1);
+    __syncthreads();
+    __shared__ int part[1024];
+    const int per = (nu + blockDim.x - 1) / blockDim.x;
+    const int lo = threadIdx.x * per, hi = min(nu, lo + per);
+    int sum = 0;
+    for (int i = lo; i < hi; ++i) sum += cnt[i];
+    part[threadIdx.x] = sum;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int run = 0;
+        for (int i = 0; i < (int)blockDim.x; ++i) {
+            const int v = part[i];
+            part[i] = run;
+            run += v;
+        }
+    }
+    __syncthreads();
+    int run = part[threadIdx.x];
+    for (int i = lo; i < hi; ++i) {
+        const int c = cnt[i];
+        a.lab_start[2 * g0 + i] = run;
+        a.lab_cnt[2 * g0 + i] = c;
+        cnt[i] = run;   // from here on: the next free entry of label i
+        run += c;
+    }
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        const int lane = threadIdx.x;
+        for (int base = 0; base < nu; base += 32) {
+            const int u = base + lane;
+            const unsigned act = __ballot_sync(0xffffffffu, u < nu);
+            if (u < nu) {
+                const int l = slab[u];
+                const unsigned peers = __match_any_sync(act, l);
+                a.lab_mem[2 * g0 + cnt[l] + __popc(peers & ((1u << lane) - 1u))] = u;
+                __syncwarp(act);   // every peer has read cnt[l] before its first lane moves it
+                if (lane == __ffs(peers) - 1) cnt[l] += __popc(peers);
+            }
+            __syncwarp();
+        }
+    }
 }
 
+// Components with more members than this are marked by a whole warp.
+constexpr int kSmallComp = 8;
+constexpr int kBigMax = 64;   // large components listed per row (more: marked by their claimant)
 template <typename T>
 __global__ void __launch_bounds__(256) k_closure(SweepArgs a) {
     extern __shared__ __align__(16) unsigned char smraw[];
     if (*a.err & (kErrCapacity | kErrSortSize)) return;   // an earlier kernel of the step overflowed
-    // everything a row block touches belongs to its own cluster: group bits and
-    // the tile map are indexed inside the cluster's ranges
+    // everything a row block touches belongs to its own cluster: units and
+    // labels are indexed inside the cluster's ranges
     const int r = blockIdx.x;
     const int k = a.mol_cluster[r];
-    const int g0 = a.cl_g0[k], ng = a.cl_g0[k + 1] - g0;
-    const int ot0 = a.cl_ot0[k], not_ = a.cl_ot0[k + 1] - ot0;
-    const int vt0 = a.cl_vt0[k], nvt = a.cl_vt0[k + 1] - vt0;
-    const int gw = (a.max_cl_groups + 31) >> 5;
-    unsigned* occ = (unsigned*)smraw;
-    unsigned* vir = occ + gw;
-    unsigned* comp = vir + gw;                   // 2 gw words: components present in the row
-    short* map = (short*)(comp + 2 * gw);        // tiles of the cluster (occupied, then virtual): old slot or -1
-    auto lt = [&](int t) { return t < a.n_occ_tiles ? t - ot0 : not_ + (t - vt0); };
+    const int g0 = a.cl_g0[k], ng = a.cl_g0[k + 1] - g0, nu = 2 * ng;
+    const int uw = (2 * a.max_cl_groups + 31) >> 5;   // words of a bitset over a cluster's units
+    const int nw = (nu + 31) >> 5;
+    unsigned* present = (unsigned*)smraw;      // by label: components holding a nonzero tile of the row
+    unsigned* onu = present + uw;              // by unit: units of the new row
+    int* wpos = (int*)(onu + uw);              // per word of onu: its tile count, then its first slot
+    int* oldt = wpos + uw;                     // the row's tile ids (sorted)
+    short* oslot = (short*)(oldt + a.cap);     // per new slot: its slot in the row, or -1
+    __shared__ int s_big[kBigMax];
+    __shared__ int s_nbig;
     __shared__ int part[256];
     __shared__ int s_total;
-    for (int i = threadIdx.x; i < gw; i += blockDim.x) occ[i] = vir[i] = comp[i] = comp[gw + i] = 0u;
-    for (int i = threadIdx.x; i < not_ + nvt; i += blockDim.x) map[i] = -1;
-    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const int* lab = a.unit_lab + 2 * g0;
+    const int* lstart = a.lab_start + 2 * g0;
+    const int* lcnt = a.lab_cnt + 2 * g0;
+    const int* lmem = a.lab_mem + 2 * g0;
+    for (int i = threadIdx.x; i < nw; i += blockDim.x) present[i] = onu[i] = 0u;
+    if (threadIdx.x == 0) s_nbig = 0;
     const int n0 = a.in_nt[r];
-    for (int s = threadIdx.x; s < n0; s += blockDim.x) {
-        const int t = a.in_tile[(size_t)r * a.cap + s];
-        map[lt(t)] = (short)s;
-        // a tile flagged all-zero holds its place but cannot create fill
-        if (a.in_nz && !a.in_nz[(size_t)r * a.cap + s]) continue;
-        const int g = a.tile_group[t] - g0;
-        const unsigned bit = 1u << (g & 31);
-        if (a.mode == 1 && a.which == 0) {
-            atomicOr(&occ[g >> 5], bit);
-            atomicOr(&vir[g >> 5], bit);
-        } else if (a.tile_kind[t] == 0) {
-            atomicOr(&occ[g >> 5], bit);
-        } else {
-            atomicOr(&vir[g >> 5], bit);
-        }
-    }
+    for (int s = threadIdx.x; s < n0; s += blockDim.x) oldt[s] = a.in_tile[(size_t)r * a.cap + s];
     __syncthreads();
-    // the components that hold a unit of this row
-    for (int u = threadIdx.x; u < 2 * ng; u += blockDim.x) {
-        const int g = u < ng ? u : u - ng;
-        const bool has = ((u < ng ? occ[g >> 5] : vir[g >> 5]) >> (g & 31)) & 1u;
-        if (has) {
-            const int l = a.unit_lab[2 * g0 + u];
-            atomicOr(&comp[l >> 5], 1u << (l & 31));
+    auto mark = [&](int l, int j0, int dj) {
+        const int m0 = lstart[l], mn = lcnt[l];
+        for (int j = j0; j < mn; j += dj) {
+            const int m = lmem[m0 + j];
+            atomicOr(&onu[m >> 5], 1u << (m & 31));
         }
-    }
-    __syncthreads();
-    auto on = [&](int u) {
-        const int l = a.unit_lab[2 * g0 + u];
-        return ((comp[l >> 5] >> (l & 31)) & 1u) != 0u;
     };
-    // new sorted tile list: occupied units by group, then virtual units
-    const int per = (2 * ng + blockDim.x - 1) / blockDim.x;
-    const int u0 = threadIdx.x * per, u1 = min(2 * ng, u0 + per);
-    int cnt = 0;
-    for (int u = u0; u < u1; ++u) {
-        const int g = u < ng ? u : u - ng;
-        if (on(u)) cnt += u < ng ? a.group_not[g0 + g] : a.group_nvt[g0 + g];
+    // The row keeps every unit of every component that holds one of its
+    // nonzero tiles: a tile flagged all-zero keeps nothing and creates no fill.
+    // The first thread to claim a component marks its members (a large one is
+    // listed for a warp instead).
+    for (int s = threadIdx.x; s < n0; s += blockDim.x) {
+        if (a.in_nz && !a.in_nz[(size_t)r * a.cap + s]) continue;
+        const int t = oldt[s];
+        const int g = a.tile_group[t] - g0;
+        const int u = ((a.mode == 1 && a.which == 0) || a.tile_kind[t] == 0) ? g : ng + g;
+        const int l = lab[u];
+        const unsigned bit = 1u << (l & 31);
+        if (atomicOr(&present[l >> 5], bit) & bit) continue;
+        if (lcnt[l] > kSmallComp) {
+            const int i = atomicAdd(&s_nbig, 1);
+            if (i < kBigMax) {
+                s_big[i] = l;
+                continue;
+            }
+        }
+        mark(l, 0, 1);
     }
+    __syncthreads();
+    const int nbig = min(s_nbig, kBigMax);
+    for (int b = warp; b < nbig; b += nwarps) mark(s_big[b], lane, 32);
+    __syncthreads();
+    // tiles per word of the new unit set, then their first slots (units in
+    // order: occupied units by group, then virtual ones, i.e. tile ids ascending)
+    auto ntiles = [&](int u) { return u < ng ? a.group_not[g0 + u] : a.group_nvt[g0 + u - ng]; };
+    for (int w = threadIdx.x; w < nw; w += blockDim.x) {
+        unsigned b = onu[w];
+        int c = 0;
+        while (b) {
+            c += ntiles(32 * w + __ffs(b) - 1);
+            b &= b - 1;
+        }
+        wpos[w] = c;
+    }
+    __syncthreads();
+    const int per = (nw + blockDim.x - 1) / blockDim.x;
+    const int w0 = threadIdx.x * per, w1 = min(nw, w0 + per);
+    int cnt = 0;
+    for (int w = w0; w < w1; ++w) cnt += wpos[w];
     part[threadIdx.x] = cnt;
     __syncthreads();
     if (threadIdx.x == 0) {
         int run = 0;
         for (int i = 0; i < (int)blockDim.x; ++i) {
-            int v = part[i];
+            const int v = part[i];
             part[i] = run;
             run += v;
         }
@@ -598,33 +669,74 @@ __global__ void __launch_bounds__(256) k_closure(SweepArgs a) {
         if (threadIdx.x == 0) atomicOr(a.err, kErrCapacity);
         return;
     }
-    int pos = part[threadIdx.x];
-    for (int u = u0; u < u1; ++u) {
-        const int g = u < ng ? u : u - ng;
-        if (!on(u)) continue;
-        const int t0 = u < ng ? a.group_ot0[g0 + g] : a.group_vt0[g0 + g];
-        const int nt = u < ng ? a.group_not[g0 + g] : a.group_nvt[g0 + g];
-        for (int i = 0; i < nt; ++i) a.out_tile[(size_t)r * a.cap + pos++] = t0 + i;
+    {
+        int run = part[threadIdx.x];
+        for (int w = w0; w < w1; ++w) {
+            const int c = wpos[w];
+            wpos[w] = run;
+            run += c;
+        }
+    }
+    __syncthreads();
+    // the new row: tile ids, the slot each had in the row (binary search of the
+    // sorted old list), flags: tiles that were in the row survived the last
+    // compaction (or come from the guess or a restart) and may be nonzero;
+    // inserted tiles are zero
+    for (int w = threadIdx.x; w < nw; w += blockDim.x) {
+        unsigned b = onu[w];
+        int pos = wpos[w];
+        while (b) {
+            const int u = 32 * w + __ffs(b) - 1;
+            b &= b - 1;
+            const int g = u < ng ? u : u - ng;
+            const int t0 = u < ng ? a.group_ot0[g0 + g] : a.group_vt0[g0 + g];
+            const int nt = ntiles(u);
+            for (int i = 0; i < nt; ++i, ++pos) {
+                const int t = t0 + i;
+                int lo = 0, hi = n0;
+                while (lo < hi) {
+                    const int mid = (lo + hi) >> 1;
+                    if (oldt[mid] < t) lo = mid + 1;
+                    else hi = mid;
+                }
+                const int os = lo < n0 && oldt[lo] == t ? lo : -1;
+                a.out_tile[(size_t)r * a.cap + pos] = t;
+                oslot[pos] = (short)os;
+                a.out_nz[(size_t)r * a.cap + pos] = os < 0 ? 0 : (a.in_nz ? a.in_nz[(size_t)r * a.cap + os] : 1);
+            }
+        }
     }
     if (threadIdx.x == 0) a.out_nt[r] = n1;
     __syncthreads();
-    // tiles copied from the input survived the last compaction (or come from the
-    // guess or a restart) and may be nonzero; inserted tiles are zero
-    for (int s = threadIdx.x; s < n1; s += blockDim.x) {
-        const int os = map[lt(a.out_tile[(size_t)r * a.cap + s])];
-        a.out_nz[(size_t)r * a.cap + s] = os < 0 ? 0 : (a.in_nz ? a.in_nz[(size_t)r * a.cap + os] : 1);
-    }
-    const T* inv = (const T*)a.in_val;
-    T* outv = (T*)a.out_val;
+    // values, 16 bytes at a time
+    using V = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
+    constexpr int kVec = 16 / (int)sizeof(T);
+    constexpr int kPer = kTileVals / kVec;   // 16-byte pieces per tile
+    const V* inv = (const V*)a.in_val + (size_t)r * a.cap * kPer;
+    V* outv = (V*)a.out_val + (size_t)r * a.cap * kPer;
     const bool normalise = a.mode == 1 && a.normalise_pass && !(a.cl_eta[k] < a.tol);
-    for (int idx = threadIdx.x; idx < n1 * kTileVals; idx += blockDim.x) {
-        const int s = idx / kTileVals, e = idx % kTileVals, col = e & 15;
-        const int t = a.out_tile[(size_t)r * a.cap + s];
-        const int os = map[lt(t)];
-        T v = os >= 0 ? inv[((size_t)r * a.cap + os) * kTileVals + e] : (T)0;
-        if (normalise && os >= 0 && (a.which == 0 || a.tile_kind[t] == 0) && col < a.tile_nmo[t])
-            v = v / (T)a.dsc[a.tile_mo0[t] + col];
-        outv[((size_t)r * a.cap + s) * kTileVals + e] = v;
+    for (int idx = threadIdx.x; idx < n1 * kPer; idx += blockDim.x) {
+        const int s = idx / kPer, piece = idx - s * kPer;
+        const int os = oslot[s];
+        V v;
+        if (os >= 0) {
+            v = inv[(size_t)os * kPer + piece];
+            const int t = a.out_tile[(size_t)r * a.cap + s];
+            if (normalise && (a.which == 0 || a.tile_kind[t] == 0)) {
+                T* e = (T*)&v;
+                const int nmo = a.tile_nmo[t], mo0 = a.tile_mo0[t];
+#pragma unroll
+                for (int q = 0; q < kVec; ++q) {
+                    const int col = (piece * kVec + q) & 15;
+                    if (col < nmo) e[q] = e[q] / (T)a.dsc[mo0 + col];
+                }
+            }
+        } else {
+            T* e = (T*)&v;
+#pragma unroll
+            for (int q = 0; q < kVec; ++q) e[q] = (T)0;
+        }
+        outv[(size_t)s * kPer + piece] = v;
     }
 }
 
@@ -1401,8 +1513,11 @@ __global__ void __launch_bounds__(256) k_compact(int cap, const int* __restrict_
 }  // namespace
 
 size_t closure_smem_bytes(const Ctx* c) {
-    return (size_t)4 * ((c->max_cl_groups + 31) / 32) * 4 + (size_t)((c->max_cl_tiles + 1) & ~1) * 2 + 16;
+    const size_t uw = (size_t)(2 * c->max_cl_groups + 31) / 32;
+    return 3 * uw * 4 + (size_t)c->cap * 4 + (size_t)((c->cap + 1) & ~1) * 2 + 16;
 }
+
+size_t closure_labels_smem_bytes(const Ctx* c) { return (size_t)4 * c->max_cl_groups * 4; }
 
 // --------------------------------------------------------------------------
 // launchers
@@ -1544,7 +1659,10 @@ static cudaError_t closure_t(Ctx* c, int mode, int which, int col_lo, int col_hi
     if (smem > (size_t)kMaxDynSmem) return cudaErrorInvalidValue;
     cudaError_t e = cudaFuncSetAttribute(k_closure<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    const size_t lsmem = (size_t)2 * c->max_cl_groups * 4;
+    a.lab_start = c->d_lab_start;
+    a.lab_cnt = c->d_lab_cnt;
+    a.lab_mem = c->d_lab_mem;
+    const size_t lsmem = closure_labels_smem_bytes(c);
     if (lsmem > (size_t)kMaxDynSmem) return cudaErrorInvalidValue;
     e = cudaFuncSetAttribute(k_closure_labels, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lsmem);
     if (e != cudaSuccess) return e;

@@ -156,6 +156,9 @@ struct Ctx {
     int* d_clblk_ptr[2] = {nullptr, nullptr};   // blocks of every cluster: [0] all directed, [1] A <= B
     int* d_clblk[2] = {nullptr, nullptr};
     int* d_unit_lab = nullptr;        // 2 n_groups: closure component labels (cluster-local)
+    int* d_lab_start = nullptr;       // 2 n_groups each: members of every closure component (CSR by label)
+    int* d_lab_cnt = nullptr;
+    int* d_lab_mem = nullptr;
     int* d_cl_nmol = nullptr;
     int* d_group_cl = nullptr;        // cluster of every group
     void* d_cl_sel = nullptr;         // per-cluster top-k state (6 words each)
@@ -298,6 +301,7 @@ cudaError_t launch_ortho_prepare(Ctx* c, int which, double tol);
 // structural fill of the sweep's colours [col_lo, col_hi) (col_hi < 0: all); cur <- other
 cudaError_t launch_closure(Ctx* c, int mode, int which, int col_lo = 0, int col_hi = -1, bool first = true);
 size_t closure_smem_bytes(const Ctx* c);
+size_t closure_labels_smem_bytes(const Ctx* c);
 // mode 0 rotations, 1 combinations, colours [col_lo, col_hi) (col_hi < 0: all); in place
 cudaError_t launch_apply(Ctx* c, int mode, int which, int col_lo = 0, int col_hi = -1);
 cudaError_t launch_compact(Ctx* c);                      // drop all-zero tiles; cur <- other
