@@ -65,11 +65,18 @@ __global__ void k_ci_fill(int n_mol, int cap, const int* __restrict__ c_nt, cons
     }
 }
 
-// Sort every tile's segment by row (bitonic sort in shared memory).
-constexpr int kSortMax = 8192;
-__global__ void k_ci_sort(const int* __restrict__ ptr, int* __restrict__ row, int* __restrict__ slot,
-                          unsigned* __restrict__ err) {
-    extern __shared__ unsigned long long keys[];
+// Sort every tile's segment by row. The rows of one tile are distinct and lie
+// in its cluster, so a bitmap over the cluster's rows orders them: an entry
+// moves to the number of set bits below its row. One CTA per tile.
+constexpr int kSortMax = 8192;          // entries per tile (16 per thread)
+constexpr int kSortThreads = 512;
+__global__ void __launch_bounds__(kSortThreads) k_ci_sort(const int* __restrict__ ptr, int* __restrict__ row,
+                                                          int* __restrict__ slot, const int* __restrict__ tile_row0,
+                                                          int n_rows, unsigned* __restrict__ err) {
+    extern __shared__ unsigned sbits[];               // n_rows bits, then the set bits before each word
+    const int nw = (n_rows + 31) >> 5;
+    int* wpre = (int*)(sbits + nw);
+    __shared__ int part[kSortThreads];
     const int t = blockIdx.x;
     const int lo = ptr[t], n = ptr[t + 1] - lo;
     if (n <= 1) return;
@@ -77,30 +84,52 @@ __global__ void k_ci_sort(const int* __restrict__ ptr, int* __restrict__ row, in
         if (threadIdx.x == 0) atomicOr(err, kErrSortSize);
         return;
     }
-    int np = 1;
-    while (np < n) np <<= 1;
-    for (int i = threadIdx.x; i < np; i += blockDim.x)
-        keys[i] = i < n ? ((unsigned long long)(unsigned)row[lo + i] << 32) | (unsigned)slot[lo + i]
-                        : ~0ull;
+    const int r0 = tile_row0[t];
+    for (int w = threadIdx.x; w < nw; w += blockDim.x) sbits[w] = 0u;
     __syncthreads();
-    for (int k = 2; k <= np; k <<= 1)
-        for (int j = k >> 1; j > 0; j >>= 1) {
-            for (int i = threadIdx.x; i < np; i += blockDim.x) {
-                int l = i ^ j;
-                if (l > i) {
-                    bool up = (i & k) == 0;
-                    unsigned long long a = keys[i], b = keys[l];
-                    if ((a > b) == up) {
-                        keys[i] = b;
-                        keys[l] = a;
-                    }
-                }
-            }
-            __syncthreads();
+    constexpr int kPer = kSortMax / kSortThreads;
+    int rv[kPer], sv[kPer];
+#pragma unroll
+    for (int j = 0; j < kPer; ++j) {
+        const int i = threadIdx.x + j * kSortThreads;
+        if (i < n) {
+            rv[j] = row[lo + i];
+            sv[j] = slot[lo + i];
+            const int rr = rv[j] - r0;
+            atomicOr(&sbits[rr >> 5], 1u << (rr & 31));
         }
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
-        row[lo + i] = (int)(keys[i] >> 32);
-        slot[lo + i] = (int)(keys[i] & 0xffffffffu);
+    }
+    __syncthreads();
+    const int per = (nw + blockDim.x - 1) / blockDim.x;
+    const int w0 = threadIdx.x * per, w1 = min(nw, w0 + per);
+    int c = 0;
+    for (int w = w0; w < w1; ++w) c += __popc(sbits[w]);
+    part[threadIdx.x] = c;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int run = 0;
+        for (int i = 0; i < (int)blockDim.x; ++i) {
+            const int v = part[i];
+            part[i] = run;
+            run += v;
+        }
+    }
+    __syncthreads();
+    int run = part[threadIdx.x];
+    for (int w = w0; w < w1; ++w) {
+        wpre[w] = run;
+        run += __popc(sbits[w]);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < kPer; ++j) {
+        const int i = threadIdx.x + j * kSortThreads;
+        if (i < n) {
+            const int rr = rv[j] - r0;
+            const int pos = wpre[rr >> 5] + __popc(sbits[rr >> 5] & ((1u << (rr & 31)) - 1u));
+            row[lo + pos] = rv[j];
+            slot[lo + pos] = sv[j];
+        }
     }
 }
 
@@ -691,8 +720,9 @@ cudaError_t launch_colindex(Ctx* c) {
     cudaMemsetAsync(c->d_cci_cnt, 0, (size_t)c->n_tiles * 4, c->stream);
     k_ci_fill<<<c->n_mol, 128, 0, c->stream>>>(c->n_mol, c->cap, c->d_c_nt[b], c->d_c_tile[b], c->d_cci_ptr,
                                                c->d_cci_cnt, c->d_cci_row, c->d_cci_slot);
-    k_ci_sort<<<c->n_tiles, 512, kSortMax * 8, c->stream>>>(c->d_cci_ptr, c->d_cci_row, c->d_cci_slot,
-                                                            &c->d_sc->err);
+    const size_t ssmem = (size_t)2 * ((c->max_cl_mol + 31) / 32) * 4;
+    k_ci_sort<<<c->n_tiles, kSortThreads, ssmem, c->stream>>>(c->d_cci_ptr, c->d_cci_row, c->d_cci_slot,
+                                                              c->d_tile_row0, c->max_cl_mol, &c->d_sc->err);
     return cudaGetLastError();
 }
 
@@ -701,8 +731,6 @@ static bool g_attr_done[64] = {false};   // per device: function attributes are 
 template <typename T>
 static cudaError_t set_attrs() {
     cudaError_t e;
-    e = cudaFuncSetAttribute(k_ci_sort, cudaFuncAttributeMaxDynamicSharedMemorySize, kSortMax * 8);
-    if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(k_xc<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(k_transform<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
