@@ -1045,7 +1045,7 @@ int sscf_get_density_blocks(sscf_ctx* h, double* P) {
 
 static int rotate_sweep_async(Ctx& c) {
     PK("colindex", launch_colindex(&c));
-    PK("xc_h", launch_xc(&c, true, 0, c.n_tiles));
+    PK("xc_h", launch_xc_rot(&c));
     PK("transform_ov", launch_transform_rot(&c));
     PK("select_rot", launch_select_rot(&c));
     if (c.closure_window > 0) {
@@ -1085,7 +1085,7 @@ int sscf_autotune(sscf_ctx* h, int* tf_split_out) {
     // inputs of the occupied-virtual transform for the current state
     CK(launch_build_h(&c, c.prm.eps));
     CK(launch_colindex(&c));
-    CK(launch_xc(&c, true, 0, c.n_tiles));
+    CK(launch_xc_rot(&c));
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));

@@ -141,7 +141,7 @@ __global__ void __launch_bounds__(kSortThreads) k_ci_sort(const int* __restrict_
 // ---------------------------------------------------------------------------
 constexpr int kXcBatch = 4;   // matched neighbours whose loads are in flight together
 template <typename T>
-__global__ void k_xc(int tile_lo, int n_rows, int cap, int capY, const int* __restrict__ tile_row0,
+__global__ void k_xc(int tile_lo, int n_rows, int own_below, int cap, int capY, const int* __restrict__ tile_row0,
                      const int* __restrict__ cci_ptr, const int* __restrict__ cci_row,
                      const int* __restrict__ cci_slot, const T* __restrict__ c_val, const int* __restrict__ mp_ptr,
                      const int* __restrict__ mp_col, const T* __restrict__ Xb, int* __restrict__ y_n,
@@ -153,7 +153,8 @@ __global__ void k_xc(int tile_lo, int n_rows, int cap, int capY, const int* __re
     int* wpre = (int*)(bits + nw);                // prefix of popcounts per word
     short* rowpos = (short*)(wpre + nw);          // n_rows: index into the tile's column list or -1
     __shared__ int s_total;
-    const int t = tile_lo + blockIdx.x;
+    // tiles from own_below on (the longer ones: every reachable row) first
+    const int t = tile_lo + (int)((blockIdx.x + (unsigned)max(own_below - tile_lo, 0)) % gridDim.x);
     const int r0 = tile_row0[t];
     const int lo = cci_ptr[t], nc = cci_ptr[t + 1] - lo;
     if (nc > 32767) {   // the 16-bit row map cannot index this column
@@ -169,6 +170,11 @@ __global__ void k_xc(int tile_lo, int n_rows, int cap, int capY, const int* __re
     for (int k = threadIdx.x; k < nc; k += blockDim.x) rowpos[cci_row[lo + k] - r0] = (short)k;
     for (int k = threadIdx.x; k < nc; k += blockDim.x) {
         int r = cci_row[lo + k];
+        if (t < own_below) {   // Y only where C[:, t] has rows: enough for C[:, t]^T Y[:, t]
+            const int n = r - r0;
+            atomicOr(&bits[n >> 5], 1u << (n & 31));
+            continue;
+        }
         for (int e = mp_ptr[r]; e < mp_ptr[r + 1]; ++e) {
             int n = mp_col[e] - r0;
             atomicOr(&bits[n >> 5], 1u << (n & 31));
@@ -753,7 +759,7 @@ static cudaError_t ensure_attrs() {
     return e;
 }
 
-cudaError_t launch_xc(Ctx* c, bool use_h, int tile_lo, int tile_hi) {
+cudaError_t launch_xc(Ctx* c, bool use_h, int tile_lo, int tile_hi, int own_below) {
     c->n_launch += 1;
     cudaError_t e = ensure_attrs();
     if (e != cudaSuccess) return e;
@@ -764,16 +770,23 @@ cudaError_t launch_xc(Ctx* c, bool use_h, int tile_lo, int tile_hi) {
     const size_t smem = (size_t)((nr + 31) / 32) * 8 + (size_t)nr * 2 + 64;
     if (smem > 200 * 1024) return cudaErrorInvalidValue;
     if (c->prec == SSCF_FP64)
-        k_xc<double><<<n, 256, smem, c->stream>>>(tile_lo, nr, c->cap, c->capY, c->d_tile_row0, c->d_cci_ptr, c->d_cci_row,
+        k_xc<double><<<n, 256, smem, c->stream>>>(tile_lo, nr, own_below, c->cap, c->capY, c->d_tile_row0, c->d_cci_ptr, c->d_cci_row,
                                                   c->d_cci_slot, (const double*)c->d_c_val[b], c->d_mp_ptr,
                                                   c->d_mp_col, (const double*)(use_h ? c->d_Hb : c->d_Sbt),
                                                   c->d_y_n, c->d_y_row, (double*)c->d_y_val, &c->d_sc->err);
     else
-        k_xc<float><<<n, 256, smem, c->stream>>>(tile_lo, nr, c->cap, c->capY, c->d_tile_row0, c->d_cci_ptr, c->d_cci_row,
+        k_xc<float><<<n, 256, smem, c->stream>>>(tile_lo, nr, own_below, c->cap, c->capY, c->d_tile_row0, c->d_cci_ptr, c->d_cci_row,
                                                  c->d_cci_slot, (const float*)c->d_c_val[b], c->d_mp_ptr,
                                                  c->d_mp_col, (const float*)(use_h ? c->d_Hb : c->d_Sbt),
                                                  c->d_y_n, c->d_y_row, (float*)c->d_y_val, &c->d_sc->err);
     return cudaGetLastError();
+}
+
+cudaError_t launch_xc_rot(Ctx* c) {
+    // the occupied tiles enter the rotation transform only through their
+    // diagonal tile pairs C[:, a]^T H C[:, a], whose sum runs over a's rows
+    // (one launch for all tiles keeps the CTAs of both kinds in one grid)
+    return launch_xc(c, true, 0, c->n_tiles, c->n_occ_tiles);
 }
 
 template <typename T>

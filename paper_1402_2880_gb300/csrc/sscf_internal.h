@@ -291,7 +291,12 @@ cudaError_t launch_build_h(Ctx* c, double eps_threshold);
 cudaError_t launch_guess(Ctx* c);
 // sparse structure and products
 cudaError_t launch_colindex(Ctx* c);
-cudaError_t launch_xc(Ctx* c, bool use_h, int tile_lo, int tile_hi);
+// Y = X C for tiles [tile_lo, tile_hi) on the row blocks reachable from each
+// tile's rows; tiles below own_below on their own rows only
+cudaError_t launch_xc(Ctx* c, bool use_h, int tile_lo, int tile_hi, int own_below = 0);
+// Y = H C for the transform of a sweep: virtual tiles on every reachable row
+// block (F_ov), occupied tiles on their own rows (only their diagonal blocks)
+cudaError_t launch_xc_rot(Ctx* c);
 cudaError_t launch_transform_rot(Ctx* c);
 cudaError_t launch_transform_ortho(Ctx* c, int which);
 cudaError_t launch_density(Ctx* c, double* P_out = nullptr);   // P blocks (n_mp x 36) too, if not NULL
