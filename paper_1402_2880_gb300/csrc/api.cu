@@ -720,6 +720,14 @@ int sscf_create(const sscf_system* sys, const sscf_params* prm, void* cuda_strea
         for (int m = 0; m < c.n_mol; ++m)
             for (int k = c.h_mp_ptr[m]; k < c.h_mp_ptr[m + 1]; ++k) row[k] = m;
         UP(c.d_mp_row, row);
+        std::vector<int> rev(c.n_mp);
+        for (int m = 0; m < c.n_mol; ++m)
+            for (int k = c.h_mp_ptr[m]; k < c.h_mp_ptr[m + 1]; ++k) {
+                const int n = c.h_mp_col[k];
+                const auto b = c.h_mp_col.begin();
+                rev[k] = (int)(std::lower_bound(b + c.h_mp_ptr[n], b + c.h_mp_ptr[n + 1], m) - b);
+            }
+        UP(c.d_mp_rev, rev);
     }
     UP(c.d_mol_group, c.h_mol_group);
     UP(c.d_mol_local, c.h_mol_local);
@@ -832,6 +840,7 @@ int sscf_create(const sscf_system* sys, const sscf_params* prm, void* cuda_strea
     } while (0)
     AL(c.d_H0b, (size_t)c.n_mp * 36 * 8);
     AL(c.d_Sb, (size_t)c.n_mp * 36 * 8);
+    AL(c.d_dens_part, (size_t)c.n_mp * 4 * 8);
     AL(c.d_Hb, (size_t)c.n_mp * 36 * ts);
     AL(c.d_Sbt, (size_t)c.n_mp * 36 * ts);
     for (int b = 0; b < 2; ++b) {

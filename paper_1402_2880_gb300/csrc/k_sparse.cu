@@ -564,18 +564,24 @@ __global__ void __launch_bounds__(kDensWarps * 32, kDensMinBlocks)
 k_density(int n_occ_tiles, int map_n, const int* __restrict__ mol_ot0, int cap, const int* __restrict__ c_nt,
           const int* __restrict__ c_tile, const T* __restrict__ c_val, const int* __restrict__ mp_ptr,
           const int* __restrict__ mp_col, const double* __restrict__ H0b, const double* __restrict__ Sb,
-          double* __restrict__ q, double* __restrict__ e_mol, double* __restrict__ P_out) {
+          const int* __restrict__ mp_rev, double2* __restrict__ dpart, double* __restrict__ P_out) {
     // slot of every occupied tile of m's cluster in row m, or -1 (map_n = largest cluster);
     // then, in mixed precision, the FP64 sums of each lane's 36 products (flushed
     // from FP32 every kDensFlush tiles), kept in shared memory to save registers
     extern __shared__ int smap[];
     constexpr bool kSplit = !std::is_same<typename Acc<T>::type, double>::value;
     double* sacc = (double*)(smap + ((map_n + 1) & ~1));   // [warp][36][32]: per-lane FP64 sums
-    __shared__ double part[kDensWarps][4];
     const int m = blockIdx.x;
     const int t0 = mol_ot0[m];
+    // P_nm = P_mn^T: this CTA takes the pairs with n >= m (neighbour lists are
+    // sorted) and hands each pair's share of the charges and of the band
+    // energy to both rows
+    __shared__ int s_jlo;
+    if (threadIdx.x == 0) s_jlo = 0;
     for (int i = threadIdx.x; i < map_n; i += blockDim.x) smap[i] = -1;
     __syncthreads();
+    for (int w = threadIdx.x; w < mp_ptr[m + 1] - mp_ptr[m]; w += blockDim.x)
+        if (mp_col[mp_ptr[m] + w] < m) atomicAdd(&s_jlo, 1);
     const int ntm = c_nt[m];
     for (int s = threadIdx.x; s < ntm; s += blockDim.x) {
         int t = c_tile[(size_t)m * cap + s];
@@ -586,8 +592,7 @@ k_density(int n_occ_tiles, int map_n, const int* __restrict__ mol_ot0, int cap, 
     const int e0 = mp_ptr[m], ne = mp_ptr[m + 1] - e0;
     using A = typename Acc<T>::type;
     const int col = lane & 15, half = lane >> 4;
-    double wq[3] = {0, 0, 0}, we = 0.0;
-    for (int w = warp; w < ne; w += kDensWarps) {
+    for (int w = s_jlo + warp; w < ne; w += kDensWarps) {
         const int e = e0 + w;
         const int n = mp_col[e];
         A acc[36];
@@ -664,48 +669,69 @@ k_density(int n_occ_tiles, int map_n, const int* __restrict__ mol_ot0, int cap, 
 #pragma unroll
         for (int u = 0; u < 36; ++u) wacc[u * 32] = flushed ? wacc[u * 32] + (double)acc[u] : (double)acc[u];
         __syncwarp();
-        double qa[3] = {0, 0, 0}, eb = 0.0;
+        // row sums of P o S by the atoms of m, column sums by the atoms of n
+        // (AOs: O s, p, p, p, then H1 s, H2 s), and sum P o H0
+        const bool self = n == m;
+        const int er = self ? e : mp_rev[e];
+        double qr[3] = {0, 0, 0}, qc[3] = {0, 0, 0}, eb = 0.0;
         for (int u = lane; u < 36; u += 32) {
             const double* row = sacc + ((size_t)warp * 36 + u) * 32;
             double v = 0.0;
             for (int j = 0; j < 32; ++j) v += row[(j + lane) & 31];
             const double P = 2.0 * v;
-            if (P_out) P_out[(size_t)e * 36 + u] = P;
-            const int k = u / 6;   // AO of m: O s, p, p, p, then H1 s, H2 s
+            const int k = u / 6, l = u - 6 * k;   // AO of m, AO of n
+            if (P_out) {
+                P_out[(size_t)e * 36 + u] = P;
+                if (!self) P_out[(size_t)er * 36 + l * 6 + k] = P;
+            }
             const double pq = P * Sb[(size_t)e * 36 + u];
-            qa[0] += k < 4 ? pq : 0.0;
-            qa[1] += k == 4 ? pq : 0.0;
-            qa[2] += k == 5 ? pq : 0.0;
+            qr[0] += k < 4 ? pq : 0.0;
+            qr[1] += k == 4 ? pq : 0.0;
+            qr[2] += k == 5 ? pq : 0.0;
+            qc[0] += l < 4 ? pq : 0.0;
+            qc[1] += l == 4 ? pq : 0.0;
+            qc[2] += l == 5 ? pq : 0.0;
             eb += P * H0b[(size_t)e * 36 + u];
         }
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) {
-            qa[0] += __shfl_xor_sync(0xffffffffu, qa[0], off);
-            qa[1] += __shfl_xor_sync(0xffffffffu, qa[1], off);
-            qa[2] += __shfl_xor_sync(0xffffffffu, qa[2], off);
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                qr[i] += __shfl_xor_sync(0xffffffffu, qr[i], off);
+                qc[i] += __shfl_xor_sync(0xffffffffu, qc[i], off);
+            }
             eb += __shfl_xor_sync(0xffffffffu, eb, off);
         }
         __syncwarp();
-        wq[0] += qa[0];
-        wq[1] += qa[1];
-        wq[2] += qa[2];
-        we += eb;
+        if (lane == 0) {
+            dpart[2 * (size_t)e] = make_double2(qr[0], qr[1]);
+            dpart[2 * (size_t)e + 1] = make_double2(qr[2], eb);
+            if (!self) {
+                dpart[2 * (size_t)er] = make_double2(qc[0], qc[1]);
+                dpart[2 * (size_t)er + 1] = make_double2(qc[2], eb);
+            }
+        }
     }
-    if (lane == 0) {
-        part[warp][0] = wq[0];
-        part[warp][1] = wq[1];
-        part[warp][2] = wq[2];
-        part[warp][3] = we;
+}
+
+// q and the band energy of every molecule: its pairs' shares summed in
+// neighbour order
+__global__ void k_density_sum(int n_mol, const int* __restrict__ mp_ptr, const double2* __restrict__ dpart,
+                              double* __restrict__ q, double* __restrict__ e_mol) {
+    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= n_mol) return;
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+    for (int e = mp_ptr[m]; e < mp_ptr[m + 1]; ++e) {
+        const double2 a = dpart[2 * (size_t)e], b = dpart[2 * (size_t)e + 1];
+        s0 += a.x;
+        s1 += a.y;
+        s2 += b.x;
+        s3 += b.y;
     }
-    __syncthreads();
-    if (threadIdx.x < 4) {
-        double s = 0.0;
-        for (int w = 0; w < kDensWarps; ++w) s += part[w][threadIdx.x];
-        if (threadIdx.x < 3)
-            q[3 * m + threadIdx.x] = s;
-        else
-            e_mol[m] = s;
-    }
+    q[3 * m] = s0;
+    q[3 * m + 1] = s1;
+    q[3 * m + 2] = s2;
+    e_mol[m] = s3;
 }
 
 }  // namespace
@@ -835,20 +861,22 @@ cudaError_t launch_transform_ortho(Ctx* c, int w) {
 }
 
 cudaError_t launch_density(Ctx* c, double* P_out) {
-    c->n_launch += 1;
+    c->n_launch += 2;
     cudaError_t e = ensure_attrs();
     if (e != cudaSuccess) return e;
     const size_t smem = (size_t)((c->max_cl_otiles + 1) & ~1) * 4 + (size_t)kDensWarps * 36 * 32 * 8;
     if (smem > 200 * 1024) return cudaErrorInvalidValue;
     const int b = c->cur;
+    double2* dpart = (double2*)c->d_dens_part;
     if (c->prec == SSCF_FP64)
-        k_density<double><<<c->n_mol, kDensWarps * 32, smem, c->stream>>>(c->n_occ_tiles, c->max_cl_otiles, c->d_mol_ot0, c->cap, c->d_c_nt[b], c->d_c_tile[b],
-                                                              (const double*)c->d_c_val[b], c->d_mp_ptr,
-                                                              c->d_mp_col, c->d_H0b, c->d_Sb, c->d_q, c->d_e_mol, P_out);
+        k_density<double><<<c->n_mol, kDensWarps * 32, smem, c->stream>>>(
+            c->n_occ_tiles, c->max_cl_otiles, c->d_mol_ot0, c->cap, c->d_c_nt[b], c->d_c_tile[b],
+            (const double*)c->d_c_val[b], c->d_mp_ptr, c->d_mp_col, c->d_H0b, c->d_Sb, c->d_mp_rev, dpart, P_out);
     else
-        k_density<float><<<c->n_mol, kDensWarps * 32, smem, c->stream>>>(c->n_occ_tiles, c->max_cl_otiles, c->d_mol_ot0, c->cap, c->d_c_nt[b], c->d_c_tile[b],
-                                                             (const float*)c->d_c_val[b], c->d_mp_ptr, c->d_mp_col,
-                                                             c->d_H0b, c->d_Sb, c->d_q, c->d_e_mol, P_out);
+        k_density<float><<<c->n_mol, kDensWarps * 32, smem, c->stream>>>(
+            c->n_occ_tiles, c->max_cl_otiles, c->d_mol_ot0, c->cap, c->d_c_nt[b], c->d_c_tile[b],
+            (const float*)c->d_c_val[b], c->d_mp_ptr, c->d_mp_col, c->d_H0b, c->d_Sb, c->d_mp_rev, dpart, P_out);
+    k_density_sum<<<(c->n_mol + 127) / 128, 128, 0, c->stream>>>(c->n_mol, c->d_mp_ptr, dpart, c->d_q, c->d_e_mol);
     return cudaGetLastError();
 }
 

@@ -124,6 +124,8 @@ struct Ctx {
     int* d_species = nullptr;
     int* d_mp_ptr = nullptr;
     int* d_mp_col = nullptr;
+    int* d_mp_rev = nullptr;          // n_mp: the entry of (n, m) for the entry of (m, n)
+    double* d_dens_part = nullptr;    // n_mp x 4: a pair's share of q (3 atoms) and band energy for its first row
     int* d_mp_row = nullptr;
     double* d_H0b = nullptr;
     double* d_Sb = nullptr;
