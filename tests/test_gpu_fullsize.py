@@ -22,6 +22,7 @@ FP64 flush, so a contraction differs from the FP64 one on the same stored
 values by at most about 64 * 2^-24 times the sum of the absolute terms; the
 tests allow 256 * 2^-24 of that sum.
 """
+import ctypes
 import functools
 
 import numpy as np
@@ -190,6 +191,12 @@ def test_transform_entries_sampled():
     mn, Hb, _, _ = ctx.get_blocks()
     ref = Co.T @ apply_blocks(mn, Hb, Cv)
     bound = np.abs(Co).T @ apply_blocks(mn, np.abs(Hb), np.abs(Cv))
+    # diag(F) of the same MOs: c_i^T H c_i (occupied tiles enter the transform
+    # only through their diagonal tile pairs, whose Y = H C covers their own rows)
+    dref = np.concatenate([np.einsum("ri,ri->i", Co, apply_blocks(mn, Hb, Co)),
+                           np.einsum("ri,ri->i", Cv, apply_blocks(mn, Hb, Cv))])
+    dbound = np.concatenate([np.einsum("ri,ri->i", np.abs(Co), apply_blocks(mn, np.abs(Hb), np.abs(Co))),
+                             np.einsum("ri,ri->i", np.abs(Cv), apply_blocks(mn, np.abs(Hb), np.abs(Cv)))])
     n_rot, max_fov = ctx.rotate_sweep()
     ii, jj = np.meshgrid(occ, vir, indexing="ij")
     F = ctx.get_F_entries(ii.ravel(), jj.ravel()).reshape(ii.shape)
@@ -198,6 +205,13 @@ def test_transform_entries_sampled():
     assert np.all(np.abs(F - want) <= K_ACC * bound + 1e-12)
     assert mask.sum() > 1000
     assert max_fov >= np.abs(F).max() and n_rot > 0
+    d = np.empty(ctx.n_mo)
+    assert ctx.lib.sscf_get_F_dense(ctx.h, None, d.ctypes.data_as(ctypes.POINTER(ctypes.c_double))) == 0
+    got = d[np.concatenate([occ, vir])]
+    assert np.all(np.abs(got - dref) <= K_ACC * dbound + 1e-12)
+    # rows holding none of the sampled occupied MOs exist: the diagonal pairs
+    # are checked on MOs that do not cover the cluster
+    assert (np.abs(Co).sum(axis=1) == 0).any()
 
 
 def test_mulliken_sampled_after_full_step():
