@@ -170,6 +170,10 @@ __global__ void k_rot_lists(int n_gnb, const int* __restrict__ gnb_row, const in
     const int no = 4 * group_nmol[A], nv = 2 * group_nmol[B], nvt = group_nvt[B];
     const int nsub = max(no, nv);
     const unsigned long long thr = cl[group_cl[A]].thr;
+    __shared__ int s_touch;
+    if (threadIdx.x == 0) s_touch = 0;
+    __syncthreads();
+    int touch_t = 0;   // side tiles this thread's kept pairs touch: bits 0-2 side A, 3-5 side B
     for (int p = threadIdx.x; p < 32 * 16; p += blockDim.x) {
         int i = p >> 4, j = p & 15;
         unsigned char kp = 0;
@@ -177,9 +181,11 @@ __global__ void k_rot_lists(int n_gnb, const int* __restrict__ gnb_row, const in
             const int tp = blk_tp0[e] + (i >> 4) * nvt + (j >> 4);
             const double f = fabs((double)F[(size_t)tp * 256 + (i & 15) * 16 + (j & 15)]);
             kp = (f >= tau && f > 0.0 && dkey(f) >= thr) ? 1 : 0;
+            if (kp) touch_t |= (1 << (i >> 4)) | (1 << (3 + (j >> 4)));
         }
         keep[p] = kp;
     }
+    if (touch_t) atomicOr(&s_touch, touch_t);
     __syncthreads();
     if ((int)threadIdx.x < nsub) {
         const int s = threadIdx.x;
@@ -202,11 +208,7 @@ __global__ void k_rot_lists(int n_gnb, const int* __restrict__ gnb_row, const in
         pr_n[e] = run;
         cnt[kMaxSub] = run;
         if (run) atomicAdd(&sc->n_rot, (unsigned long long)run);
-        int touch = 0;
-        for (int i = 0; i < no; ++i)
-            for (int j = 0; j < nv; ++j)
-                if (keep[i * 16 + j]) touch |= (1 << (i >> 4)) | (1 << (3 + (j >> 4)));
-        pr_touch[e] = touch;
+        pr_touch[e] = s_touch;
     }
     __syncthreads();
     if ((int)threadIdx.x < nsub) {
@@ -316,6 +318,7 @@ __global__ void k_ortho_lists(int w, double tol, const int* __restrict__ oblk, c
                               int* __restrict__ pr_n, int* __restrict__ pr_lvl, uint16_t* __restrict__ pr_ij,
                               T* __restrict__ pr_cs, int* __restrict__ pr_touch) {
     __shared__ unsigned char keep[48 * 48];
+    __shared__ double s_sh[48 * 48];   // the normalised overlap of every kept pair
     __shared__ int cnt[kMaxSub + 1];
     const int e = oblk[blockIdx.x];
     const int A = gnb_row[e], B = gnb_col[e];
@@ -326,6 +329,10 @@ __global__ void k_ortho_lists(int w, double tol, const int* __restrict__ oblk, c
     const double eta = cl_eta[group_cl[A]];   // threshold of the block's own cluster
     const bool active = !(eta < tol);
     const double cut = 1e-3 * eta;
+    __shared__ int s_touch;
+    if (threadIdx.x == 0) s_touch = 0;
+    __syncthreads();
+    int touch_t = 0;   // side tiles this thread's kept pairs touch: bits 0-2 side A, 3-5 side B
     for (int p = threadIdx.x; p < 48 * 48; p += blockDim.x) {
         const int i = p / 48, j = p % 48;
         unsigned char kp = 0;
@@ -334,10 +341,16 @@ __global__ void k_ortho_lists(int w, double tol, const int* __restrict__ oblk, c
             side_pos(i, noA, group_not[A], ia, ci);
             side_pos(j, noB, group_not[B], ib, cj);
             const double di = dsc[pass_mo(i, noA, occ0, virt0, A)], dj = dsc[pass_mo(j, noB, occ0, virt0, B)];
-            kp = fabs(sig_hat(sig, blk_tp, e, same, ia, ib, ci, cj, di, dj)) >= cut ? 1 : 0;
+            const double sh = sig_hat(sig, blk_tp, e, same, ia, ib, ci, cj, di, dj);
+            kp = fabs(sh) >= cut ? 1 : 0;
+            if (kp) {
+                touch_t |= (1 << ia) | (1 << (3 + ib));
+                s_sh[p] = sh;
+            }
         }
         keep[p] = kp;
     }
+    if (touch_t) atomicOr(&s_touch, touch_t);
     __syncthreads();
     if ((int)threadIdx.x < nsub) {
         const int s = threadIdx.x;
@@ -359,16 +372,7 @@ __global__ void k_ortho_lists(int w, double tol, const int* __restrict__ oblk, c
         for (int s = nsub; s <= kMaxSub; ++s) lvl[s] = run;
         pr_n[e] = run;
         if (run) atomicAdd(&sc->n_combo, (unsigned long long)run);
-        int touch = 0;
-        for (int i = 0; i < nA; ++i)
-            for (int j = 0; j < nB; ++j)
-                if (keep[i * 48 + j]) {
-                    int ia, ci, ib, cj;
-                    side_pos(i, noA, group_not[A], ia, ci);
-                    side_pos(j, noB, group_not[B], ib, cj);
-                    touch |= (1 << ia) | (1 << (3 + ib));
-                }
-        pr_touch[e] = touch;
+        pr_touch[e] = s_touch;
     }
     __syncthreads();
     if ((int)threadIdx.x < nsub) {
@@ -377,11 +381,7 @@ __global__ void k_ortho_lists(int w, double tol, const int* __restrict__ oblk, c
         for (int i = 0; i < nA; ++i) {
             int j = ((s - i) % nsub + nsub) % nsub;
             if (!(j < nB && keep[i * 48 + j])) continue;
-            int ia, ci, ib, cj;
-            side_pos(i, noA, group_not[A], ia, ci);
-            side_pos(j, noB, group_not[B], ib, cj);
-            const double di = dsc[pass_mo(i, noA, occ0, virt0, A)], dj = dsc[pass_mo(j, noB, occ0, virt0, B)];
-            const double sh = sig_hat(sig, blk_tp, e, same, ia, ib, ci, cj, di, dj);
+            const double sh = s_sh[i * 48 + j];
             const size_t q = (size_t)e * kOrthoCap + pos;
             pr_ij[q] = (uint16_t)(i | (j << 8));
             pr_cs[2 * q] = (T)__dmul_rn(0.5, sh);
