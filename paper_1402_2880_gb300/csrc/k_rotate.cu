@@ -899,6 +899,13 @@ __global__ void __launch_bounds__(apply_threads<T>()) k_apply_colour(SweepArgs a
         }
         s_cp[p] = tile >= 0 ? a.cci_ptr[tile] : -1;
     }
+    __syncthreads();
+    // a chunk whose held tiles are all flagged zero in all its rows stays as it
+    // is (the updates of zeros are zeros): nothing to load, update or store
+    bool work = false;
+    for (int t = threadIdx.x; t < nk; t += blockDim.x)
+        for (int p = 0; p < NT; ++p) work |= s_cp[p] >= 0 && a.col_nz[s_cp[p] + k0 + t];
+    if (!__syncthreads_or(work)) return;
     const int* lvl = a.pr_lvl + (size_t)e * (kMaxSub + 1);
     for (int i = threadIdx.x; i <= kMaxSub; i += blockDim.x) s_lvl[i] = lvl[i];
     const T* cs = (const T*)a.pr_cs + (size_t)e * kOrthoCap * 2;
