@@ -726,6 +726,8 @@ int sscf_create(const sscf_system* sys, const sscf_params* prm, void* cuda_strea
                 const int n = c.h_mp_col[k];
                 const auto b = c.h_mp_col.begin();
                 rev[k] = (int)(std::lower_bound(b + c.h_mp_ptr[n], b + c.h_mp_ptr[n + 1], m) - b);
+                // the pattern is symmetric (a distance test on both orders of the pair)
+                if (rev[k] >= c.h_mp_ptr[n + 1] || c.h_mp_col[rev[k]] != m) return fail(SSCF_ERR_INVALID_ARG);
             }
         UP(c.d_mp_rev, rev);
     }
