@@ -136,8 +136,9 @@ __global__ void __launch_bounds__(kSortThreads) k_ci_sort(const int* __restrict_
 // ---------------------------------------------------------------------------
 // Y[:, t] = X C[:, t] for tiles t in [tile_lo, tile_hi), column-major output.
 // One CTA per tile: mark the row blocks reachable from the tile's rows
-// through the molecule-pair pattern, then one warp per output row block sums
-// X[r, n] (6x6) C[n, t] (6x16) over the pattern neighbours n holding t.
+// through the molecule-pair pattern (tiles below own_below: the tile's own
+// rows only), then one warp per output row block sums X[r, n] (6x6)
+// C[n, t] (6x16) over the pattern neighbours n holding t.
 // ---------------------------------------------------------------------------
 constexpr int kXcBatch = 4;   // matched neighbours whose loads are in flight together
 template <typename T>
