@@ -554,7 +554,9 @@ __global__ void k_extract_diag(int n_tiles, const int* __restrict__ tile_mo0, co
 // Density: P_mn = 2 sum_{occ tiles t in rows m and n} C[m,t] C[n,t]^T on the
 // molecule-pair pattern; q_a += sum_{mu in a} sum_nu P_mu,nu S_mu,nu and the
 // band energy sum P*H0 per molecule (Eq. pop). One CTA per row block m, one
-// warp per neighbour n, results combined in neighbour order.
+// warp per neighbour n >= m (P_nm = P_mn^T): each pair's shares of q and of
+// the band energy are written for both rows, and k_density_sum adds them per
+// molecule in neighbour order.
 // ---------------------------------------------------------------------------
 constexpr int kDensWarps = 8;
 constexpr int kDensFlush = 32;  // tiles per lane between FP64 flushes (FP32 sums of at most 32 products)
