@@ -363,12 +363,14 @@ def main():
         prep = ctx.orthonormalise(SSCF_ORTHO_ALL, max_pass=args.prep_passes)
         ctx.set_thresholds(args.eps, 10 * args.eps, 1e-6)
         ctx.reset_charges()
-        # warm-up: one eager step, the launch-shape autotuner, then the rest
-        # (graph-captured when asked, so that no capture falls in the timed region)
+        # warm-up: eager steps, then the launch-shape autotuner on the state of
+        # the last warm-up step (the closest to the replayed one), which that step
+        # runs with (graph-captured when asked, so that no capture falls in the
+        # timed region)
         warm = None
         tuned = None
         for w in range(max(args.warmup, 0)):
-            if w == 1 or (w == 0 and args.warmup == 1):
+            if w == max(args.warmup - 1, 0):
                 if not args.no_autotune:
                     tuned = ctx.autotune()
                 if args.graph:
