@@ -58,3 +58,27 @@ def test_create_rejects_bad_layout_without_touching_the_gpu():
     assert lib.sscf_create(ctypes.byref(sysc), ctypes.byref(prm), None, ctypes.byref(h)) == -1
     with pytest.raises(Exception):
         _lib.Context(species, xyz, grp, default_params())
+
+
+def test_create_rejects_empty_and_ragged_systems_without_touching_the_gpu():
+    """No atoms, a negative count, or a count that is not whole molecules
+    (O, H, H) is refused with SSCF_ERR_INVALID_ARG before any CUDA call."""
+    import ctypes
+
+    import numpy as np
+
+    from paper_1402_2880_gb300 import _lib, build
+    from synth import default_params
+    build.build()
+    lib = _lib.load()
+    prm = _lib.make_params(default_params())
+    for n_atoms in (0, -3, 4):
+        species = np.tile(np.array([0, 1, 1], dtype=np.int32), 2)
+        xyz = np.zeros(18)
+        grp = np.zeros(2, dtype=np.int32)
+        sysc = _lib.System(n_atoms=n_atoms, species=species.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                           xyz=xyz.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                           group_of_mol=grp.ctypes.data_as(ctypes.POINTER(ctypes.c_int)))
+        h = ctypes.c_void_p()
+        assert lib.sscf_create(ctypes.byref(sysc), ctypes.byref(prm), None, ctypes.byref(h)) == -1
+        assert not h.value
