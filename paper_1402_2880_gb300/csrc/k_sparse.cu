@@ -295,7 +295,7 @@ __global__ void k_xc(int tile_lo, int n_rows, int own_below, int cap, int capY, 
 // one 16-byte shared load. Rows are summed in ascending order (fixed order);
 // mixed precision flushes the FP32 partial sums to FP64 every 32 rows.
 // ---------------------------------------------------------------------------
-constexpr int kTfWarps = 8;
+constexpr int kTfWarps = 4;
 constexpr int kStage = 4;   // row blocks staged per warp at a time
 constexpr int kTcStride = 24;   // floats per staged AO row in the tensor-core path (bank-conflict-free fragments)
 constexpr int kTcRows = kStage * kAoPerMol;   // staged AO rows (K) per round: 24 = 3 k-steps of 8
